@@ -1,0 +1,169 @@
+/*
+ * gakco.h -- C ABI of the GB300-native gapped k-mer string kernel engine.
+ *
+ * The engine computes the gapped k-mer string kernel of GaKCo (Singh et al.,
+ * "GaKCo: a Fast Gapped k-mer string Kernel using Counting",
+ * arXiv 1704.07468):
+ *
+ *   Input (Table 1, Alg. 1 "Require L, g, k"): a dataset D = {x_1 .. x_N} of
+ *   strings over an alphabet of sigma symbols and the user parameters g (the
+ *   g-mer length) and k (the non-gapped length), 1 <= k <= g; M = g - k.
+ *
+ *   Mismatch profile (Definition 1, Eq. 7): N_m(x, y) = number of pairs
+ *   (i, j), i a window of x and j a window of y, whose g-mers differ in
+ *   exactly m positions.  A sequence of length l has max(0, l - g + 1)
+ *   windows (Eq. 5).  All ordered pairs count, including i == j for x == y.
+ *
+ *   Kernel (Eq. 6, Eq. 7; Alg. 1 "Ensure K"): K(x, y) = sum_{m=0}^{M}
+ *   h_m N_m(x, y) with h_m = C(g - m, k).
+ *
+ *   Normalised kernel (not in the paper; part of this interface):
+ *   Khat(x, y) = K(x, y) / sqrt(K(x, x) K(y, y)), 0 where K(x, x) or
+ *   K(y, y) is 0, and exactly 1.0 on a nonzero diagonal.  Computed in fp64;
+ *   relative error below 1e-15.
+ *
+ * The engine follows the paper's counting route (Section 2.2, Alg. 1): for
+ * every level m and every one of the C(g, m) position masks it deletes the
+ * masked positions from every g-mer, sorts the (g-m)-mers, counts equal
+ * runs, accumulates the cumulative mismatch profile C_m (Eq. 8) and
+ * recovers N_m by inclusion-exclusion (Eq. 9).  Integer outputs are exact.
+ *
+ * Conventions
+ *   - Symbols are bytes with values in [0, sigma).  A byte >= sigma makes the
+ *     call fail with GAKCO_E_INVALID (mapping unknown characters to an extra
+ *     symbol, as Section S:5.2 describes, is the caller's job).
+ *   - A dataset is `codes` (all sequences concatenated) plus `offsets`
+ *     (int64, n + 1 entries, offsets[0] = 0, non-decreasing; sequence x is
+ *     codes[offsets[x] .. offsets[x+1])).  `offsets` is always a HOST
+ *     pointer, also in the *_device calls: the host plans the work from it.
+ *   - Output matrices are row-major: K[x * n + y]; N_m at Nm[(m * n + x) * n
+ *     + y] for m = 0..M.
+ *   - Every output pointer except the kernel K may be NULL to skip it.  In
+ *     the host-buffer calls K may also be NULL.
+ *   - The caller owns every buffer.  The library copies what it needs and
+ *     keeps no pointer to caller memory after a call returns (the *_device
+ *     calls read and write the caller's device buffers on the given stream).
+ *   - Limits: n <= 65535 sequences per dataset; the number of windows of a
+ *     dataset below 2^32; g * ceil(log2 sigma) <= 64; M + 1 <= 16; and
+ *     max_m C(g, m) * W_max^2 < 2^31 (W_max = most windows of any sequence),
+ *     which keeps every C_m and K inside int32.  A call beyond a limit
+ *     returns GAKCO_E_OVERFLOW or GAKCO_E_INVALID without touching outputs.
+ *   - Errors: every call returns GAKCO_OK (0) or a negative code; the
+ *     context's message is available from gakco_last_error.  After an error
+ *     the context remains usable.
+ *   - Threads: a context is used by one host thread at a time.
+ */
+#ifndef GAKCO_H
+#define GAKCO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GAKCO_OK 0
+#define GAKCO_E_INVALID (-1)   /* bad argument or input symbol */
+#define GAKCO_E_OOM (-2)       /* device or host allocation failed */
+#define GAKCO_E_OVERFLOW (-3)  /* the int32 bound above is exceeded */
+#define GAKCO_E_CUDA (-4)      /* a CUDA call failed */
+#define GAKCO_E_TIMEOUT (-5)   /* a bounded wait ran out */
+#define GAKCO_E_PENDING (-6)   /* asynchronous work not finished yet */
+#define GAKCO_E_INTERNAL (-7)  /* an internal consistency check failed */
+
+typedef struct gakco_ctx gakco_ctx;
+
+/*
+ * Create a context for alphabet size `sigma` (2..255) and parameters g, k
+ * (1 <= k <= g, Table 1).  Selects the current CUDA device.  On success
+ * *out receives the context (owned by the caller, freed by gakco_destroy).
+ * Returns GAKCO_E_INVALID for parameters outside the limits above,
+ * GAKCO_E_CUDA when no usable device is present.
+ */
+int gakco_create(int sigma, int g, int k, gakco_ctx **out);
+
+/* Free a context and all device memory it holds.  NULL is ignored. */
+void gakco_destroy(gakco_ctx *ctx);
+
+/* Message describing the last error on this context ("" if none).  The
+ * string is owned by the context and valid until its next call. */
+const char *gakco_last_error(const gakco_ctx *ctx);
+
+/*
+ * Tuning and engine options (key, value).  Unknown keys return
+ * GAKCO_E_INVALID.
+ */
+#define GAKCO_OPT_ENGINE 1          /* 0 = batched (default), 1 = plain per-mask */
+#define GAKCO_OPT_RADIX_BITS 2      /* widest sort digit, 4..11 (default 8) */
+#define GAKCO_OPT_CHUNK_ELEMS 3     /* sort elements per batched chunk (>= 4096) */
+#define GAKCO_OPT_GRAPH 4           /* 1 = replay batched work from a CUDA graph */
+#define GAKCO_OPT_ACCUM_THREADS 5   /* 256, 512 or 1024 */
+#define GAKCO_OPT_PROFILE 6         /* 1 = time every kernel launch (no graph) */
+#define GAKCO_OPT_SMEM_COLS 7       /* cap on columns per accumulation tile (0 = auto) */
+#define GAKCO_OPT_FAIL_ALLOC_AFTER 8 /* fault injection: fail the Nth next device
+                                        allocation (0 = off); host side only */
+int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
+
+/*
+ * Statistics of the last completed call.
+ *   GAKCO_STAT_LAUNCHES     kernels launched by the call
+ *   GAKCO_STAT_MASK_PASSES  (dataset, mask) passes processed
+ *   GAKCO_STAT_DEVICE_BYTES device workspace held by the context
+ *   GAKCO_STAT_GRAPH_REPLAY 1 if the call replayed a cached CUDA graph
+ */
+#define GAKCO_STAT_LAUNCHES 1
+#define GAKCO_STAT_MASK_PASSES 2
+#define GAKCO_STAT_DEVICE_BYTES 3
+#define GAKCO_STAT_GRAPH_REPLAY 4
+int gakco_get_stat(const gakco_ctx *ctx, int key, double *value);
+
+/*
+ * Per-kernel timing of the last call made with GAKCO_OPT_PROFILE = 1:
+ * entry `idx` (0-based) gives the kernel's name, total milliseconds and
+ * number of launches.  Returns GAKCO_E_INVALID past the last entry.
+ */
+int gakco_kernel_timing(const gakco_ctx *ctx, int idx, char *name,
+                        int name_len, double *total_ms, int64_t *launches);
+
+/*
+ * Gram kernel of one dataset, host buffers (Alg. 1 CALCULATEKERNEL).
+ *   codes, offsets, n : the dataset (host)
+ *   K      : n*n int32 kernel, or NULL
+ *   Khat   : n*n fp64 normalised kernel, or NULL
+ *   Nm     : (M+1)*n*n int32 mismatch profiles N_0..N_M, or NULL
+ * Synchronous: returns after the outputs are written.
+ */
+int gakco_gram(gakco_ctx *ctx, const uint8_t *codes, const int64_t *offsets,
+               int32_t n, int32_t *K, double *Khat, int32_t *Nm);
+
+/*
+ * Gram kernels of several independent datasets in one batched pass (all
+ * datasets share sigma, g, k).  Arrays have `ndata` entries; per-dataset
+ * output pointers follow gakco_gram.  Host buffers; synchronous.
+ */
+int gakco_gram_batch(gakco_ctx *ctx, int32_t ndata,
+                     const uint8_t *const *codes,
+                     const int64_t *const *offsets, const int32_t *n,
+                     int32_t *const *K, double *const *Khat,
+                     int32_t *const *Nm);
+
+/*
+ * Device-buffer forms.  `codes`, K, Khat, Nm are device pointers (K is
+ * required); `offsets` are host pointers; `stream` is a cudaStream_t (NULL
+ * = the legacy default stream).  Work is ordered on `stream`; the call
+ * returns after it completes and the device status has been checked.
+ */
+int gakco_gram_device(gakco_ctx *ctx, const uint8_t *codes,
+                      const int64_t *offsets, int32_t n, int32_t *K,
+                      double *Khat, int32_t *Nm, void *stream);
+int gakco_gram_batch_device(gakco_ctx *ctx, int32_t ndata,
+                            const uint8_t *const *codes,
+                            const int64_t *const *offsets, const int32_t *n,
+                            int32_t *const *K, double *const *Khat,
+                            int32_t *const *Nm, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GAKCO_H */

@@ -1,1 +1,224 @@
-"""GB300-native gapped k-mer string kernel (GaKCo, arXiv 1704.07468)."""
+"""GB300-native gapped k-mer string kernel (GaKCo, arXiv 1704.07468).
+
+Thin Python binding over the C ABI declared in ``include/gakco.h``: argument
+marshalling only, every step of the computation runs in the CUDA library
+``_lib/libgakco.so``.  The names mirror the C functions:
+
+    ctx = gakco_create(sigma, g, k)
+    out = ctx.gram(codes, offsets, khat=True, nm=False)      # host buffers
+    ctx.gram_device(codes_ptr, offsets, n, K_ptr, ...)       # device buffers
+
+Loading fails loudly (``RuntimeError``) when the library is missing; there
+is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["gakco_create", "Context", "GakcoError", "load_library",
+           "library_path", "OPT", "STAT", "ERRORS"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libgakco.so")
+_lib = None
+
+GAKCO_OK = 0
+ERRORS = {
+    -1: "GAKCO_E_INVALID", -2: "GAKCO_E_OOM", -3: "GAKCO_E_OVERFLOW",
+    -4: "GAKCO_E_CUDA", -5: "GAKCO_E_TIMEOUT", -6: "GAKCO_E_PENDING",
+    -7: "GAKCO_E_INTERNAL",
+}
+OPT = {"engine": 1, "radix_bits": 2, "chunk_elems": 3, "graph": 4,
+       "accum_threads": 5, "profile": 6, "smem_cols": 7,
+       "fail_alloc_after": 8}
+STAT = {"launches": 1, "mask_passes": 2, "device_bytes": 3,
+        "graph_replay": 4}
+
+
+class GakcoError(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__(f"{ERRORS.get(code, code)}: {message}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library(build_if_missing: bool = False):
+    """Load the CUDA library.  Raises RuntimeError if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        from . import build as _build
+        _build.build()
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(
+            f"GaKCo CUDA library not found at {_LIB_PATH}; build it with "
+            "`python -m paper_1704_07468_gb300.build` (there is no CPU fallback)")
+    lib = ctypes.CDLL(_LIB_PATH)
+    p, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "gakco_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, pp], ctypes.c_int),
+        "gakco_destroy": ([p], None),
+        "gakco_last_error": ([p], ctypes.c_char_p),
+        "gakco_set_option": ([p, ctypes.c_int, i64], ctypes.c_int),
+        "gakco_get_stat": ([p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "gakco_kernel_timing": ([p, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "gakco_gram": ([p, p, p, i32, p, p, p], ctypes.c_int),
+        "gakco_gram_batch": ([p, i32, p, p, p, p, p, p], ctypes.c_int),
+        "gakco_gram_device": ([p, p, p, i32, p, p, p, p], ctypes.c_int),
+        "gakco_gram_batch_device": ([p, i32, p, p, p, p, p, p, p], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * max(1, len(ptrs)))()
+    for i, v in enumerate(ptrs):
+        arr[i] = v
+    return arr
+
+
+def _dataset(codes, offsets):
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    return codes, offsets
+
+
+class Context:
+    """A GaKCo engine context for one (sigma, g, k)."""
+
+    def __init__(self, sigma: int, g: int, k: int):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        rc = self._lib.gakco_create(int(sigma), int(g), int(k), ctypes.byref(h))
+        if rc != GAKCO_OK:
+            raise GakcoError(rc, f"gakco_create(sigma={sigma}, g={g}, k={k}) failed")
+        self._h = h
+        self.sigma, self.g, self.k, self.M = int(sigma), int(g), int(k), int(g) - int(k)
+
+    # -- lifetime --------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gakco_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- helpers ---------------------------------------------------------
+    def last_error(self) -> str:
+        return self._lib.gakco_last_error(self._h).decode()
+
+    def _check(self, rc):
+        if rc != GAKCO_OK:
+            raise GakcoError(rc, self.last_error())
+
+    def set_option(self, name, value):
+        key = OPT[name] if isinstance(name, str) else int(name)
+        self._check(self._lib.gakco_set_option(self._h, key, int(value)))
+        return self
+
+    def get_stat(self, name) -> float:
+        key = STAT[name] if isinstance(name, str) else int(name)
+        v = ctypes.c_double()
+        self._check(self._lib.gakco_get_stat(self._h, key, ctypes.byref(v)))
+        return v.value
+
+    def kernel_timings(self):
+        """{kernel name: (total ms, launches)} of the last profiled call."""
+        out = {}
+        buf = ctypes.create_string_buffer(64)
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        i = 0
+        while self._lib.gakco_kernel_timing(self._h, i, buf, 64, ctypes.byref(ms),
+                                            ctypes.byref(n)) == GAKCO_OK:
+            out[buf.value.decode()] = (ms.value, n.value)
+            i += 1
+        return out
+
+    # -- host-buffer calls -----------------------------------------------
+    def gram(self, codes, offsets, khat=True, nm=False, K=True):
+        """Gram kernel of one dataset (host arrays).  Returns a dict with
+        ``K`` (n, n) int32, ``Khat`` (n, n) float64, ``Nm`` (M+1, n, n)."""
+        return self.gram_batch([(codes, offsets)], khat=khat, nm=nm, K=K)[0]
+
+    def gram_batch(self, datasets, khat=True, nm=False, K=True):
+        """Gram kernels of several datasets in one batched call."""
+        ds = [_dataset(c, o) for c, o in datasets]
+        nd = len(ds)
+        ns = np.array([len(o) - 1 for _, o in ds], dtype=np.int32)
+        outs = []
+        for (c, o), n in zip(ds, ns):
+            outs.append({
+                "K": np.empty((n, n), np.int32) if K else None,
+                "Khat": np.empty((n, n), np.float64) if khat else None,
+                "Nm": np.empty((self.M + 1, n, n), np.int32) if nm else None,
+            })
+        keep = [c if c.size else np.zeros(1, np.uint8) for c, _ in ds]
+        rc = self._lib.gakco_gram_batch(
+            self._h, nd,
+            _ptr_array([k.ctypes.data for k in keep]),
+            _ptr_array([o.ctypes.data for _, o in ds]),
+            ns.ctypes.data_as(ctypes.c_void_p),
+            _ptr_array([o["K"].ctypes.data if o["K"] is not None else None for o in outs]),
+            _ptr_array([o["Khat"].ctypes.data if o["Khat"] is not None else None for o in outs]),
+            _ptr_array([o["Nm"].ctypes.data if o["Nm"] is not None else None for o in outs]))
+        self._check(rc)
+        return outs
+
+    # -- device-buffer calls ---------------------------------------------
+    def gram_device(self, codes_ptr, offsets, K_ptr, Khat_ptr=None, Nm_ptr=None,
+                    stream=None):
+        """Device form: pointers are device addresses (ints), ``offsets`` a
+        host int64 array, ``stream`` a cudaStream_t as int (None = default)."""
+        return self.gram_batch_device([codes_ptr], [offsets], [K_ptr], [Khat_ptr],
+                                      [Nm_ptr], stream)
+
+    def gram_batch_device(self, codes_ptrs, offsets, K_ptrs, Khat_ptrs=None,
+                          Nm_ptrs=None, stream=None):
+        nd = len(codes_ptrs)
+        offs = [np.ascontiguousarray(o, dtype=np.int64) for o in offsets]
+        ns = np.array([len(o) - 1 for o in offs], dtype=np.int32)
+        Khat_ptrs = Khat_ptrs or [None] * nd
+        Nm_ptrs = Nm_ptrs or [None] * nd
+        rc = self._lib.gakco_gram_batch_device(
+            self._h, nd, _ptr_array(codes_ptrs),
+            _ptr_array([o.ctypes.data for o in offs]),
+            ns.ctypes.data_as(ctypes.c_void_p), _ptr_array(K_ptrs),
+            _ptr_array(Khat_ptrs), _ptr_array(Nm_ptrs),
+            ctypes.c_void_p(stream) if stream else None)
+        self._check(rc)
+
+
+def gakco_create(sigma: int, g: int, k: int) -> Context:
+    """Create an engine context (C: ``gakco_create``)."""
+    return Context(sigma, g, k)

@@ -1,0 +1,359 @@
+// Kernel-update stage (Section 2.2, steps 2-5; Alg. 1 countAndUpdate and
+// the sum C_m = sum_i C_m^i), inclusion-exclusion (Eq. 9), the kernel
+// K = sum_m h_m N_m (Eq. 6, Eq. 7) and normalisation.
+//
+// For one mask, let F be the count matrix with F[f, x] = number of windows
+// of sequence x whose (g-m)-mer is feature f.  The mask adds F^T F to C_m:
+// for every feature, c_x * c_y to every pair of sequences holding it.  Only
+// features held by several sequences touch off-diagonal entries (the paper
+// counts those, "> 1", at step 2).
+//
+// k_accum computes whole rows of C_0..C_M at once.  One block owns row x of
+// one dataset and keeps C_0(x, .) .. C_M(x, .) in shared memory; its warps
+// walk every mask, and for each entry (f, x, c_x) of the row they add
+// c_x * c_y for every entry (f, y, c_y) of the same feature with y >= x.
+// Entries of a feature are sorted by sequence, so y >= x is the tail of the
+// feature's entry range.  When the row is done the block applies Eq. 9 and
+// Eq. 7 elementwise and writes the upper triangle of K (and N_m).  The sum
+// over masks is thus formed on chip, and C_m never exists in global memory.
+#include <cstdint>
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace gk {
+
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr uint32_t kLong = 32;  // entry ranges this long are walked by a warp
+
+// First entry in [lo, hi) whose sequence is >= seq.
+__device__ __forceinline__ uint32_t lower_bound_seq(const uint32_t* __restrict__ es,
+                                                    uint32_t lo, uint32_t hi,
+                                                    uint32_t seq) {
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if ((es[mid] >> 16) < seq)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Eq. 9 then Eq. 7 for one (x, y): N_m = C_m - sum_{j<m} C(g-j, m-j) N_j,
+// K = sum_m h_m N_m.  Arithmetic is modulo 2^32; every final N_m lies in
+// [0, W_x W_y] and K < 2^31 (checked on the host), so the results are exact.
+__device__ __forceinline__ uint32_t ie_combine(const uint32_t* C, uint32_t M,
+                                               const uint32_t (*ie)[kMaxLevels],
+                                               const uint32_t* h,
+                                               uint32_t* N) {
+  uint32_t K = 0;
+#pragma unroll
+  for (int m = 0; m < kMaxLevels; ++m) {
+    if ((uint32_t)m <= M) {
+      uint32_t v = C[m];
+#pragma unroll
+      for (int j = 0; j < m; ++j) v -= ie[m][j] * N[j];
+      N[m] = v;
+      K += h[m] * v;
+    }
+  }
+  return K;
+}
+
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads)
+k_accum(const AccParams p) {
+  extern __shared__ uint32_t acc[];   // (M + 1) x ncols
+  __shared__ uint32_t s_item;
+  constexpr int kWarps = kThreads / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t M = p.M;
+  const uint32_t NC = p.ncols;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(p.counter, 1u);
+    __syncthreads();
+    const uint32_t it = s_item;
+    if (it >= p.nitems) return;
+    const uint32_t d = p.items[4 * (uint64_t)it];
+    const uint32_t x = p.items[4 * (uint64_t)it + 1];
+    const uint32_t c0 = p.items[4 * (uint64_t)it + 2];
+    const uint32_t c1 = p.items[4 * (uint64_t)it + 3];
+    const DsInfo ds = p.ds[d];
+    const uint32_t width = c1 - c0;
+    for (uint32_t lv = 0; lv <= M; ++lv)
+      for (uint32_t i = threadIdx.x; i < width; i += kThreads) acc[lv * NC + i] = 0;
+    __syncthreads();
+    const uint32_t wbeg = ds.woff[x], wend = ds.woff[x + 1];
+    const uint32_t gd = ds.woff[ds.n];  // windows of the dataset: bound of every entry index
+    const bool lo_cut = c0 > x, hi_cut = c1 < ds.n;
+    for (uint32_t mu = w; mu < p.nmasks; mu += kWarps) {
+      const uint64_t pool = (uint64_t)mu * p.gtot + ds.win0;
+      const uint32_t* __restrict__ ew = p.ewin + pool;
+      const uint32_t* __restrict__ es = p.eseq + pool;
+      const uint32_t* __restrict__ ef = p.efe + pool;
+      uint32_t* a = acc + p.mask_level[mu] * NC;
+      for (uint32_t w0 = wbeg; w0 < wend; w0 += 32) {
+        const uint32_t wi = w0 + lane;
+        uint32_t e = wi < wend ? ew[wi] : kNone;
+        uint32_t lo = 0, cnt = 0, c = 0;
+        if (e != kNone && (e >= gd || ef[e] > gd || ef[e] <= e)) {
+          atomicOr(p.status, kErrBadEntry);  // corrupt entry: skip it
+          e = kNone;
+        }
+        if (e != kNone) {
+          c = es[e] & 0xFFFFu;
+          uint32_t hi = ef[e];
+          lo = e;
+          if (lo_cut) lo = lower_bound_seq(es, e, hi, c0);
+          if (hi_cut) hi = lower_bound_seq(es, lo, hi, c1);
+          cnt = hi - lo;
+        }
+        // Long entry ranges: the whole warp walks one range at a time.
+        uint32_t longm = __ballot_sync(kFull, cnt >= kLong);
+        while (longm) {
+          const int L = __ffs(longm) - 1;
+          longm &= longm - 1;
+          const uint32_t lL = __shfl_sync(kFull, lo, L);
+          const uint32_t nL = __shfl_sync(kFull, cnt, L);
+          const uint32_t cL = __shfl_sync(kFull, c, L);
+          for (uint32_t q = lane; q < nL; q += 32) {
+            const uint32_t v = es[lL + q];
+            const uint32_t yy = (v >> 16) - c0;
+            if (yy < width)
+              atomicAdd(&a[yy], cL * (v & 0xFFFFu));
+            else
+              atomicOr(p.status, kErrBadEntry);
+          }
+        }
+        if (cnt >= kLong) cnt = 0;
+        // Short ranges: expand all pairs of the 32 lanes, 32 at a time.
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        const uint32_t excl = incl - cnt;
+        for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+          const uint32_t pp = p0 + lane;
+          uint32_t o = 0;  // owner lane: first lane whose inclusive count > pp
+#pragma unroll
+          for (int step = 16; step >= 1; step >>= 1) {
+            const uint32_t v = __shfl_sync(kFull, incl, o + step - 1);
+            if (v <= pp) o += step;
+          }
+          const uint32_t lo_o = __shfl_sync(kFull, lo, o);
+          const uint32_t ex_o = __shfl_sync(kFull, excl, o);
+          const uint32_t c_o = __shfl_sync(kFull, c, o);
+          if (pp < total) {
+            const uint32_t v = es[lo_o + (pp - ex_o)];
+            const uint32_t yy = (v >> 16) - c0;
+            if (yy < width)
+              atomicAdd(&a[yy], c_o * (v & 0xFFFFu));
+            else
+              atomicOr(p.status, kErrBadEntry);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // Row epilogue: Eq. 9, Eq. 7 and the identity K == C_M.
+    const uint64_t nn = (uint64_t)ds.n * ds.n;
+    for (uint32_t y = c0 + threadIdx.x; y < c1; y += kThreads) {
+      uint32_t C[kMaxLevels], N[kMaxLevels];
+#pragma unroll
+      for (int m = 0; m < kMaxLevels; ++m)
+        C[m] = (uint32_t)m <= M ? acc[m * NC + (y - c0)] : 0u;
+      const uint32_t K = ie_combine(C, M, p.ie, p.h, N);
+      uint32_t CM = 0;
+#pragma unroll
+      for (int m = 0; m < kMaxLevels; ++m)
+        if ((uint32_t)m == M) CM = C[m];
+      if (K != CM) atomicOr(p.status, kErrKneCM);
+      const uint64_t o = (uint64_t)x * ds.n + y;
+      ds.K[o] = (int32_t)K;
+      if (ds.Nm) {
+#pragma unroll
+        for (int m = 0; m < kMaxLevels; ++m)
+          if ((uint32_t)m <= M) ds.Nm[(uint64_t)m * nn + o] = (int32_t)N[m];
+      }
+      if (y == x) ds.rinv[x] = K ? 1.0 / sqrt((double)K) : 0.0;
+    }
+  }
+}
+
+// Mirror the strict lower triangle of K (and of each N_m) from the upper
+// triangle, and write the normalised kernel
+//   Khat(x, y) = K(x, y) / sqrt(K(x, x) K(y, y)),
+// computed as (K * r_x) * r_y with r = 1 / sqrt(K(x, x)) (relative error a
+// few ulp), exactly 1 on a nonzero diagonal and 0 where a diagonal is 0.
+// One block per 32 x 32 output tile.
+__global__ void __launch_bounds__(256)
+k_finish(const DsInfo* __restrict__ dsv, uint32_t nds, uint32_t M, int want_nm,
+         int want_khat) {
+  __shared__ int32_t tile[32][33];
+  const uint32_t b = blockIdx.x;
+  uint32_t d = 0;
+  while (d + 1 < nds && dsv[d + 1].tile0 <= b) ++d;
+  const DsInfo D = dsv[d];
+  const uint32_t n = D.n, nt = (n + 31) / 32;
+  const uint32_t t = b - D.tile0;
+  const uint32_t I = t / nt, J = t % nt;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const uint64_t nn = (uint64_t)n * n;
+  const int nplanes = 1 + ((want_nm && D.Nm) ? (int)M + 1 : 0);
+  for (int pl = 0; pl < nplanes; ++pl) {
+    int32_t* X = pl == 0 ? D.K : D.Nm + (uint64_t)(pl - 1) * nn;
+    if (I >= J) {
+      for (int r = ty; r < 32; r += 8) {
+        const uint32_t row = J * 32 + r, col = I * 32 + tx;
+        if (row < n && col < n) tile[r][tx] = X[(uint64_t)row * n + col];
+      }
+      __syncthreads();
+      for (int r = ty; r < 32; r += 8) {
+        const uint32_t row = I * 32 + r, col = J * 32 + tx;
+        if (row < n && col < n && row > col) X[(uint64_t)row * n + col] = tile[tx][r];
+      }
+    }
+    if (pl == 0 && want_khat && D.Khat) {
+      for (int r = ty; r < 32; r += 8) {
+        const uint32_t row = I * 32 + r, col = J * 32 + tx;
+        if (row >= n || col >= n) continue;
+        int32_t k;
+        if (I > J || (I == J && row > col))
+          k = tile[tx][r];
+        else if (I == J)
+          k = tile[r][tx];
+        else
+          k = X[(uint64_t)row * n + col];
+        double v;
+        if (row == col)
+          v = D.rinv[row] > 0.0 ? 1.0 : 0.0;
+        else
+          v = ((double)k * D.rinv[row]) * D.rinv[col];
+        D.Khat[(uint64_t)row * n + col] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// countAndUpdate exactly as Alg. 1 states it: one thread per entry
+// (f, x, c_x) adds c_x * c_y into the global C_m(x, y) for every entry
+// (f, y, c_y) of its feature with y >= x.
+__global__ void __launch_bounds__(256)
+k_pairs_global(const uint32_t* __restrict__ segtot_E, const uint32_t* __restrict__ eseq,
+               const uint32_t* __restrict__ efe, uint32_t* __restrict__ Cm, uint32_t n,
+               uint32_t* __restrict__ status) {
+  const uint32_t E = *segtot_E;
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const uint32_t v = eseq[e];
+  const uint64_t row = (uint64_t)(v >> 16) * n;
+  const uint32_t c = v & 0xFFFFu, hi = efe[e];
+  if (hi > E || (v >> 16) >= n) {
+    atomicOr(status, kErrBadEntry);
+    return;
+  }
+  for (uint32_t e2 = e; e2 < hi; ++e2) {
+    const uint32_t v2 = eseq[e2];
+    if ((v2 >> 16) < n)
+      atomicAdd(&Cm[row + (v2 >> 16)], c * (v2 & 0xFFFFu));
+    else
+      atomicOr(status, kErrBadEntry);
+  }
+}
+
+// Eq. 9 and Eq. 7 over the upper triangle of the global C_0..C_M.
+__global__ void __launch_bounds__(256)
+k_ie_combine(const DsInfo* __restrict__ dsv, const uint32_t* __restrict__ Cg,
+             const AccParams p) {
+  const DsInfo D = *dsv;
+  const uint64_t nn = (uint64_t)D.n * D.n;
+  for (uint64_t o = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; o < nn;
+       o += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t x = (uint32_t)(o / D.n), y = (uint32_t)(o % D.n);
+    if (y < x) continue;
+    uint32_t C[kMaxLevels], N[kMaxLevels];
+#pragma unroll
+    for (int m = 0; m < kMaxLevels; ++m) C[m] = (uint32_t)m <= p.M ? Cg[m * nn + o] : 0u;
+    const uint32_t K = ie_combine(C, p.M, p.ie, p.h, N);
+    uint32_t CM = 0;
+#pragma unroll
+    for (int m = 0; m < kMaxLevels; ++m)
+      if ((uint32_t)m == p.M) CM = C[m];
+    if (K != CM) atomicOr(p.status, kErrKneCM);
+    D.K[o] = (int32_t)K;
+    if (D.Nm) {
+#pragma unroll
+      for (int m = 0; m < kMaxLevels; ++m)
+        if ((uint32_t)m <= p.M) D.Nm[m * nn + o] = (int32_t)N[m];
+    }
+    if (y == x) D.rinv[x] = K ? 1.0 / sqrt((double)K) : 0.0;
+  }
+}
+
+}  // namespace
+
+int accum_max_threads() { return 1024; }
+
+template <int T>
+static void accum_t(const AccParams& p, int blocks, size_t smem, cudaStream_t st) {
+  k_accum<T><<<blocks, T, smem, st>>>(p);
+}
+
+void launch_accum(const AccParams& p, int threads, int blocks, size_t smem,
+                  cudaStream_t st) {
+  if (p.nitems == 0) return;
+  if (threads == 256)
+    accum_t<256>(p, blocks, smem, st);
+  else if (threads == 1024)
+    accum_t<1024>(p, blocks, smem, st);
+  else
+    accum_t<512>(p, blocks, smem, st);
+}
+
+int accum_blocks_per_sm(int threads, size_t smem) {
+  int nb = 0;
+  cudaError_t e;
+  if (threads == 256) {
+    e = cudaFuncSetAttribute(k_accum<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_accum<256>, 256, smem);
+  } else if (threads == 1024) {
+    e = cudaFuncSetAttribute(k_accum<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_accum<1024>, 1024, smem);
+  } else {
+    e = cudaFuncSetAttribute(k_accum<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_accum<512>, 512, smem);
+  }
+  return e ? -1 : nb;
+}
+
+void launch_finish(const DsInfo* d_ds, uint32_t nds, uint32_t ntiles, uint32_t M,
+                   bool want_nm, bool want_khat, cudaStream_t st) {
+  if (ntiles == 0) return;
+  k_finish<<<ntiles, 256, 0, st>>>(d_ds, nds, M, want_nm ? 1 : 0, want_khat ? 1 : 0);
+}
+
+void launch_pairs_global(const uint32_t* segtot_E, const uint32_t* eseq,
+                         const uint32_t* efe, uint32_t G, uint32_t* Cm, uint32_t n,
+                         uint32_t* status, cudaStream_t st) {
+  if (G == 0) return;
+  k_pairs_global<<<(G + 255) / 256, 256, 0, st>>>(segtot_E, eseq, efe, Cm, n, status);
+}
+
+void launch_ie_combine(const DsInfo* d_ds, const uint32_t* C, uint32_t n,
+                       const AccParams& coef, cudaStream_t st) {
+  const uint64_t nn = (uint64_t)n * n;
+  if (nn == 0) return;
+  uint64_t blocks = (nn + 255) / 256;
+  if (blocks > 65535ull * 16) blocks = 65535ull * 16;
+  k_ie_combine<<<(unsigned)blocks, 256, 0, st>>>(d_ds, C, coef);
+}
+
+}  // namespace gk

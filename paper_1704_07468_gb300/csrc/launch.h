@@ -1,0 +1,82 @@
+// Host-side launch wrappers of the engine's kernels (one definition per .cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace gk {
+
+// Per-dataset description for the g-mer packing kernel.
+struct DsPack {
+  const uint8_t* codes;   // device, symbols of all sequences concatenated
+  const int64_t* coff;    // device, n + 1 code offsets
+  const uint32_t* woff;   // device, n + 1 window offsets
+  uint64_t win0;          // first global window
+  uint32_t n;
+  uint32_t seq0;          // first global sequence
+};
+
+// k_prep.cu -------------------------------------------------------------
+int prep_init();  // one-time kernel attributes; returns a cudaError_t
+void launch_pack(const DsPack* d_ds, uint32_t nds, uint32_t nseq_total,
+                 int g, int bits, int sigma, uint64_t* fullkey,
+                 uint32_t* win2seq, uint32_t* status, cudaStream_t st);
+
+// One LSD radix-sort pass over every segment of a chunk.  For the first
+// pass the keys are cut out of the full g-mer keys (`fullkey`) and the
+// payload is the dataset-local window index; later passes read kin/vin.
+void launch_sort_pass(bool wide, bool first, const SegDesc* segs,
+                      uint32_t nsegs, const uint32_t* tile_seg,
+                      uint32_t ntiles, const MaskDesc* masks,
+                      const uint64_t* fullkey, const void* kin,
+                      const uint32_t* vin, void* kout, uint32_t* vout,
+                      uint32_t* hist, int shift, int rbits, cudaStream_t st);
+
+// Run-length pass over sorted segments: entries (feature, sequence, count)
+// and features (runs of equal keys).  Writes, per segment, ewin / eseq /
+// efe into the pools.
+void launch_rle(bool wide, const SegDesc* segs, uint32_t nsegs,
+                const uint32_t* tile_seg, uint32_t ntiles, const void* keys,
+                const uint32_t* vals, const uint32_t* win2seq,
+                uint32_t* tcnt, uint32_t* segtot, uint32_t* estart,
+                uint32_t* etseq, uint32_t* efid, uint32_t* fstart,
+                uint32_t* ewin, uint32_t* eseq, uint32_t* efe,
+                cudaStream_t st);
+
+// k_accum.cu ------------------------------------------------------------
+struct AccParams {
+  const DsInfo* ds;
+  const uint32_t* items;      // 4 x u32 per item: dataset, row, c0, c1
+  uint32_t nitems;
+  uint32_t* counter;
+  const uint32_t* mask_level;
+  uint32_t nmasks;
+  uint32_t M;
+  uint64_t gtot;
+  const uint32_t* ewin;
+  const uint32_t* eseq;
+  const uint32_t* efe;
+  uint32_t ncols;             // columns held in shared memory per level
+  uint32_t* status;
+  uint32_t h[kMaxLevels];
+  uint32_t ie[kMaxLevels][kMaxLevels];
+};
+
+int accum_max_threads();
+void launch_accum(const AccParams& p, int threads, int blocks,
+                  size_t smem, cudaStream_t st);
+int accum_blocks_per_sm(int threads, size_t smem);
+
+void launch_finish(const DsInfo* d_ds, uint32_t nds, uint32_t ntiles,
+                   uint32_t M, bool want_nm, bool want_khat, cudaStream_t st);
+
+// Plain per-mask path (Alg. 1 as written: countAndUpdate straight into the
+// global C_m with atomics, then inclusion-exclusion).
+void launch_pairs_global(const uint32_t* segtot_E, const uint32_t* eseq,
+                         const uint32_t* efe, uint32_t G, uint32_t* Cm,
+                         uint32_t n, uint32_t* status, cudaStream_t st);
+void launch_ie_combine(const DsInfo* d_ds, const uint32_t* C, uint32_t n,
+                       const AccParams& coef, cudaStream_t st);
+
+}  // namespace gk

@@ -1,0 +1,184 @@
+"""Parity of the CUDA engine with the CPU oracle, through the C ABI.
+
+Integer outputs (K and every N_m) must be bit-exact; the normalised kernel
+must agree within 1e-12 relative (both sides compute it in fp64, the engine
+as (K * r_x) * r_y with r = 1/sqrt(K(x, x)), a few ulp from the oracle's
+K / sqrt(Kxx Kyy)).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1704_07468_gb300 as pkg
+from paper_1704_07468_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+KHAT_RTOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1704_07468_gb300 import build as lib_build
+    lib_build.build()
+    pkg.load_library()
+
+
+def _check(out, ref, rows=None, nm=True):
+    K = out["K"] if rows is None else out["K"][rows]
+    np.testing.assert_array_equal(K, ref["K"])
+    if nm:
+        Nm = out["Nm"] if rows is None else out["Nm"][:, rows]
+        np.testing.assert_array_equal(Nm, ref["Nm"])
+    Kh = out["Khat"] if rows is None else out["Khat"][rows]
+    err = np.abs(Kh - ref["Khat"])
+    assert np.all(err <= KHAT_RTOL * np.maximum(np.abs(ref["Khat"]), 1e-300) + 1e-300), \
+        f"max Khat err {err.max()}"
+
+
+def _gram(sigma, g, k, codes, off, **opts):
+    with pkg.gakco_create(sigma, g, k) as ctx:
+        for name, v in opts.items():
+            ctx.set_option(name, v)
+        return ctx.gram(codes, off, khat=True, nm=True)
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+def test_dna_toy_bit_exact(engine):
+    codes, off = synth.dna_toy()
+    ref = oracle.gram(codes, off, 7, 5)
+    _check(_gram(4, 7, 5, codes, off, engine=engine), ref)
+
+
+RAGGED = [  # (seed, n, sigma, lo, hi, g, k)
+    (20, 37, 4, 0, 260, 6, 3),      # empty and short sequences, several tiles
+    (21, 64, 20, 0, 400, 8, 4),     # protein alphabet, 40-bit keys
+    (22, 50, 36, 5, 300, 8, 5),     # text alphabet, 48-bit keys (wide sort)
+    (23, 20, 4, 8, 120, 10, 6),     # DNA g = 10, M = 4
+    (24, 9, 2, 0, 50, 3, 1),        # binary alphabet, M = 2
+    (25, 15, 5, 1, 90, 5, 5),       # k = g: spectrum kernel, M = 0
+    (26, 12, 3, 2, 60, 9, 1),       # M = 8: nine levels
+]
+
+
+@pytest.mark.parametrize("case", RAGGED)
+@pytest.mark.parametrize("engine", [0, 1])
+def test_ragged_random_bit_exact(case, engine):
+    seed, n, sigma, lo, hi, g, k = case
+    codes, off = synth.random_small(seed, n, sigma, lo, hi)
+    ref = oracle.gram(codes, off, g, k)
+    _check(_gram(sigma, g, k, codes, off, engine=engine), ref)
+
+
+@pytest.mark.parametrize("opts", [
+    {"radix_bits": 4}, {"radix_bits": 11}, {"chunk_elems": 4096},
+    {"smem_cols": 7}, {"smem_cols": 32, "accum_threads": 256},
+    {"accum_threads": 1024}, {"graph": 0},
+])
+def test_tuning_options_do_not_change_results(opts):
+    codes, off = synth.random_small(30, 70, 20, 0, 300)
+    ref = oracle.gram(codes, off, 8, 4)
+    _check(_gram(20, 8, 4, codes, off, **opts), ref)
+
+
+@pytest.mark.parametrize("kind", ["homopolymer", "period2", "mixed"])
+def test_repetitive_sequences_large_counts(kind):
+    """Counts of one feature in one sequence far above 127."""
+    codes, off = synth.repeats(kind, n=5, length=700)
+    ref = oracle.gram(codes, off, 10, 6)
+    _check(_gram(4, 10, 6, codes, off), ref)
+
+
+def test_batch_equals_individual_calls():
+    sets = [synth.random_small(40 + i, n, 4, 50, 200) for i, n in enumerate([30, 1, 0, 45])]
+    with pkg.gakco_create(4, 8, 5) as ctx:
+        batch = ctx.gram_batch(sets, khat=True, nm=True)
+        for (c, o), b in zip(sets, batch):
+            single = ctx.gram(c, o, khat=True, nm=True)
+            for key in ("K", "Nm", "Khat"):
+                np.testing.assert_array_equal(b[key], single[key])
+            if len(o) > 1:
+                ref = oracle.gram(c, o, 8, 5)
+                _check(b, ref)
+
+
+def test_graph_replay_is_used_and_identical():
+    codes, off = synth.random_small(50, 40, 4, 20, 150)
+    with pkg.gakco_create(4, 7, 4) as ctx:
+        a = ctx.gram(codes, off, khat=True, nm=True)
+        assert ctx.get_stat("graph_replay") == 0
+        b = ctx.gram(codes, off, khat=True, nm=True)
+        assert ctx.get_stat("graph_replay") == 1
+        for key in ("K", "Nm", "Khat"):
+            np.testing.assert_array_equal(a[key], b[key])
+        assert ctx.get_stat("launches") > 0
+
+
+def test_degenerate_inputs():
+    g, k = 5, 3
+    cases = [
+        synth.pack([]),                                  # no sequences
+        synth.pack([np.zeros(3, np.uint8)]),             # one sequence, no window
+        synth.pack([np.zeros(5, np.uint8)]),             # exactly one window
+        synth.pack([np.array([], np.uint8)] * 3),        # empty sequences only
+    ]
+    with pkg.gakco_create(4, g, k) as ctx:
+        for codes, off in cases:
+            out = ctx.gram(codes, off, khat=True, nm=True)
+            n = len(off) - 1
+            if n:
+                ref = oracle.gram(codes, off, g, k)
+                _check(out, ref)
+            else:
+                assert out["K"].shape == (0, 0)
+
+
+def test_invalid_symbol_is_rejected_and_context_survives():
+    codes, off = synth.random_small(60, 6, 4, 10, 40)
+    bad = codes.copy()
+    bad[5] = 4
+    with pkg.gakco_create(4, 5, 3) as ctx:
+        with pytest.raises(pkg.GakcoError) as ei:
+            ctx.gram(bad, off)
+        assert ei.value.name == "GAKCO_E_INVALID"
+        _check(ctx.gram(codes, off, khat=True, nm=True), oracle.gram(codes, off, 5, 3))
+
+
+def test_overflow_bound_is_enforced():
+    # C(10, 4) * W^2 >= 2^31 for W = 3200.
+    codes, off = synth.pack([np.zeros(3209, np.uint8)])
+    with pkg.gakco_create(4, 10, 6) as ctx:
+        with pytest.raises(pkg.GakcoError) as ei:
+            ctx.gram(codes, off)
+        assert ei.value.name == "GAKCO_E_OVERFLOW"
+
+
+def test_injected_allocation_failure_leaves_context_usable():
+    codes, off = synth.random_small(61, 10, 4, 10, 60)
+    with pkg.gakco_create(4, 6, 3) as ctx:
+        ctx.set_option("fail_alloc_after", 1)
+        with pytest.raises(pkg.GakcoError) as ei:
+            ctx.gram(codes, off)
+        assert ei.value.name == "GAKCO_E_OOM"
+        _check(ctx.gram(codes, off, khat=True, nm=True), oracle.gram(codes, off, 6, 3))
+
+
+def test_device_api_with_torch_buffers_and_stream():
+    import torch
+
+    codes, off = synth.random_small(62, 33, 20, 30, 200)
+    g, k = 8, 4
+    n = len(off) - 1
+    dev = torch.device("cuda:0")
+    d_codes = torch.from_numpy(codes).to(dev)
+    K = torch.empty((n, n), dtype=torch.int32, device=dev)
+    Kh = torch.empty((n, n), dtype=torch.float64, device=dev)
+    Nm = torch.empty((g - k + 1, n, n), dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream()
+    with pkg.gakco_create(20, g, k) as ctx:
+        ctx.gram_device(d_codes.data_ptr(), off, K.data_ptr(), Kh.data_ptr(),
+                        Nm.data_ptr(), stream=s.cuda_stream)
+    s.synchronize()
+    ref = oracle.gram(codes, off, g, k)
+    _check({"K": K.cpu().numpy(), "Nm": Nm.cpu().numpy(), "Khat": Kh.cpu().numpy()}, ref)
