@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Benchmark of the gapped k-mer kernel engine on one node.
+
+One step = the whole hot path over one batch of synthetic datasets: g-mer
+packing, every (m, mask) sort and run-length pass, the on-chip C_m
+accumulation with inclusion-exclusion and K = sum h_m N_m, mirroring and
+fp64 normalisation.  Default workload: five independent DNA datasets
+(N = 500, 1000, 2000, 3000, 4000; lengths uniform in [100, 300]; GC 0.4;
+g = 10, k = 6, M = 4), all in one batched call replayed from a CUDA graph.
+
+Prints one JSON line.  ``value`` is Gram entries per second (sum of N_i^2
+over datasets and ranks / step time) with inputs resident on the device;
+``e2e`` is the same metric through the host-buffer C ABI call, host<->device
+copies included.  ``--impl reference`` times the CPU oracle instead.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W]
+                       [--workload dna_large|dna_toy|protein|text]
+                       [--impl ours|reference]
+Multi-GPU: launch with torch.distributed.run, one rank per GPU; each rank
+processes its own independently seeded batch (weak scaling, no collective
+on the data path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1704_07468_gb300 import synth  # noqa: E402
+
+METRIC = "Gram entries/s"
+UNIT = "entries/s"
+L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
+SMEM_BANKS = 32              # shared-memory banks per SM (32-bit each)
+
+
+def make_workload(name, rank=0):
+    """-> (description, sigma, g, k, list of (codes, offsets))."""
+    off = 1000 * rank
+    if name == "dna_large":
+        sets = synth.dna_large(seeds=tuple(s + off for s in (2, 3, 4, 5, 6)))
+        return ("DNA large-M batched: 5 datasets, N=500/1000/2000/3000/4000, "
+                "lengths U[100,300], GC 0.4, g=10 k=6 (M=4)", 4, 10, 6, sets)
+    if name == "dna_toy":
+        return ("DNA toy: N=200, length 100, uniform ACGT, g=7 k=5 (M=2)", 4, 7, 5,
+                [synth.dna_toy(seed=1 + off)])
+    if name == "protein":
+        return ("protein: N=3312, sigma=20, Dirichlet(2) residues, log-normal lengths "
+                "(median 300, clipped [50,1000]), g=8 k=4 (M=4)", 20, 8, 4,
+                [synth.protein(seed=7 + off)])
+    if name == "text":
+        return ("text: N=6000, sigma=36, Zipf(1.1) symbols, lengths U[200,2000], "
+                "g=8 k=5 (M=3)", 36, 8, 5, [synth.text(seed=8 + off)])
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], 0, set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = max(smax, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def oracle_sample(sigma, g, k, sets, rows_per_set, threads):
+    """Time the CPU oracle on a bounded sample: `rows_per_set` rows of the
+    largest dataset against all of its columns.  Returns (entries/s,
+    seconds, description)."""
+    import oracle
+
+    codes, off = max(sets, key=lambda s: len(s[1]))
+    n = len(off) - 1
+    rows = np.linspace(0, n - 1, rows_per_set).round().astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.gram(codes, off, g, k, rows=rows, threads=threads)
+    dt = time.perf_counter() - t0
+    desc = (f"{rows_per_set} evenly spaced rows x all {n} columns of the N={n} dataset, "
+            f"plus the {n} self-profiles for the diagonal")
+    return rows_per_set * n / dt, dt, desc
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    desc, sigma, g, k, sets = make_workload(args.workload, 0)
+    import oracle
+    oracle.build()
+    threads = oracle.default_threads()
+    rows = args.ref_rows
+    oracle_sample(sigma, g, k, sets, 2, threads)  # warm-up (page-in)
+    vals, secs = [], []
+    for _ in range(args.warmup):
+        oracle_sample(sigma, g, k, sets, rows, threads)
+    for _ in range(args.steps):
+        v, dt, sdesc = oracle_sample(sigma, g, k, sets, rows, threads)
+        vals.append(v)
+        secs.append(dt)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * float(np.mean(secs)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sdesc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def alg_bytes_sort(ctx_sets, g, bits, radix_bits, masks_per_level):
+    """Algorithmic bytes of all sort passes of one step: per element per
+    pass, one read and one write of (key, payload); the first pass reads
+    the 8-byte full g-mer key instead."""
+    G = sum(int(np.sum(np.maximum(np.diff(o) - g + 1, 0))) for _, o in ctx_sets)
+    total = 0
+    for m, nmask in enumerate(masks_per_level):
+        kb = (g - m) * bits
+        npass = -(-kb // radix_bits)
+        kbytes = 8 if kb > 32 else 4
+        per = (8 + kbytes + 4) + (npass - 1) * 2 * (kbytes + 4)
+        total += nmask * G * per
+    return total
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1704_07468_gb300 as pkg
+    from paper_1704_07468_gb300 import build as lib_build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    lib_build.build()
+    desc, sigma, g, k, sets = make_workload(args.workload, rank)
+    ns = [len(o) - 1 for _, o in sets]
+    entries = float(sum(n * n for n in ns))
+
+    ctx = pkg.gakco_create(sigma, g, k)
+    n_masks = sum(1 for m in range(g - k + 1) for _ in range(__import__("math").comb(g, m)))
+    d_codes = [torch.from_numpy(c).to(dev) for c, _ in sets]
+    d_K = [torch.empty((n, n), dtype=torch.int32, device=dev) for n in ns]
+    d_Kh = [torch.empty((n, n), dtype=torch.float64, device=dev) for n in ns]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    offs = [o for _, o in sets]
+
+    def step():
+        ctx.gram_batch_device([t.data_ptr() for t in d_codes], offs,
+                              [t.data_ptr() for t in d_K], [t.data_ptr() for t in d_Kh],
+                              None, stream=stream.cuda_stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    launches = int(ctx.get_stat("launches"))
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        times.append((a, b))
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in times]
+    step_ms = float(np.mean(ms))
+    replay = int(ctx.get_stat("graph_replay"))
+    pairs = ctx.get_stat("pair_updates")
+    if ws > 1:
+        t = torch.tensor([step_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t.item())
+        torch.distributed.barrier()
+    value = entries * ws / (step_ms / 1000.0)
+
+    # Per-kernel timing: one profiled replay of the same step (every launch
+    # bracketed by CUDA events on the engine's stream).
+    ctx.set_option("profile", 1)
+    step()
+    torch.cuda.synchronize()
+    timings = ctx.kernel_timings()
+    ctx.set_option("profile", 0)
+    step()  # re-capture the graph for the calls below
+
+    # End to end through the host-buffer C ABI (copies included).
+    e2e_ms = []
+    for i in range(max(1, args.e2e_steps) + 1):
+        t0 = time.perf_counter()
+        ctx.gram_batch(sets, khat=True, nm=False)
+        dt = (time.perf_counter() - t0) * 1000.0
+        if i > 0:
+            e2e_ms.append(dt)
+    e2e_step = float(np.mean(e2e_ms))
+    h2d = int(sum(c.nbytes + o.nbytes for c, o in sets))
+    d2h = int(sum(n * n * (4 + 8) for n in ns))
+
+    # Plain per-mask GPU path (same kernels, one mask per launch, global
+    # atomics, no graph) for the batched-vs-plain comparison.
+    plain = None
+    if args.plain_steps > 0:
+        pctx = pkg.gakco_create(sigma, g, k)
+        pctx.set_option("engine", 1)
+        pk = [torch.empty((n, n), dtype=torch.int32, device=dev) for n in ns]
+        pkh = [torch.empty((n, n), dtype=torch.float64, device=dev) for n in ns]
+
+        def pstep():
+            pctx.gram_batch_device([t.data_ptr() for t in d_codes], offs,
+                                   [t.data_ptr() for t in pk], [t.data_ptr() for t in pkh],
+                                   None, stream=stream.cuda_stream)
+        pstep()
+        pms = []
+        for _ in range(args.plain_steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pstep()
+            b.record(stream)
+            torch.cuda.synchronize()
+            pms.append(a.elapsed_time(b))
+        same = all(torch.equal(x, y) for x, y in zip(pk, d_K))
+        plain = {"value": entries / (float(np.mean(pms)) / 1000.0), "unit": UNIT,
+                 "ms_per_step": float(np.mean(pms)),
+                 "mask_passes_per_s": len(sets) * n_masks / (float(np.mean(pms)) / 1000.0),
+                 "launches": int(pctx.get_stat("launches")),
+                 "bit_identical_K": bool(same)}
+        pctx.close()
+
+    # Roofline of the dominant kernel.
+    peaks, peak_kind = measured_peaks()
+    dom = max(timings.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    per_launch_ms = dom_ms / dom_n
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof = None
+    if dom_name == "accumulate":
+        # Bound by shared-memory read-modify-write throughput: one 32-bit
+        # add per pair update; peak = banks x SMs x max SM clock.
+        peak = SMEM_BANKS * sm_count * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = pairs / (per_launch_ms / 1000.0) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tupdates/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_accum",
+                "peak_source": "32 shared-memory banks x SMs x max SM clock"}
+    elif dom_name == "sort_pass":
+        bits = max(1, (sigma - 1).bit_length())
+        lv = [__import__("math").comb(g, m) for m in range(g - k + 1)]
+        nbytes = alg_bytes_sort(sets, g, bits, 8, lv) / dom_n
+        achieved = nbytes / (per_launch_ms / 1000.0) / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "sort pass"}
+    else:
+        roof = {"bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": None, "traffic": None, "kernel": dom_name}
+    roof["peak_kind"] = peak_kind
+    roof["launch_ms"] = per_launch_ms
+    roof["share_of_step"] = dom_ms / sum(v[0] for v in timings.values())
+
+    cpu = None
+    if rank == 0 and ws == 1 and args.cpu_rows > 0:
+        import oracle
+        oracle.build()
+        thr = oracle.default_threads()
+        v, dt, sdesc = oracle_sample(sigma, g, k, sets, args.cpu_rows, thr)
+        cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sdesc,
+               "seconds": dt}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": desc, "datasets": ns, "g": g, "k": k, "sigma": sigma,
+                   "outputs": "K int32 + Khat fp64 per dataset",
+                   "l2": "256 MiB write between timed steps",
+                   "graph_replay": bool(replay), "parallelism": f"replicas x{ws} (weak)"},
+        "mask_passes_per_s": len(sets) * n_masks * ws / (step_ms / 1000.0),
+        "pair_updates_per_step": pairs,
+        "plain_gpu": plain,
+        "e2e": {"value": entries * ws / (e2e_step / 1000.0), "unit": UNIT,
+                "ms_per_step": e2e_step, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * args.steps,
+        "kernel_ms": {kname: {"ms": v[0], "launches": v[1]} for kname, v in timings.items()},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="dna_large")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-rows", type=int, default=64)
+    ap.add_argument("--ref-rows", type=int, default=16)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -110,11 +110,16 @@ int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
  *   GAKCO_STAT_MASK_PASSES  (dataset, mask) passes processed
  *   GAKCO_STAT_DEVICE_BYTES device workspace held by the context
  *   GAKCO_STAT_GRAPH_REPLAY 1 if the call replayed a cached CUDA graph
+ *   GAKCO_STAT_PAIR_UPDATES, _ENTRIES_VISITED, _WINDOWS_VISITED: work
+ *   counted on the device by the accumulation stage (0 for the plain engine)
  */
 #define GAKCO_STAT_LAUNCHES 1
 #define GAKCO_STAT_MASK_PASSES 2
 #define GAKCO_STAT_DEVICE_BYTES 3
 #define GAKCO_STAT_GRAPH_REPLAY 4
+#define GAKCO_STAT_PAIR_UPDATES 5     /* batched engine: c_x*c_y additions made */
+#define GAKCO_STAT_ENTRIES_VISITED 6  /* batched engine: (feature, sequence) entries visited */
+#define GAKCO_STAT_WINDOWS_VISITED 7  /* batched engine: (window, mask) slots read */
 int gakco_get_stat(const gakco_ctx *ctx, int key, double *value);
 
 /*

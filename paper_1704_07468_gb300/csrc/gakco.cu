@@ -119,6 +119,7 @@ struct gakco_ctx {
   int64_t launches = 0;
   int64_t last_launches = 0, last_mask_passes = 0;
   int last_replay = 0;
+  double last_pairs = 0, last_entries = 0, last_windows = 0;
   std::vector<Timed> timed;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -423,7 +424,7 @@ int plan_memory_and_tables(gakco_ctx* c, Plan& p, bool plain) {
   uint64_t nsum = 0;
   for (auto& D : p.ds) nsum += (uint64_t)D.n;
   ENSURE(rinv, nsum * 8);
-  ENSURE(status, 64);
+  ENSURE(status, 128);
   if (plain) ENSURE(Cplain, (uint64_t)(c->M + 1) * p.nmax * p.nmax * 4);
 
   Tables t;
@@ -510,6 +511,7 @@ AccParams acc_params(gakco_ctx* c, const Plan& p, uint32_t* counter) {
   a.efe = (const uint32_t*)c->efe.p;
   a.ncols = p.ncols;
   a.status = (uint32_t*)c->status.p;
+  a.work = (unsigned long long*)((uint8_t*)c->status.p + 64);
   memcpy(a.h, c->h, sizeof a.h);
   memcpy(a.ie, c->ie, sizeof a.ie);
   return a;
@@ -546,7 +548,7 @@ void enqueue_chunk(gakco_ctx* c, const Plan& p, const Chunk& ch) {
 int enqueue_work(gakco_ctx* c, const Plan& p, bool plain) {
   uint8_t* base = (uint8_t*)c->tables.p;
   uint32_t* status = (uint32_t*)c->status.p;
-  cudaMemsetAsync(status, 0, 64, c->cs);
+  cudaMemsetAsync(status, 0, 128, c->cs);
   {
     Bracket b(c, "pack", 1);
     launch_pack((const DsPack*)(base + p.o_pack), (uint32_t)p.ds.size(), p.nseq, c->g, c->bits,
@@ -608,7 +610,7 @@ uint64_t plan_key(gakco_ctx* c, const Plan& p, bool plain) {
 }
 
 int finish_call(gakco_ctx* c) {
-  cudaError_t e = cudaMemcpyAsync(c->h_status, c->status.p, 64, cudaMemcpyDeviceToHost, c->cs);
+  cudaError_t e = cudaMemcpyAsync(c->h_status, c->status.p, 128, cudaMemcpyDeviceToHost, c->cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->cs);
   if (e != cudaSuccess) return cuda_fail(c, e, "engine run");
   if (c->profile) {
@@ -627,6 +629,10 @@ int finish_call(gakco_ctx* c) {
     }
   }
   const uint32_t st = ((const uint32_t*)c->h_status)[0];
+  const unsigned long long* wk = (const unsigned long long*)((const uint8_t*)c->h_status + 64);
+  c->last_pairs = (double)wk[0];
+  c->last_entries = (double)wk[1];
+  c->last_windows = (double)wk[2];
   if (st & kErrBadCode) return fail(c, GAKCO_E_INVALID, "input holds a symbol >= sigma (%d)", c->sigma);
   if (st & kErrKneCM) return fail(c, GAKCO_E_INTERNAL, "internal check failed: sum h_m N_m != C_M");
   if (st & kErrBadEntry) return fail(c, GAKCO_E_INTERNAL, "internal check failed: entry out of range");
@@ -832,7 +838,7 @@ int gakco_create(int sigma, int g, int k, gakco_ctx** out) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMallocHost(&c->h_status, 64);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_status, 128);
   if (e == cudaSuccess) e = (cudaError_t)prep_init();
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -924,6 +930,15 @@ int gakco_get_stat(const gakco_ctx* c, int key, double* v) {
     }
     case GAKCO_STAT_GRAPH_REPLAY:
       *v = c->last_replay;
+      return GAKCO_OK;
+    case GAKCO_STAT_PAIR_UPDATES:
+      *v = c->last_pairs;
+      return GAKCO_OK;
+    case GAKCO_STAT_ENTRIES_VISITED:
+      *v = c->last_entries;
+      return GAKCO_OK;
+    case GAKCO_STAT_WINDOWS_VISITED:
+      *v = c->last_windows;
       return GAKCO_OK;
   }
   return GAKCO_E_INVALID;

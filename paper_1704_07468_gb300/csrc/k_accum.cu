@@ -89,6 +89,7 @@ k_accum(const AccParams p) {
     __syncthreads();
     const uint32_t wbeg = ds.woff[x], wend = ds.woff[x + 1];
     const uint32_t gd = ds.woff[ds.n];  // windows of the dataset: bound of every entry index
+    uint32_t n_pairs = 0, n_ent = 0;    // work counters of this thread
     const bool lo_cut = c0 > x, hi_cut = c1 < ds.n;
     for (uint32_t mu = w; mu < p.nmasks; mu += kWarps) {
       const uint64_t pool = (uint64_t)mu * p.gtot + ds.win0;
@@ -129,6 +130,8 @@ k_accum(const AccParams p) {
               atomicOr(p.status, kErrBadEntry);
           }
         }
+        n_pairs += cnt;
+        n_ent += e != kNone;
         if (cnt >= kLong) cnt = 0;
         // Short ranges: expand all pairs of the 32 lanes, 32 at a time.
         uint32_t incl = cnt;
@@ -159,6 +162,18 @@ k_accum(const AccParams p) {
               atomicOr(p.status, kErrBadEntry);
           }
         }
+      }
+    }
+    if (p.work) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        n_pairs += __shfl_xor_sync(kFull, n_pairs, o);
+        n_ent += __shfl_xor_sync(kFull, n_ent, o);
+      }
+      if (lane == 0) {
+        atomicAdd(&p.work[0], (unsigned long long)n_pairs);
+        atomicAdd(&p.work[1], (unsigned long long)n_ent);
+        if (w == 0) atomicAdd(&p.work[2], (unsigned long long)(wend - wbeg) * p.nmasks);
       }
     }
     __syncthreads();

@@ -59,6 +59,7 @@ struct AccParams {
   const uint32_t* efe;
   uint32_t ncols;             // columns held in shared memory per level
   uint32_t* status;
+  unsigned long long* work;   // [0] pair updates, [1] entries visited, [2] windows visited
   uint32_t h[kMaxLevels];
   uint32_t ie[kMaxLevels][kMaxLevels];
 };

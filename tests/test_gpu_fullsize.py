@@ -1,0 +1,121 @@
+"""Full-size parity: the workloads at their benchmark sizes, run in the
+benchmark's launch configuration (one batched device call, CUDA graph).
+
+The oracle cannot afford whole matrices here, so sampled rows are checked
+against it entry by entry (bit-exact K and N_m over all columns; normalised
+values within 1e-12), and the whole matrices are checked for properties
+that hold at any size: symmetry, unit diagonal, |Khat| <= 1, K == N-weighted
+sum, and agreement between the batched and the plain per-mask engines.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1704_07468_gb300 as pkg
+from paper_1704_07468_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+KHAT_RTOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1704_07468_gb300 import build as lib_build
+    lib_build.build()
+    oracle.build()
+
+
+def _device_batch(sigma, g, k, sets, nm=False, **opts):
+    import torch
+
+    dev = torch.device("cuda:0")
+    ns = [len(o) - 1 for _, o in sets]
+    d_codes = [torch.from_numpy(c).to(dev) for c, _ in sets]
+    K = [torch.empty((n, n), dtype=torch.int32, device=dev) for n in ns]
+    Kh = [torch.empty((n, n), dtype=torch.float64, device=dev) for n in ns]
+    Nm = [torch.empty((g - k + 1, n, n), dtype=torch.int32, device=dev) for n in ns] if nm else None
+    with pkg.gakco_create(sigma, g, k) as ctx:
+        for kk, v in opts.items():
+            ctx.set_option(kk, v)
+        ctx.gram_batch_device([t.data_ptr() for t in d_codes], [o for _, o in sets],
+                              [t.data_ptr() for t in K], [t.data_ptr() for t in Kh],
+                              [t.data_ptr() for t in Nm] if nm else None,
+                              stream=torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        out = []
+        for i in range(len(sets)):
+            out.append({"K": K[i].cpu().numpy(), "Khat": Kh[i].cpu().numpy(),
+                        "Nm": Nm[i].cpu().numpy() if nm else None})
+        return out
+
+
+def _sample_rows(n, count, seed):
+    rng = np.random.default_rng(seed)
+    rows = {0, n - 1} | set(rng.choice(n, size=min(n, count), replace=False).tolist())
+    return np.array(sorted(rows), dtype=np.int32)
+
+
+def _check_rows(out, codes, off, g, k, rows, nm):
+    ref = oracle.gram(codes, off, g, k, rows=rows, threads=len(rows))
+    np.testing.assert_array_equal(out["K"][rows], ref["K"])
+    if nm:
+        np.testing.assert_array_equal(out["Nm"][:, rows], ref["Nm"])
+    err = np.abs(out["Khat"][rows] - ref["Khat"])
+    assert np.all(err <= KHAT_RTOL * np.abs(ref["Khat"]) + 1e-300)
+    # The diagonal of every column, from the oracle's self profiles.
+    np.testing.assert_array_equal(np.diag(out["K"]), ref["diag"])
+
+
+def _check_properties(out, g, k, off):
+    K, Kh = out["K"], out["Khat"]
+    assert np.array_equal(K, K.T)
+    W = np.maximum(np.diff(off) - g + 1, 0)
+    d = np.diag(K).astype(np.int64)
+    # Self pairs alone give N_0(x, x) >= W_x, so K(x, x) >= C(g, k) W_x.
+    assert np.all(d >= math.comb(g, k) * W)
+    assert np.all(K >= 0)
+    dk = np.diag(Kh)
+    assert np.all(dk[W > 0] == 1.0) and np.all(dk[W == 0] == 0.0)
+    assert np.all(np.abs(Kh) <= 1.0 + 1e-12)
+
+
+def test_dna_large_batched_full_size():
+    sets = synth.dna_large()
+    outs = _device_batch(4, 10, 6, sets, nm=True)
+    for i, ((codes, off), out) in enumerate(zip(sets, outs)):
+        n = len(off) - 1
+        _check_properties(out, 10, 6, off)
+        _check_rows(out, codes, off, 10, 6, _sample_rows(n, 4, i), nm=True)
+        # Eq. 7 over the returned profiles.
+        h = oracle.h_coefficients(10, 6)
+        np.testing.assert_array_equal(
+            np.tensordot(h, out["Nm"].astype(np.int64), axes=(0, 0)), out["K"])
+
+
+def test_protein_full_size_and_plain_engine_agree():
+    codes, off = synth.protein()
+    out = _device_batch(20, 8, 4, [(codes, off)])[0]
+    _check_properties(out, 8, 4, off)
+    _check_rows(out, codes, off, 8, 4, _sample_rows(len(off) - 1, 8, 7), nm=False)
+    plain = _device_batch(20, 8, 4, [(codes, off)], engine=1)[0]
+    np.testing.assert_array_equal(plain["K"], out["K"])
+    np.testing.assert_array_equal(plain["Khat"], out["Khat"])
+
+
+def test_text_full_size():
+    codes, off = synth.text()
+    out = _device_batch(36, 8, 5, [(codes, off)])[0]
+    _check_properties(out, 8, 5, off)
+    _check_rows(out, codes, off, 8, 5, _sample_rows(len(off) - 1, 6, 8), nm=False)
+
+
+def test_dna_toy_config_exact():
+    codes, off = synth.dna_toy()
+    out = _device_batch(4, 7, 5, [(codes, off)], nm=True)[0]
+    ref = oracle.gram(codes, off, 7, 5)
+    np.testing.assert_array_equal(out["K"], ref["K"])
+    np.testing.assert_array_equal(out["Nm"], ref["Nm"])
+    assert np.all(np.abs(out["Khat"] - ref["Khat"]) <= KHAT_RTOL * np.abs(ref["Khat"]) + 1e-300)
