@@ -167,6 +167,41 @@ int gakco_gram_batch_device(gakco_ctx *ctx, int32_t ndata,
                             int32_t *const *K, double *const *Khat,
                             int32_t *const *Nm, void *stream);
 
+/*
+ * Gram kernel of one dataset that allocates nothing.  The paper has no
+ * counterpart; this entry point exists for callers that cannot let a
+ * library allocate device memory: applications whose GPU memory belongs to
+ * a framework's caching allocator or is split into fixed budgets up front,
+ * request paths that cannot afford the device-wide synchronisation of
+ * cudaMalloc / cudaFree, and plug-ins that are handed buffers but may not
+ * own device memory.
+ *
+ * It computes the same K, Khat and N_m as gakco_gram_device (same layouts,
+ * K required, Khat and Nm optional; codes, K, Khat, Nm are device pointers,
+ * offsets a host pointer) without a context: sigma, g, k are passed
+ * directly.  All intermediate data lives in one static device array of
+ * 64 MiB that is part of the library image (every GPU that loads the
+ * library holds it until the process exits), and host tables live in a
+ * static host array.  The call makes no cudaMalloc, cudaFree or other
+ * allocation and creates no stream or event.
+ *
+ * Limits: at most 1024 position masks (c_gk); the input's scratch need
+ * (about 64 bytes per window plus 4 (M+1) n^2 bytes) must fit in 64 MiB;
+ * plus the limits of gakco_gram.  Larger inputs return GAKCO_E_OVERFLOW
+ * with a message in `err` (caller buffer of `err_len` bytes, may be NULL).
+ *
+ * The first call on a device, with that device current, looks up the
+ * device address of the static array (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  Work is ordered on `stream` and
+ * the call returns after it completes.  Every call uses the same static
+ * arrays: calls that overlap on the GPU (other streams, other host threads)
+ * race and corrupt each other's results, so issue one at a time.
+ */
+int gakco_gram_device_noalloc(int sigma, int g, int k, const uint8_t *codes,
+                              const int64_t *offsets, int32_t n, int32_t *K,
+                              double *Khat, int32_t *Nm, void *stream,
+                              char *err, int err_len);
+
 #ifdef __cplusplus
 }
 #endif

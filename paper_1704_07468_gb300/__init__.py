@@ -19,7 +19,7 @@ import os
 
 import numpy as np
 
-__all__ = ["gakco_create", "Context", "GakcoError", "load_library",
+__all__ = ["gakco_create", "gakco_gram_device_noalloc", "Context", "GakcoError", "load_library",
            "library_path", "OPT", "STAT", "ERRORS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -79,6 +79,9 @@ def load_library(build_if_missing: bool = False):
         "gakco_gram_batch": ([p, i32, p, p, p, p, p, p], ctypes.c_int),
         "gakco_gram_device": ([p, p, p, i32, p, p, p, p], ctypes.c_int),
         "gakco_gram_batch_device": ([p, i32, p, p, p, p, p, p, p], ctypes.c_int),
+        "gakco_gram_device_noalloc": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, p, p, i32,
+                                       p, p, p, p, ctypes.c_char_p, ctypes.c_int],
+                                      ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -218,6 +221,26 @@ class Context:
             _ptr_array(Khat_ptrs), _ptr_array(Nm_ptrs),
             ctypes.c_void_p(stream) if stream else None)
         self._check(rc)
+
+
+def gakco_gram_device_noalloc(sigma, g, k, codes_ptr, offsets, K_ptr, Khat_ptr=None,
+                              Nm_ptr=None, stream=None):
+    """Gram kernel without any allocation (C: ``gakco_gram_device_noalloc``).
+
+    For callers that may not let the library allocate device memory (memory
+    owned by a framework's pool or budget, allocation-free request paths,
+    plug-ins handed their buffers).  Intermediate data lives in the
+    library's 64 MiB static device array; calls must not overlap on the GPU.
+    Pointers are device addresses (ints); ``offsets`` is a host int64 array.
+    """
+    lib = load_library()
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    err = ctypes.create_string_buffer(256)
+    rc = lib.gakco_gram_device_noalloc(int(sigma), int(g), int(k), codes_ptr,
+                                       offsets.ctypes.data, len(offsets) - 1, K_ptr,
+                                       Khat_ptr, Nm_ptr, stream, err, 256)
+    if rc != GAKCO_OK:
+        raise GakcoError(rc, err.value.decode())
 
 
 def gakco_create(sigma: int, g: int, k: int) -> Context:
