@@ -46,12 +46,14 @@ L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 SMEM_BANKS = 32              # shared-memory banks per SM (32-bit each)
 
 
-def make_workload(name, rank=0):
+def make_workload(name, rank=0, dna_sizes=None):
     """-> (description, sigma, g, k, list of (codes, offsets))."""
     off = 1000 * rank
     if name == "dna_large":
-        sets = synth.dna_large(seeds=tuple(s + off for s in (2, 3, 4, 5, 6)))
-        return ("DNA large-M batched: 5 datasets, N=500/1000/2000/3000/4000, "
+        sizes = tuple(dna_sizes) if dna_sizes else synth.DNA_LARGE_SIZES
+        seeds = tuple(s + off for s in (2, 3, 4, 5, 6))[:len(sizes)]
+        sets = synth.dna_large(seeds=seeds, sizes=sizes)
+        return (f"DNA large-M batched: {len(sizes)} datasets, N={'/'.join(map(str, sizes))}, "
                 "lengths U[100,300], GC 0.4, g=10 k=6 (M=4)", 4, 10, 6, sets)
     if name == "dna_toy":
         return ("DNA toy: N=200, length 100, uniform ACGT, g=7 k=5 (M=2)", 4, 7, 5,
@@ -159,7 +161,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if ws > 1 and rank != 0:
         return
-    desc, sigma, g, k, sets = make_workload(args.workload, 0)
+    desc, sigma, g, k, sets = make_workload(args.workload, 0, args.dna_sizes)
     import oracle
     oracle.build()
     threads = oracle.default_threads()
@@ -217,7 +219,7 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     lib_build.build()
-    desc, sigma, g, k, sets = make_workload(args.workload, rank)
+    desc, sigma, g, k, sets = make_workload(args.workload, rank, args.dna_sizes)
     ns = [len(o) - 1 for _, o in sets]
     entries = float(sum(n * n for n in ns))
 
@@ -395,6 +397,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-rows", type=int, default=64)
     ap.add_argument("--ref-rows", type=int, default=16)
+    ap.add_argument("--dna-sizes", type=lambda v: [int(t) for t in v.split(",")], default=None,
+                    help="subset of DNA dataset sizes (small cases for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -102,6 +102,7 @@ const char *gakco_last_error(const gakco_ctx *ctx);
 #define GAKCO_OPT_SMEM_COLS 7       /* cap on columns per accumulation tile (0 = auto) */
 #define GAKCO_OPT_FAIL_ALLOC_AFTER 8 /* fault injection: fail the Nth next device
                                         allocation (0 = off); host side only */
+#define GAKCO_OPT_GROUP_BYTES 9     /* entry-array bytes per accumulation mask group */
 int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 
 /*

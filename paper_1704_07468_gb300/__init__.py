@@ -34,7 +34,7 @@ ERRORS = {
 }
 OPT = {"engine": 1, "radix_bits": 2, "chunk_elems": 3, "graph": 4,
        "accum_threads": 5, "profile": 6, "smem_cols": 7,
-       "fail_alloc_after": 8}
+       "fail_alloc_after": 8, "group_bytes": 9}
 STAT = {"launches": 1, "mask_passes": 2, "device_bytes": 3,
         "graph_replay": 4, "pair_updates": 5, "entries_visited": 6,
         "windows_visited": 7}

@@ -66,9 +66,12 @@ struct DsInfo {
   int32_t* Nm;            // (M+1) x n x n mismatch profiles, or null
   double* Khat;           // n x n normalised kernel, or null
   double* rinv;           // n: 1 / sqrt(K(x, x)), 0 when K(x, x) = 0
+  uint32_t* C;            // (M+1) x n x n cumulative profiles (batched engine)
   uint64_t win0;          // first global window
   uint32_t n;
   uint32_t tile0;         // first 32x32 finishing tile of this dataset
+  uint32_t seq0;          // first global sequence
+  uint32_t pad;
 };
 
 // Error bits raised by kernels into the context's device status word.

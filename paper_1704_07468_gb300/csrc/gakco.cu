@@ -98,6 +98,7 @@ struct gakco_ctx {
   int profile = 0;
   int64_t smem_cols = 0;
   int64_t fail_alloc_after = 0;
+  int64_t group_bytes = (int64_t)64 << 20;
 
   std::string err;
   int device = 0;
@@ -108,7 +109,7 @@ struct gakco_ctx {
 
   DevBuf fullkey, win2seq, ewin, eseq, efe, keyA, keyB, valA, valB, hist, tcnt,
       segtot, estart, etseq, efid, fstart, tables, codes, outK, outKhat, outNm,
-      rinv, status, Cplain;
+      rinv, status, Cplain, Cacc;
   void* h_tables = nullptr;
   size_t h_tables_cap = 0;
   void* h_status = nullptr;
@@ -217,6 +218,7 @@ struct Plan {
   uint32_t ncols = 0;
   size_t acc_smem = 0;
   int acc_blocks = 0;
+  uint64_t c_elems = 0;
   std::vector<uint32_t> seg_ds;  // dataset of each segment
   bool want_nm = false, want_khat = false;
   // device table offsets
@@ -339,41 +341,58 @@ void plan_chunks(gakco_ctx* c, Plan& p, bool plain) {
   }
 }
 
-// Work items of the accumulation kernel: (dataset, row, c0, c1), most
-// expensive first.
+// Work items of the accumulation kernel: (dataset, level, first mask, mask
+// count, row, c0, c1).  The masks of a level are cut into groups whose
+// entry arrays (about 12 bytes per window per mask) fit `group_bytes`, so
+// the rows processed together share an L2-resident working set; items go
+// out group by group, most expensive rows first within a group.
 void plan_items(gakco_ctx* c, Plan& p) {
-  const size_t per_level = 4 * (size_t)(c->M + 1);
   size_t avail = c->smem_optin > 2048 ? c->smem_optin - 1024 : 0;
-  uint32_t ncols = (uint32_t)std::min<size_t>(avail / per_level, 65535);
+  uint32_t ncols = (uint32_t)std::min<size_t>(avail / 4, 65535);
   if (c->smem_cols > 0) ncols = std::min<uint32_t>(ncols, (uint32_t)c->smem_cols);
   ncols = std::max<uint32_t>(1, std::min<uint32_t>(ncols, std::max<uint32_t>(p.nmax, 1)));
   p.ncols = ncols;
-  p.acc_smem = per_level * ncols;
-  struct It {
+  p.acc_smem = 4 * (size_t)ncols;
+  std::vector<uint32_t> level_first(c->M + 2, 0);
+  for (uint32_t mu = 0; mu < c->masks.size(); ++mu) level_first[c->mask_level[mu] + 1] = mu + 1;
+  for (int m = 1; m <= c->M + 1; ++m) level_first[m] = std::max(level_first[m], level_first[m - 1]);
+  struct Row {
     double cost;
-    uint32_t d, x, c0, c1;
+    uint32_t x, c0, c1;
   };
-  std::vector<It> its;
+  p.items.clear();
   for (size_t d = 0; d < p.ds.size(); ++d) {
     const DsHost& D = p.ds[d];
+    if (D.n == 0) continue;
+    std::vector<Row> rows;
     for (int32_t x = 0; x < D.n; ++x) {
       const double W = (double)(D.woff[x + 1] - D.woff[x]);
       for (uint32_t t0 = 0; t0 < (uint32_t)D.n; t0 += ncols) {
         const uint32_t t1 = std::min<uint32_t>((uint32_t)D.n, t0 + ncols);
         if (t1 <= (uint32_t)x) continue;
         const uint32_t c0 = std::max<uint32_t>((uint32_t)x, t0);
-        its.push_back({W * (double)(t1 - c0) + 8.0 * W * c->masks.size() / 64.0 + (t1 - c0),
-                       (uint32_t)d, (uint32_t)x, c0, t1});
+        rows.push_back({W * (double)(t1 - c0) + W + (double)(t1 - c0), (uint32_t)x, c0, t1});
       }
     }
-  }
-  std::stable_sort(its.begin(), its.end(), [](const It& a, const It& b) { return a.cost > b.cost; });
-  p.items.resize(4 * its.size());
-  for (size_t i = 0; i < its.size(); ++i) {
-    p.items[4 * i] = its[i].d;
-    p.items[4 * i + 1] = its[i].x;
-    p.items[4 * i + 2] = its[i].c0;
-    p.items[4 * i + 3] = its[i].c1;
+    std::stable_sort(rows.begin(), rows.end(),
+                     [](const Row& a, const Row& b) { return a.cost > b.cost; });
+    // Rows without windows still need their (zero) row of C: they are
+    // covered by the memset; only rows with windows get items.
+    const double per_mask = 12.0 * (double)std::max<uint64_t>(D.G, 1);
+    const uint32_t gmax = (uint32_t)std::max(1.0, std::floor((double)c->group_bytes / per_mask));
+    for (int m = 0; m <= c->M; ++m) {
+      const uint32_t mf = level_first[m], mc = level_first[m + 1] - level_first[m];
+      const uint32_t ng = (mc + gmax - 1) / gmax;
+      for (uint32_t gi = 0; gi < ng; ++gi) {
+        const uint32_t a = mf + (uint32_t)((uint64_t)mc * gi / ng);
+        const uint32_t b = mf + (uint32_t)((uint64_t)mc * (gi + 1) / ng);
+        for (const Row& r : rows) {
+          if (D.woff[r.x + 1] == D.woff[r.x]) continue;
+          const uint32_t it[kItemWords] = {(uint32_t)d, (uint32_t)m, a, b - a, r.x, r.c0, r.c1, 0};
+          p.items.insert(p.items.end(), it, it + kItemWords);
+        }
+      }
+    }
   }
 }
 
@@ -426,6 +445,10 @@ int plan_memory_and_tables(gakco_ctx* c, Plan& p, bool plain) {
   ENSURE(rinv, nsum * 8);
   ENSURE(status, 128);
   if (plain) ENSURE(Cplain, (uint64_t)(c->M + 1) * p.nmax * p.nmax * 4);
+  uint64_t csum = 0;
+  for (auto& D : p.ds) csum += (uint64_t)(c->M + 1) * D.n * D.n;
+  p.c_elems = csum;
+  if (!plain) ENSURE(Cacc, csum * 4);
 
   Tables t;
   p.o_masks = t.add(c->masks.data(), c->masks.size() * sizeof(MaskDesc));
@@ -445,6 +468,7 @@ int plan_memory_and_tables(gakco_ctx* c, Plan& p, bool plain) {
   ENSURE(tables, t.buf.size());
   uint8_t* base = (uint8_t*)c->tables.p;
   double* rinv = (double*)c->rinv.p;
+  uint64_t cacc = 0;
   uint32_t ftile = 0;
   for (size_t d = 0; d < p.ds.size(); ++d) {
     DsHost& D = p.ds[d];
@@ -463,6 +487,9 @@ int plan_memory_and_tables(gakco_ctx* c, Plan& p, bool plain) {
     in.Khat = D.Khat;
     in.rinv = rinv;
     rinv += D.n;
+    in.C = plain ? nullptr : (uint32_t*)c->Cacc.p + cacc;
+    cacc += (uint64_t)(c->M + 1) * D.n * D.n;
+    in.seq0 = D.seq0;
     in.win0 = D.win0;
     in.n = (uint32_t)D.n;
     in.tile0 = ftile;
@@ -500,10 +527,8 @@ AccParams acc_params(gakco_ctx* c, const Plan& p, uint32_t* counter) {
   AccParams a{};
   a.ds = (const DsInfo*)(base + p.o_info);
   a.items = (const uint32_t*)(base + p.o_items);
-  a.nitems = (uint32_t)(p.items.size() / 4);
+  a.nitems = (uint32_t)(p.items.size() / kItemWords);
   a.counter = counter;
-  a.mask_level = (const uint32_t*)(base + p.o_level);
-  a.nmasks = (uint32_t)c->masks.size();
   a.M = (uint32_t)c->M;
   a.gtot = p.gtot;
   a.ewin = (const uint32_t*)c->ewin.p;
@@ -557,9 +582,14 @@ int enqueue_work(gakco_ctx* c, const Plan& p, bool plain) {
   if (!plain) {
     for (const Chunk& ch : p.chunks) enqueue_chunk(c, p, ch);
     AccParams a = acc_params(c, p, status + 8);
+    if (p.c_elems) cudaMemsetAsync(c->Cacc.p, 0, p.c_elems * 4, c->cs);
     {
       Bracket b(c, "accumulate", 1);
       launch_accum(a, c->accum_threads, p.acc_blocks, p.acc_smem, c->cs);
+    }
+    {
+      Bracket b(c, "diag", 1);
+      launch_diag((const DsInfo*)(base + p.o_info), (uint32_t)p.ds.size(), p.nseq, a, c->cs);
     }
   } else {
     AccParams a = acc_params(c, p, status + 8);
@@ -585,10 +615,14 @@ int enqueue_work(gakco_ctx* c, const Plan& p, bool plain) {
       launch_ie_combine(infos + d, (const uint32_t*)c->Cplain.p, (uint32_t)D.n, a, c->cs);
     }
   }
-  {
+  if (plain) {
     Bracket b(c, "finish", 1);
     launch_finish((const DsInfo*)(base + p.o_info), (uint32_t)p.ds.size(), p.ftiles, (uint32_t)c->M,
                   p.want_nm, p.want_khat, c->cs);
+  } else {
+    Bracket b(c, "combine", 1);
+    launch_combine((const DsInfo*)(base + p.o_info), (uint32_t)p.ds.size(), p.ftiles,
+                   acc_params(c, p, status + 8), p.want_nm, p.want_khat, c->cs);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
@@ -598,7 +632,7 @@ int enqueue_work(gakco_ctx* c, const Plan& p, bool plain) {
 uint64_t plan_key(gakco_ctx* c, const Plan& p, bool plain) {
   uint64_t h = 1469598103934665603ull;
   int64_t o[8] = {plain, c->radix_bits, c->chunk_elems, c->accum_threads, c->smem_cols,
-                  (int64_t)p.ds.size(), 0, 0};
+                  (int64_t)p.ds.size(), c->group_bytes, 0};
   h = fnv1a(h, o, sizeof o);
   for (const DsHost& D : p.ds) {
     const void* ptrs[4] = {D.codes, D.K, D.Khat, D.Nm};
@@ -856,7 +890,8 @@ void gakco_destroy(gakco_ctx* c) {
   DevBuf* bufs[] = {&c->fullkey, &c->win2seq, &c->ewin, &c->eseq, &c->efe, &c->keyA,
                     &c->keyB,    &c->valA,    &c->valB, &c->hist, &c->tcnt, &c->segtot,
                     &c->estart,  &c->etseq,   &c->efid, &c->fstart, &c->tables, &c->codes,
-                    &c->outK,    &c->outKhat, &c->outNm, &c->rinv, &c->status, &c->Cplain};
+                    &c->outK,    &c->outKhat, &c->outNm, &c->rinv, &c->status, &c->Cplain,
+                    &c->Cacc};
   for (DevBuf* b : bufs) release(*b);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -898,6 +933,10 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
       if (v < 0) return fail(c, GAKCO_E_INVALID, "column cap must be >= 0");
       c->smem_cols = v;
       break;
+    case GAKCO_OPT_GROUP_BYTES:
+      if (v < 1) return fail(c, GAKCO_E_INVALID, "group bytes must be >= 1");
+      c->group_bytes = v;
+      break;
     case GAKCO_OPT_FAIL_ALLOC_AFTER:
       if (v < 0) return fail(c, GAKCO_E_INVALID, "allocation countdown must be >= 0");
       c->fail_alloc_after = v;
@@ -922,7 +961,8 @@ int gakco_get_stat(const gakco_ctx* c, int key, double* v) {
       const DevBuf* bufs[] = {&c->fullkey, &c->win2seq, &c->ewin, &c->eseq, &c->efe, &c->keyA,
                               &c->keyB,    &c->valA,    &c->valB, &c->hist, &c->tcnt, &c->segtot,
                               &c->estart,  &c->etseq,   &c->efid, &c->fstart, &c->tables, &c->codes,
-                              &c->outK,    &c->outKhat, &c->outNm, &c->rinv, &c->status, &c->Cplain};
+                              &c->outK,    &c->outKhat, &c->outNm, &c->rinv, &c->status, &c->Cplain,
+                              &c->Cacc};
       double s = 0;
       for (const DevBuf* b : bufs) s += (double)b->cap;
       *v = s;

@@ -8,14 +8,15 @@
 // features held by several sequences touch off-diagonal entries (the paper
 // counts those, "> 1", at step 2).
 //
-// k_accum computes whole rows of C_0..C_M at once.  One block owns row x of
-// one dataset and keeps C_0(x, .) .. C_M(x, .) in shared memory; its warps
-// walk every mask, and for each entry (f, x, c_x) of the row they add
-// c_x * c_y for every entry (f, y, c_y) of the same feature with y >= x.
-// Entries of a feature are sorted by sequence, so y >= x is the tail of the
-// feature's entry range.  When the row is done the block applies Eq. 9 and
-// Eq. 7 elementwise and writes the upper triangle of K (and N_m).  The sum
-// over masks is thus formed on chip, and C_m never exists in global memory.
+// k_accum accumulates rows of C_m in shared memory.  A work item is one row
+// x of one dataset, one level m and a group of that level's masks; its
+// warps walk the group's masks over the windows of x, and for each entry
+// (f, x, c_x) of the row add c_x * c_y for every entry (f, y, c_y) of the
+// same feature with y >= x.  Entries of a feature are sorted by sequence,
+// so y >= x is the tail of the feature's entry range.  The row is then
+// added to the global C_m with coalesced reductions.  Items are handed out
+// group by group, so the rows being processed at any moment read the same
+// few masks' entry arrays, which stay in L2.
 #include <cstdint>
 
 #include "common.cuh"
@@ -66,101 +67,111 @@ __device__ __forceinline__ uint32_t ie_combine(const uint32_t* C, uint32_t M,
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads)
 k_accum(const AccParams p) {
-  extern __shared__ uint32_t acc[];   // (M + 1) x ncols
+  extern __shared__ uint32_t acc[];   // ncols counters of one row of C_m
   __shared__ uint32_t s_item;
   constexpr int kWarps = kThreads / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint32_t M = p.M;
-  const uint32_t NC = p.ncols;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_item = atomicAdd(p.counter, 1u);
     __syncthreads();
     const uint32_t it = s_item;
     if (it >= p.nitems) return;
-    const uint32_t d = p.items[4 * (uint64_t)it];
-    const uint32_t x = p.items[4 * (uint64_t)it + 1];
-    const uint32_t c0 = p.items[4 * (uint64_t)it + 2];
-    const uint32_t c1 = p.items[4 * (uint64_t)it + 3];
+    const uint32_t* I = p.items + (uint64_t)it * kItemWords;
+    const uint32_t d = I[0], lvl = I[1], mfirst = I[2], mcount = I[3];
+    const uint32_t x = I[4], c0 = I[5], c1 = I[6];
     const DsInfo ds = p.ds[d];
     const uint32_t width = c1 - c0;
-    for (uint32_t lv = 0; lv <= M; ++lv)
-      for (uint32_t i = threadIdx.x; i < width; i += kThreads) acc[lv * NC + i] = 0;
+    for (uint32_t i = threadIdx.x; i < width; i += kThreads) acc[i] = 0;
     __syncthreads();
     const uint32_t wbeg = ds.woff[x], wend = ds.woff[x + 1];
     const uint32_t gd = ds.woff[ds.n];  // windows of the dataset: bound of every entry index
-    uint32_t n_pairs = 0, n_ent = 0;    // work counters of this thread
     const bool lo_cut = c0 > x, hi_cut = c1 < ds.n;
-    for (uint32_t mu = w; mu < p.nmasks; mu += kWarps) {
+    const uint32_t nch = (wend - wbeg + 31) / 32;
+    uint32_t n_pairs = 0, n_ent = 0;    // work counters of this thread
+    for (uint32_t ch = w; ch < mcount * nch; ch += kWarps) {
+      const uint32_t mu = mfirst + ch / nch;
+      const uint32_t wi = wbeg + (ch % nch) * 32 + lane;
       const uint64_t pool = (uint64_t)mu * p.gtot + ds.win0;
       const uint32_t* __restrict__ ew = p.ewin + pool;
       const uint32_t* __restrict__ es = p.eseq + pool;
       const uint32_t* __restrict__ ef = p.efe + pool;
-      uint32_t* a = acc + p.mask_level[mu] * NC;
-      for (uint32_t w0 = wbeg; w0 < wend; w0 += 32) {
-        const uint32_t wi = w0 + lane;
-        uint32_t e = wi < wend ? ew[wi] : kNone;
-        uint32_t lo = 0, cnt = 0, c = 0;
-        if (e != kNone && (e >= gd || ef[e] > gd || ef[e] <= e)) {
+      uint32_t e = wi < wend ? ew[wi] : kNone;
+      uint32_t lo = 0, cnt = 0, c = 0;
+      if (e != kNone) {
+        const uint32_t hi0 = e < gd ? ef[e] : 0;
+        if (e >= gd || hi0 > gd || hi0 <= e) {
           atomicOr(p.status, kErrBadEntry);  // corrupt entry: skip it
           e = kNone;
-        }
-        if (e != kNone) {
+        } else {
           c = es[e] & 0xFFFFu;
-          uint32_t hi = ef[e];
+          uint32_t hi = hi0;
           lo = e;
           if (lo_cut) lo = lower_bound_seq(es, e, hi, c0);
           if (hi_cut) hi = lower_bound_seq(es, lo, hi, c1);
           cnt = hi - lo;
         }
-        // Long entry ranges: the whole warp walks one range at a time.
-        uint32_t longm = __ballot_sync(kFull, cnt >= kLong);
-        while (longm) {
-          const int L = __ffs(longm) - 1;
-          longm &= longm - 1;
-          const uint32_t lL = __shfl_sync(kFull, lo, L);
-          const uint32_t nL = __shfl_sync(kFull, cnt, L);
-          const uint32_t cL = __shfl_sync(kFull, c, L);
-          for (uint32_t q = lane; q < nL; q += 32) {
-            const uint32_t v = es[lL + q];
-            const uint32_t yy = (v >> 16) - c0;
+      }
+      n_pairs += cnt;
+      n_ent += e != kNone;
+      // Long entry ranges: the whole warp walks one range at a time, four
+      // loads in flight per lane.
+      uint32_t longm = __ballot_sync(kFull, cnt >= kLong);
+      while (longm) {
+        const int L = __ffs(longm) - 1;
+        longm &= longm - 1;
+        const uint32_t lL = __shfl_sync(kFull, lo, L);
+        const uint32_t nL = __shfl_sync(kFull, cnt, L);
+        const uint32_t cL = __shfl_sync(kFull, c, L);
+        for (uint32_t q = lane; q < nL; q += 128) {
+          uint32_t v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = q + 32 * u < nL ? es[lL + q + 32 * u] : kNone;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (v[u] == kNone) continue;
+            const uint32_t yy = (v[u] >> 16) - c0;
             if (yy < width)
-              atomicAdd(&a[yy], cL * (v & 0xFFFFu));
+              atomicAdd(&acc[yy], cL * (v[u] & 0xFFFFu));
             else
               atomicOr(p.status, kErrBadEntry);
           }
         }
-        n_pairs += cnt;
-        n_ent += e != kNone;
-        if (cnt >= kLong) cnt = 0;
-        // Short ranges: expand all pairs of the 32 lanes, 32 at a time.
-        uint32_t incl = cnt;
+      }
+      if (cnt >= kLong) cnt = 0;
+      // Short ranges: expand all pairs of the 32 lanes, 64 at a time.
+      uint32_t incl = cnt;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t t = __shfl_up_sync(kFull, incl, o);
-          if (lane >= o) incl += t;
-        }
-        const uint32_t total = __shfl_sync(kFull, incl, 31);
-        const uint32_t excl = incl - cnt;
-        for (uint32_t p0 = 0; p0 < total; p0 += 32) {
-          const uint32_t pp = p0 + lane;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const uint32_t total = __shfl_sync(kFull, incl, 31);
+      const uint32_t excl = incl - cnt;
+      for (uint32_t p0 = 0; p0 < total; p0 += 64) {
+        uint32_t v[2], cw[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const uint32_t pp = p0 + 32 * u + lane;
           uint32_t o = 0;  // owner lane: first lane whose inclusive count > pp
 #pragma unroll
           for (int step = 16; step >= 1; step >>= 1) {
-            const uint32_t v = __shfl_sync(kFull, incl, o + step - 1);
-            if (v <= pp) o += step;
+            const uint32_t t = __shfl_sync(kFull, incl, o + step - 1);
+            if (t <= pp) o += step;
           }
           const uint32_t lo_o = __shfl_sync(kFull, lo, o);
           const uint32_t ex_o = __shfl_sync(kFull, excl, o);
-          const uint32_t c_o = __shfl_sync(kFull, c, o);
-          if (pp < total) {
-            const uint32_t v = es[lo_o + (pp - ex_o)];
-            const uint32_t yy = (v >> 16) - c0;
-            if (yy < width)
-              atomicAdd(&a[yy], c_o * (v & 0xFFFFu));
-            else
-              atomicOr(p.status, kErrBadEntry);
-          }
+          cw[u] = __shfl_sync(kFull, c, o);
+          v[u] = pp < total ? es[lo_o + (pp - ex_o)] : kNone;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (v[u] == kNone) continue;
+          const uint32_t yy = (v[u] >> 16) - c0;
+          if (yy < width)
+            atomicAdd(&acc[yy], cw[u] * (v[u] & 0xFFFFu));
+          else
+            atomicOr(p.status, kErrBadEntry);
         }
       }
     }
@@ -173,31 +184,128 @@ k_accum(const AccParams p) {
       if (lane == 0) {
         atomicAdd(&p.work[0], (unsigned long long)n_pairs);
         atomicAdd(&p.work[1], (unsigned long long)n_ent);
-        if (w == 0) atomicAdd(&p.work[2], (unsigned long long)(wend - wbeg) * p.nmasks);
+        if (w == 0) atomicAdd(&p.work[2], (unsigned long long)(wend - wbeg) * mcount);
       }
     }
     __syncthreads();
-    // Row epilogue: Eq. 9, Eq. 7 and the identity K == C_M.
-    const uint64_t nn = (uint64_t)ds.n * ds.n;
-    for (uint32_t y = c0 + threadIdx.x; y < c1; y += kThreads) {
-      uint32_t C[kMaxLevels], N[kMaxLevels];
+    // Add the row into the global C_m (other groups of the level add to the
+    // same row, possibly at the same time).
+    uint32_t* __restrict__ crow = ds.C + ((uint64_t)lvl * ds.n + x) * ds.n + c0;
+    for (uint32_t i = threadIdx.x; i < width; i += kThreads) {
+      const uint32_t v = acc[i];
+      if (v) atomicAdd(&crow[i], v);
+    }
+  }
+}
+
+// K(x, x) from the diagonal of C_0..C_M and r_x = 1 / sqrt(K(x, x)) (0
+// when K(x, x) = 0) for normalisation.
+__global__ void __launch_bounds__(256)
+k_diag(const DsInfo* __restrict__ dsv, uint32_t nds, uint32_t nseq, const AccParams p) {
+  const uint32_t gs = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gs >= nseq) return;
+  uint32_t d = 0;
+  while (d + 1 < nds && dsv[d + 1].seq0 <= gs) ++d;
+  const DsInfo D = dsv[d];
+  const uint32_t x = gs - D.seq0;
+  const uint64_t nn = (uint64_t)D.n * D.n;
+  const uint64_t o = (uint64_t)x * D.n + x;
+  uint32_t C[kMaxLevels], N[kMaxLevels];
 #pragma unroll
-      for (int m = 0; m < kMaxLevels; ++m)
-        C[m] = (uint32_t)m <= M ? acc[m * NC + (y - c0)] : 0u;
-      const uint32_t K = ie_combine(C, M, p.ie, p.h, N);
+  for (int m = 0; m < kMaxLevels; ++m) C[m] = (uint32_t)m <= p.M ? D.C[m * nn + o] : 0u;
+  const uint32_t K = ie_combine(C, p.M, p.ie, p.h, N);
+  D.rinv[x] = K ? 1.0 / sqrt((double)K) : 0.0;
+}
+
+// Eq. 9 and Eq. 7 on the upper triangle of C, tile by tile, writing K, N_m
+// and Khat at (x, y) and, through a shared-memory transpose, at (y, x).
+// Khat(x, y) = (K * r_x) * r_y (a few ulp from K / sqrt(Kxx Kyy)), exactly
+// 1 on a nonzero diagonal, 0 where a diagonal is 0.  Lower tiles exit.
+__global__ void __launch_bounds__(256)
+k_combine(const DsInfo* __restrict__ dsv, uint32_t nds, const AccParams p, int want_nm,
+          int want_khat) {
+  __shared__ int32_t ti[32][33];
+  __shared__ double td[32][33];
+  const uint32_t b = blockIdx.x;
+  uint32_t d = 0;
+  while (d + 1 < nds && dsv[d + 1].tile0 <= b) ++d;
+  const DsInfo D = dsv[d];
+  const uint32_t n = D.n, nt = (n + 31) / 32;
+  const uint32_t t = b - D.tile0;
+  const uint32_t I = t / nt, J = t % nt;
+  if (I > J) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const uint64_t nn = (uint64_t)n * n;
+  const uint32_t M = p.M;
+  // Four elements per thread: rows I*32 + ty + 8 r, column J*32 + tx.
+  uint32_t Nv[4][kMaxLevels];
+  uint32_t Kv[4];
+  bool up[4];
+  const uint32_t col = J * 32 + tx;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const uint32_t row = I * 32 + ty + 8 * r;
+    up[r] = row < n && col < n && row <= col;
+    Kv[r] = 0;
+#pragma unroll
+    for (int m = 0; m < kMaxLevels; ++m) Nv[r][m] = 0;
+    if (up[r]) {
+      uint32_t C[kMaxLevels];
+      const uint64_t o = (uint64_t)row * n + col;
+#pragma unroll
+      for (int m = 0; m < kMaxLevels; ++m) C[m] = (uint32_t)m <= M ? D.C[m * nn + o] : 0u;
+      Kv[r] = ie_combine(C, M, p.ie, p.h, Nv[r]);
       uint32_t CM = 0;
 #pragma unroll
       for (int m = 0; m < kMaxLevels; ++m)
         if ((uint32_t)m == M) CM = C[m];
-      if (K != CM) atomicOr(p.status, kErrKneCM);
-      const uint64_t o = (uint64_t)x * ds.n + y;
-      ds.K[o] = (int32_t)K;
-      if (ds.Nm) {
+      if (Kv[r] != CM) atomicOr(p.status, kErrKneCM);
+    }
+  }
+  // Plane 0 is K, planes 1..M+1 are N_0..N_M: upper write, then the
+  // mirrored lower write.
+  const int nplanes = 1 + ((want_nm && D.Nm) ? (int)M + 1 : 0);
+  for (int pl = 0; pl < nplanes; ++pl) {
+    int32_t* X = pl == 0 ? D.K : D.Nm + (uint64_t)(pl - 1) * nn;
 #pragma unroll
-        for (int m = 0; m < kMaxLevels; ++m)
-          if ((uint32_t)m <= M) ds.Nm[(uint64_t)m * nn + o] = (int32_t)N[m];
+    for (int r = 0; r < 4; ++r) {
+      uint32_t v = Kv[r];
+#pragma unroll
+      for (int m = 0; m < kMaxLevels; ++m)
+        if (m == pl - 1) v = Nv[r][m];
+      const uint32_t row = I * 32 + ty + 8 * r;
+      if (up[r]) X[(uint64_t)row * n + col] = (int32_t)v;
+      ti[ty + 8 * r][tx] = (int32_t)v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      // Output (J*32 + ty + 8r, I*32 + tx) mirrors source (I*32 + tx, J*32 + ty + 8r).
+      const uint32_t orow = J * 32 + ty + 8 * r, ocol = I * 32 + tx;
+      if (orow < n && ocol < n && ocol < orow) X[(uint64_t)orow * n + ocol] = ti[tx][ty + 8 * r];
+    }
+    __syncthreads();
+  }
+  if (want_khat && D.Khat) {
+    const double rc = col < n ? D.rinv[col] : 0.0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const uint32_t row = I * 32 + ty + 8 * r;
+      double v = 0.0;
+      if (up[r]) {
+        if (row == col)
+          v = D.rinv[row] > 0.0 ? 1.0 : 0.0;
+        else
+          v = ((double)Kv[r] * D.rinv[row]) * rc;
+        D.Khat[(uint64_t)row * n + col] = v;
       }
-      if (y == x) ds.rinv[x] = K ? 1.0 / sqrt((double)K) : 0.0;
+      td[ty + 8 * r][tx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const uint32_t orow = J * 32 + ty + 8 * r, ocol = I * 32 + tx;
+      if (orow < n && ocol < n && ocol < orow) D.Khat[(uint64_t)orow * n + ocol] = td[tx][ty + 8 * r];
     }
   }
 }
@@ -353,6 +461,18 @@ void launch_finish(const DsInfo* d_ds, uint32_t nds, uint32_t ntiles, uint32_t M
                    bool want_nm, bool want_khat, cudaStream_t st) {
   if (ntiles == 0) return;
   k_finish<<<ntiles, 256, 0, st>>>(d_ds, nds, M, want_nm ? 1 : 0, want_khat ? 1 : 0);
+}
+
+void launch_diag(const DsInfo* d_ds, uint32_t nds, uint32_t nseq_total, const AccParams& coef,
+                 cudaStream_t st) {
+  if (nseq_total == 0) return;
+  k_diag<<<(nseq_total + 255) / 256, 256, 0, st>>>(d_ds, nds, nseq_total, coef);
+}
+
+void launch_combine(const DsInfo* d_ds, uint32_t nds, uint32_t ntiles, const AccParams& coef,
+                    bool want_nm, bool want_khat, cudaStream_t st) {
+  if (ntiles == 0) return;
+  k_combine<<<ntiles, 256, 0, st>>>(d_ds, nds, coef, want_nm ? 1 : 0, want_khat ? 1 : 0);
 }
 
 void launch_pairs_global(const uint32_t* segtot_E, const uint32_t* eseq,

@@ -47,22 +47,24 @@ void launch_rle(bool wide, const SegDesc* segs, uint32_t nsegs,
 // k_accum.cu ------------------------------------------------------------
 struct AccParams {
   const DsInfo* ds;
-  const uint32_t* items;      // 4 x u32 per item: dataset, row, c0, c1
+  const uint32_t* items;      // kItemWords x u32 per item, see gakco.cu
   uint32_t nitems;
   uint32_t* counter;
-  const uint32_t* mask_level;
-  uint32_t nmasks;
   uint32_t M;
   uint64_t gtot;
   const uint32_t* ewin;
   const uint32_t* eseq;
   const uint32_t* efe;
-  uint32_t ncols;             // columns held in shared memory per level
+  uint32_t ncols;             // columns held in shared memory
   uint32_t* status;
   unsigned long long* work;   // [0] pair updates, [1] entries visited, [2] windows visited
   uint32_t h[kMaxLevels];
   uint32_t ie[kMaxLevels][kMaxLevels];
 };
+
+// Accumulation work item: dataset, level, first mask, mask count, row,
+// first column, end column.
+constexpr int kItemWords = 8;
 
 int accum_max_threads();
 void launch_accum(const AccParams& p, int threads, int blocks,
@@ -71,6 +73,15 @@ int accum_blocks_per_sm(int threads, size_t smem);
 
 void launch_finish(const DsInfo* d_ds, uint32_t nds, uint32_t ntiles,
                    uint32_t M, bool want_nm, bool want_khat, cudaStream_t st);
+
+// Batched engine tail: K(x, x) and 1/sqrt(K(x, x)) from the diagonal of
+// C_0..C_M, then Eq. 9 / Eq. 7 over the upper triangle of C with the
+// mirrored K, N_m and Khat written in one pass.
+void launch_diag(const DsInfo* d_ds, uint32_t nds, uint32_t nseq_total,
+                 const AccParams& coef, cudaStream_t st);
+void launch_combine(const DsInfo* d_ds, uint32_t nds, uint32_t ntiles,
+                    const AccParams& coef, bool want_nm, bool want_khat,
+                    cudaStream_t st);
 
 // Plain per-mask path (Alg. 1 as written: countAndUpdate straight into the
 // global C_m with atomics, then inclusion-exclusion).

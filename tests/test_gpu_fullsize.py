@@ -102,7 +102,11 @@ def test_protein_full_size_and_plain_engine_agree():
     _check_rows(out, codes, off, 8, 4, _sample_rows(len(off) - 1, 8, 7), nm=False)
     plain = _device_batch(20, 8, 4, [(codes, off)], engine=1)[0]
     np.testing.assert_array_equal(plain["K"], out["K"])
-    np.testing.assert_array_equal(plain["Khat"], out["Khat"])
+    # Both engines normalise as (K * r_x) * r_y, but the batched one mirrors
+    # the upper value (exactly symmetric) while the plain one multiplies the
+    # lower triangle's factors in the other order: equal within rounding.
+    assert np.all(np.abs(plain["Khat"] - out["Khat"]) <= KHAT_RTOL * np.abs(out["Khat"]) + 1e-300)
+    assert np.array_equal(out["Khat"], out["Khat"].T)
 
 
 def test_text_full_size():
