@@ -348,11 +348,11 @@ void plan_chunks(gakco_ctx* c, Plan& p, bool plain) {
 // out group by group, most expensive rows first within a group.
 void plan_items(gakco_ctx* c, Plan& p) {
   size_t avail = c->smem_optin > 2048 ? c->smem_optin - 1024 : 0;
-  uint32_t ncols = (uint32_t)std::min<size_t>(avail / 4, 65535);
+  uint32_t ncols = (uint32_t)std::min<size_t>(avail / 4 - 1, 65535);
   if (c->smem_cols > 0) ncols = std::min<uint32_t>(ncols, (uint32_t)c->smem_cols);
   ncols = std::max<uint32_t>(1, std::min<uint32_t>(ncols, std::max<uint32_t>(p.nmax, 1)));
   p.ncols = ncols;
-  p.acc_smem = 4 * (size_t)ncols;
+  p.acc_smem = 4 * ((size_t)ncols + 1);  // + the trash slot
   std::vector<uint32_t> level_first(c->M + 2, 0);
   for (uint32_t mu = 0; mu < c->masks.size(); ++mu) level_first[c->mask_level[mu] + 1] = mu + 1;
   for (int m = 1; m <= c->M + 1; ++m) level_first[m] = std::max(level_first[m], level_first[m - 1]);
@@ -548,10 +548,10 @@ void enqueue_chunk(gakco_ctx* c, const Plan& p, const Chunk& ch) {
   const SegDesc* segs = (const SegDesc*)(base + p.o_segs) + ch.seg_first;
   const uint32_t* tseg = (const uint32_t*)(base + p.o_tiles) + ch.tile_first;
   const MaskDesc* masks = (const MaskDesc*)(base + p.o_masks);
-  void* kin = nullptr;
-  uint32_t* vin = nullptr;
   void* kbuf[2] = {c->keyA.p, c->keyB.p};
   uint32_t* vbuf[2] = {(uint32_t*)c->valA.p, (uint32_t*)c->valB.p};
+  void* kin = kbuf[1];  // the first pass extracts the masked keys here
+  uint32_t* vin = nullptr;
   int cur = 0;
   for (size_t q = 0; q < ch.passes.size(); ++q) {
     Bracket b(c, "sort_pass", 3);

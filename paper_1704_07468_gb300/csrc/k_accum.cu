@@ -67,7 +67,7 @@ __device__ __forceinline__ uint32_t ie_combine(const uint32_t* C, uint32_t M,
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads)
 k_accum(const AccParams p) {
-  extern __shared__ uint32_t acc[];   // ncols counters of one row of C_m
+  extern __shared__ uint32_t acc[];   // ncols counters of one row of C_m + a trash slot
   __shared__ uint32_t s_item;
   constexpr int kWarps = kThreads / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -82,7 +82,7 @@ k_accum(const AccParams p) {
     const uint32_t x = I[4], c0 = I[5], c1 = I[6];
     const DsInfo ds = p.ds[d];
     const uint32_t width = c1 - c0;
-    for (uint32_t i = threadIdx.x; i < width; i += kThreads) acc[i] = 0;
+    for (uint32_t i = threadIdx.x; i <= width; i += kThreads) acc[i] = 0;
     __syncthreads();
     const uint32_t wbeg = ds.woff[x], wend = ds.woff[x + 1];
     const uint32_t gd = ds.woff[ds.n];  // windows of the dataset: bound of every entry index
@@ -115,7 +115,8 @@ k_accum(const AccParams p) {
       n_pairs += cnt;
       n_ent += e != kNone;
       // Long entry ranges: the whole warp walks one range at a time, four
-      // loads in flight per lane.
+      // loads in flight per lane.  Column indices are clamped to the trash
+      // slot acc[width]; anything landing there is reported after the item.
       uint32_t longm = __ballot_sync(kFull, cnt >= kLong);
       while (longm) {
         const int L = __ffs(longm) - 1;
@@ -123,19 +124,14 @@ k_accum(const AccParams p) {
         const uint32_t lL = __shfl_sync(kFull, lo, L);
         const uint32_t nL = __shfl_sync(kFull, cnt, L);
         const uint32_t cL = __shfl_sync(kFull, c, L);
+        const uint32_t* __restrict__ src = es + lL;
         for (uint32_t q = lane; q < nL; q += 128) {
           uint32_t v[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) v[u] = q + 32 * u < nL ? es[lL + q + 32 * u] : kNone;
+          for (int u = 0; u < 4; ++u) v[u] = q + 32 * u < nL ? src[q + 32 * u] : 0u;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (v[u] == kNone) continue;
-            const uint32_t yy = (v[u] >> 16) - c0;
-            if (yy < width)
-              atomicAdd(&acc[yy], cL * (v[u] & 0xFFFFu));
-            else
-              atomicOr(p.status, kErrBadEntry);
-          }
+          for (int u = 0; u < 4; ++u)
+            if (q + 32 * u < nL) atomicAdd(&acc[min((v[u] >> 16) - c0, width)], cL * (v[u] & 0xFFFFu));
         }
       }
       if (cnt >= kLong) cnt = 0;
@@ -165,14 +161,8 @@ k_accum(const AccParams p) {
           v[u] = pp < total ? es[lo_o + (pp - ex_o)] : kNone;
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          if (v[u] == kNone) continue;
-          const uint32_t yy = (v[u] >> 16) - c0;
-          if (yy < width)
-            atomicAdd(&acc[yy], cw[u] * (v[u] & 0xFFFFu));
-          else
-            atomicOr(p.status, kErrBadEntry);
-        }
+        for (int u = 0; u < 2; ++u)
+          if (v[u] != kNone) atomicAdd(&acc[min((v[u] >> 16) - c0, width)], cw[u] * (v[u] & 0xFFFFu));
       }
     }
     if (p.work) {
@@ -188,6 +178,7 @@ k_accum(const AccParams p) {
       }
     }
     __syncthreads();
+    if (threadIdx.x == 0 && acc[width] != 0) atomicOr(p.status, kErrBadEntry);
     // Add the row into the global C_m (other groups of the level add to the
     // same row, possibly at the same time).
     uint32_t* __restrict__ crow = ds.C + ((uint64_t)lvl * ds.n + x) * ds.n + c0;

@@ -88,22 +88,44 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v,
 
 // ------------------------------------------------------------- radix sort --
 
-template <typename KeyT, bool kFirst>
-__device__ __forceinline__ KeyT load_key(const SegDesc& sd, uint64_t i,
-                                         const MaskDesc& md,
-                                         const uint64_t* __restrict__ fullkey,
-                                         const KeyT* __restrict__ kin) {
-  if (kFirst) return (KeyT)masked_key(fullkey[sd.win0 + i], md);
-  return kin[sd.base + i];
+// Masked key with the mask's runs held in registers (up to kRegRuns runs,
+// i.e. M <= kRegRuns - 1 deleted positions; longer masks take the loop).
+constexpr int kRegRuns = 6;
+
+struct MaskRegs {
+  uint32_t sr[kRegRuns], sl[kRegRuns];
+  uint64_t mk[kRegRuns];
+  bool fits;
+};
+
+__device__ __forceinline__ void mask_regs(const MaskDesc& md, MaskRegs& r) {
+  r.fits = md.nruns <= (uint32_t)kRegRuns;
+#pragma unroll
+  for (int i = 0; i < kRegRuns; ++i) {
+    const bool on = (uint32_t)i < md.nruns;
+    r.sr[i] = on ? md.sr[i] : 0u;
+    r.sl[i] = on ? md.sl[i] : 0u;
+    r.mk[i] = on ? md.msk[i] : 0ull;
+  }
 }
 
-// Per-tile digit counts: hist[seg.hist + digit * ntiles + tile].
+__device__ __forceinline__ uint64_t masked_key_r(uint64_t full, const MaskRegs& r,
+                                                 const MaskDesc& md) {
+  if (!r.fits) return masked_key(full, md);
+  uint64_t k = 0;
+#pragma unroll
+  for (int i = 0; i < kRegRuns; ++i) k |= ((full >> r.sr[i]) & r.mk[i]) << r.sl[i];
+  return k;
+}
+
+// Per-tile digit counts: hist[seg.hist + digit * ntiles + tile].  The first
+// pass also cuts the masked keys out of the full g-mer keys and stores them
+// in `kx`, which that pass's scatter then reads.
 template <typename KeyT, bool kFirst>
 __global__ void __launch_bounds__(kSortThreads)
 k_upsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg,
           const MaskDesc* __restrict__ masks, const uint64_t* __restrict__ fullkey,
-          const KeyT* __restrict__ kin, uint32_t* __restrict__ hist, int shift,
-          int rbits) {
+          KeyT* __restrict__ kx, uint32_t* __restrict__ hist, int shift, int rbits) {
   extern __shared__ uint32_t sh[];
   __shared__ MaskDesc md;
   const uint32_t t = blockIdx.x;
@@ -113,10 +135,18 @@ k_upsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_se
   if (kFirst && threadIdx.x == 0) md = masks[sd.mask];
   for (uint32_t i = threadIdx.x; i < radix; i += blockDim.x) sh[i] = 0;
   __syncthreads();
+  MaskRegs mr;
+  if (kFirst) mask_regs(md, mr);
   const uint64_t beg = (uint64_t)lt * kTile;
   const uint32_t cnt = (uint32_t)min((uint64_t)kTile, sd.G - beg);
   for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-    KeyT key = load_key<KeyT, kFirst>(sd, beg + i, md, fullkey, kin);
+    KeyT key;
+    if (kFirst) {
+      key = (KeyT)masked_key_r(fullkey[sd.win0 + beg + i], mr, md);
+      kx[sd.base + beg + i] = key;
+    } else {
+      key = kx[sd.base + beg + i];
+    }
     atomicAdd(&sh[(uint32_t)(key >> shift) & (radix - 1)], 1u);
   }
   __syncthreads();
@@ -153,27 +183,36 @@ k_seg_scan(const SegDesc* __restrict__ segs, uint32_t* __restrict__ hist,
   }
 }
 
-// Stable scatter.  Warp w of the block owns elements
-// [w*32*IPT, (w+1)*32*IPT) of the tile and visits them as j*32 + lane, so
-// the visiting order is the element order; peers with the same digit are
-// ranked with match.any, and running per-warp digit counts carry the rank
-// across j.
+// Shared-memory footprint of the scatter kernel for a digit width.
+__host__ __device__ constexpr size_t downsweep_smem(int rbits, int key_bytes) {
+  return ((size_t)(kWarps + 2) << rbits) * 4 + (size_t)kTile * (key_bytes + 4);
+}
+
+// Stable scatter of one tile.  Warp w owns elements [w*32*IPT, (w+1)*32*IPT)
+// and visits them as j*32 + lane, so the visiting order is the element
+// order.  Elements with the same digit are ranked with match.any: the
+// group's leader reserves slots of the warp's running count for the digit
+// with an atomic add, and the shuffle of its result is the convergence
+// point that orders consecutive items.  The tile is then laid out in digit
+// order in shared memory and written out with consecutive threads on
+// consecutive addresses of each digit's run.
 template <typename KeyT, bool kFirst>
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 2)
 k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg,
-            const MaskDesc* __restrict__ masks, const uint64_t* __restrict__ fullkey,
             const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin,
             KeyT* __restrict__ kout, uint32_t* __restrict__ vout,
             const uint32_t* __restrict__ hist, int shift, int rbits) {
-  extern __shared__ uint32_t sh[];
-  __shared__ MaskDesc md;
+  extern __shared__ __align__(16) uint32_t sh[];
+  __shared__ uint32_t sw[kWarps + 1];
   const uint32_t radix = 1u << rbits;
-  uint32_t* wc = sh;                   // kWarps x radix running counts
-  uint32_t* gb = sh + kWarps * radix;  // radix global bases of this tile
+  uint32_t* wc = sh;                     // kWarps x radix running counts
+  uint32_t* gb = sh + kWarps * radix;    // global base of each digit in this tile
+  uint32_t* ts = gb + radix;             // tile-local start of each digit
+  KeyT* skey = (KeyT*)(ts + radix);      // tile in digit order
+  uint32_t* sval = (uint32_t*)(skey + kTile);
   const uint32_t t = blockIdx.x;
   const SegDesc sd = segs[tile_seg[t]];
   const uint32_t lt = t - sd.tile0;
-  if (kFirst && threadIdx.x == 0) md = masks[sd.mask];
   for (uint32_t i = threadIdx.x; i < kWarps * radix; i += blockDim.x) wc[i] = 0;
   for (uint32_t i = threadIdx.x; i < radix; i += blockDim.x)
     gb[i] = hist[sd.hist + (uint64_t)i * sd.ntiles + lt];
@@ -188,33 +227,47 @@ k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
 #pragma unroll
   for (int j = 0; j < kSortIpt; ++j) {
     const uint32_t idx = (uint32_t)w * 32 * kSortIpt + j * 32 + lane;
+    keys[j] = idx < cnt ? kin[sd.base + beg + idx] : (KeyT)0;
+    vals[j] = idx < cnt ? (kFirst ? (uint32_t)(beg + idx) : vin[sd.base + beg + idx]) : 0u;
+  }
+#pragma unroll
+  for (int j = 0; j < kSortIpt; ++j) {
+    const uint32_t idx = (uint32_t)w * 32 * kSortIpt + j * 32 + lane;
     const bool valid = idx < cnt;
-    KeyT key = 0;
-    uint32_t val = 0;
-    if (valid) {
-      key = load_key<KeyT, kFirst>(sd, beg + idx, md, fullkey, kin);
-      val = kFirst ? (uint32_t)(beg + idx) : vin[sd.base + beg + idx];
-    }
-    const uint32_t dg = valid ? ((uint32_t)(key >> shift) & (radix - 1)) : radix;
+    const uint32_t dg = valid ? ((uint32_t)(keys[j] >> shift) & (radix - 1)) : radix;
     const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-    const uint32_t rank = __popc(peers & lt_mask);
-    const uint32_t base = valid ? wc[w * radix + dg] : 0;
-    __syncwarp();
-    if (valid && rank == 0) wc[w * radix + dg] = base + __popc(peers);
-    __syncwarp();
-    keys[j] = key;
-    vals[j] = val;
-    rk[j] = base + rank;
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(&wc[w * radix + dg], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    rk[j] = base + __popc(peers & lt_mask);
   }
   __syncthreads();
-  for (uint32_t dg = threadIdx.x; dg < radix; dg += blockDim.x) {
+  // Per digit: exclusive prefix over warps, and the digit's tile total.
+  const uint32_t per = (radix + kSortThreads - 1) / kSortThreads;
+  const uint32_t d0 = threadIdx.x * per;
+  uint32_t mysum = 0;
+  for (uint32_t q = 0; q < per; ++q) {
+    const uint32_t dg = d0 + q;
+    if (dg >= radix) break;
     uint32_t run = 0;
 #pragma unroll
     for (int ww = 0; ww < kWarps; ++ww) {
-      uint32_t c = wc[ww * radix + dg];
+      const uint32_t c = wc[ww * radix + dg];
       wc[ww * radix + dg] = run;
       run += c;
     }
+    ts[dg] = run;
+    mysum += run;
+  }
+  // Tile-local digit starts: exclusive scan of the totals.
+  uint32_t pre = block_excl_scan(mysum, sw, nullptr);
+  for (uint32_t q = 0; q < per; ++q) {
+    const uint32_t dg = d0 + q;
+    if (dg >= radix) break;
+    const uint32_t c = ts[dg];
+    ts[dg] = pre;
+    pre += c;
   }
   __syncthreads();
 #pragma unroll
@@ -222,33 +275,74 @@ k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
     const uint32_t idx = (uint32_t)w * 32 * kSortIpt + j * 32 + lane;
     if (idx < cnt) {
       const uint32_t dg = (uint32_t)(keys[j] >> shift) & (radix - 1);
-      const uint64_t pos = sd.base + gb[dg] + wc[w * radix + dg] + rk[j];
-      kout[pos] = keys[j];
-      vout[pos] = vals[j];
+      const uint32_t lpos = ts[dg] + wc[w * radix + dg] + rk[j];
+      skey[lpos] = keys[j];
+      sval[lpos] = vals[j];
     }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const KeyT k = skey[i];
+    const uint32_t dg = (uint32_t)(k >> shift) & (radix - 1);
+    const uint64_t pos = sd.base + gb[dg] + (i - ts[dg]);
+    kout[pos] = k;
+    vout[pos] = sval[i];
   }
 }
 
 // ------------------------------------------------------------ run-length --
 
-// Flags of sorted element i: a new entry starts where the (key, sequence)
-// pair changes, a new feature where the key changes.
+// Loads the elements a warp owns in a tile (element w*32*IPT + j*32 + lane)
+// with their sequence ids, and flags: a new entry starts where the (key,
+// sequence) pair changes, a new feature where the key changes.  The
+// predecessor comes from the neighbouring lane by shuffle; only the warp's
+// first element reads its predecessor from memory.
 template <typename KeyT>
-__device__ __forceinline__ void rle_flags(const SegDesc& sd, uint32_t i,
-                                          const KeyT* __restrict__ keys,
-                                          const uint32_t* __restrict__ vals,
-                                          const uint32_t* __restrict__ win2seq,
-                                          uint32_t& seq, bool& ne, bool& nf) {
-  const KeyT k = keys[sd.base + i];
-  seq = win2seq[sd.win0 + vals[sd.base + i]];
-  if (i == 0) {
-    ne = nf = true;
-    return;
+__device__ __forceinline__ void rle_load_flags(const SegDesc& sd, uint64_t beg, uint32_t cnt,
+                                               int w, int lane,
+                                               const KeyT* __restrict__ keys,
+                                               const uint32_t* __restrict__ vals,
+                                               const uint32_t* __restrict__ win2seq,
+                                               uint32_t (&vv)[kSortIpt], uint32_t (&sq)[kSortIpt],
+                                               uint32_t& ne_bits, uint32_t& nf_bits) {
+  // Predecessor of the warp's first element.
+  const uint64_t first = beg + (uint64_t)w * 32 * kSortIpt;
+  KeyT k_prev = 0;
+  uint32_t s_prev = kNone;
+  if (lane == 0 && first > 0 && first - beg < cnt) {
+    k_prev = keys[sd.base + first - 1];
+    s_prev = win2seq[sd.win0 + vals[sd.base + first - 1]];
   }
-  const KeyT kp = keys[sd.base + i - 1];
-  const uint32_t sp = win2seq[sd.win0 + vals[sd.base + i - 1]];
-  nf = k != kp;
-  ne = nf || seq != sp;
+  ne_bits = nf_bits = 0;
+#pragma unroll
+  for (int j = 0; j < kSortIpt; ++j) {
+    const uint32_t idx = (uint32_t)w * 32 * kSortIpt + j * 32 + lane;
+    KeyT kj = 0;
+    vv[j] = 0;
+    sq[j] = kNone;
+    if (idx < cnt) {
+      kj = keys[sd.base + beg + idx];
+      vv[j] = vals[sd.base + beg + idx];
+      sq[j] = win2seq[sd.win0 + vv[j]];
+    }
+    KeyT kp = __shfl_up_sync(0xffffffffu, kj, 1);
+    uint32_t sp = __shfl_up_sync(0xffffffffu, sq[j], 1);
+    const KeyT k31 = __shfl_sync(0xffffffffu, kj, 31);
+    const uint32_t s31 = __shfl_sync(0xffffffffu, sq[j], 31);
+    if (lane == 0) {
+      kp = k_prev;
+      sp = s_prev;
+    }
+    if (idx < cnt) {
+      const bool at0 = beg + idx == 0;
+      const bool nf = at0 || kj != kp;
+      const bool ne = nf || sq[j] != sp;
+      nf_bits |= (uint32_t)nf << j;
+      ne_bits |= (uint32_t)ne << j;
+    }
+    k_prev = k31;  // lane 0 of the next item follows lane 31 of this one
+    s_prev = s31;
+  }
 }
 
 template <typename KeyT>
@@ -262,20 +356,15 @@ k_rle_count(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
   const uint32_t lt = t - sd.tile0;
   const uint64_t beg = (uint64_t)lt * kTile;
   const uint32_t cnt = (uint32_t)min((uint64_t)kTile, sd.G - beg);
-  uint32_t ce = 0, cf = 0;
-  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-    uint32_t seq;
-    bool ne, nf;
-    rle_flags<KeyT>(sd, (uint32_t)(beg + i), keys, vals, win2seq, seq, ne, nf);
-    ce += ne;
-    cf += nf;
-  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t vv[kSortIpt], sq[kSortIpt], ne_bits, nf_bits;
+  rle_load_flags<KeyT>(sd, beg, cnt, w, lane, keys, vals, win2seq, vv, sq, ne_bits, nf_bits);
+  uint32_t ce = __popc(ne_bits), cf = __popc(nf_bits);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     ce += __shfl_xor_sync(0xffffffffu, ce, o);
     cf += __shfl_xor_sync(0xffffffffu, cf, o);
   }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) {
     sw[0][w] = ce;
     sw[1][w] = cf;
@@ -325,7 +414,7 @@ k_rle_scan(const SegDesc* __restrict__ segs, uint32_t* __restrict__ tcnt,
 // Entry and feature numbering.  Temporaries of segment s live at
 // [sd.base + s, sd.base + s + G + 1).
 template <typename KeyT>
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 3)
 k_rle_emit(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg,
            const KeyT* __restrict__ keys, const uint32_t* __restrict__ vals,
            const uint32_t* __restrict__ win2seq, const uint32_t* __restrict__ tcnt,
@@ -341,16 +430,13 @@ k_rle_emit(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_s
   const uint32_t cnt = (uint32_t)min((uint64_t)kTile, sd.G - beg);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t lt_mask = lanemask_lt();
-  // Pass 1: per-warp totals.
-  uint32_t we = 0, wf = 0;
-#pragma unroll 4
-  for (int j = 0; j < kSortIpt; ++j) {
-    const uint32_t idx = (uint32_t)w * 32 * kSortIpt + j * 32 + lane;
-    bool ne = false, nf = false;
-    uint32_t seq;
-    if (idx < cnt) rle_flags<KeyT>(sd, (uint32_t)(beg + idx), keys, vals, win2seq, seq, ne, nf);
-    we += __popc(__ballot_sync(0xffffffffu, ne));
-    wf += __popc(__ballot_sync(0xffffffffu, nf));
+  uint32_t vv[kSortIpt], sq[kSortIpt], ne_bits, nf_bits;
+  rle_load_flags<KeyT>(sd, beg, cnt, w, lane, keys, vals, win2seq, vv, sq, ne_bits, nf_bits);
+  uint32_t we = __popc(ne_bits), wf = __popc(nf_bits);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    we += __shfl_xor_sync(0xffffffffu, we, o);
+    wf += __shfl_xor_sync(0xffffffffu, wf, o);
   }
   if (lane == 0) {
     swe[w] = we;
@@ -363,24 +449,21 @@ k_rle_emit(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_s
     rf += swf[i];
   }
   const uint64_t tb = sd.base + s;
-  // Pass 2: numbering and writes.  re / rf count entries / features that
-  // start before the current element.
+  // re / rf count entries / features that start before the current item.
+#pragma unroll
   for (int j = 0; j < kSortIpt; ++j) {
     const uint32_t idx = (uint32_t)w * 32 * kSortIpt + j * 32 + lane;
-    bool ne = false, nf = false;
-    uint32_t seq = 0;
-    if (idx < cnt) rle_flags<KeyT>(sd, (uint32_t)(beg + idx), keys, vals, win2seq, seq, ne, nf);
+    const bool ne = (ne_bits >> j) & 1u, nf = (nf_bits >> j) & 1u;
     const uint32_t be = __ballot_sync(0xffffffffu, ne);
     const uint32_t bf = __ballot_sync(0xffffffffu, nf);
     if (idx < cnt) {
       const uint32_t i = (uint32_t)(beg + idx);
-      // Index of this element's entry / feature.
       const uint32_t e = re + __popc(be & lt_mask) - (ne ? 0u : 1u);
       const uint32_t f = rf + __popc(bf & lt_mask) - (nf ? 0u : 1u);
-      ewin[sd.pool + vals[sd.base + i]] = ne ? e : kNone;
+      ewin[sd.pool + vv[j]] = ne ? e : kNone;
       if (ne) {
         estart[tb + e] = i;
-        etseq[tb + e] = seq;
+        etseq[tb + e] = sq[j];
         efid[tb + e] = f;
       }
       if (nf) fstart[tb + f] = e;
@@ -422,26 +505,26 @@ template <typename KeyT>
 void sort_pass_t(bool first, const SegDesc* segs, uint32_t nsegs,
                  const uint32_t* tile_seg, uint32_t ntiles,
                  const MaskDesc* masks, const uint64_t* fullkey,
-                 const void* kin, const uint32_t* vin, void* kout,
+                 void* kin, const uint32_t* vin, void* kout,
                  uint32_t* vout, uint32_t* hist, int shift, int rbits,
                  cudaStream_t st) {
   const size_t radix = (size_t)1 << rbits;
   const size_t up_smem = radix * 4;
-  const size_t dn_smem = (kWarps + 1) * radix * 4;
-  const KeyT* ki = (const KeyT*)kin;
+  const size_t dn_smem = downsweep_smem(rbits, (int)sizeof(KeyT));
+  KeyT* ki = (KeyT*)kin;
   KeyT* ko = (KeyT*)kout;
   if (first) {
-    auto ku = k_upsweep<KeyT, true>;
-    auto kd = k_downsweep<KeyT, true>;
-    ku<<<ntiles, kSortThreads, up_smem, st>>>(segs, tile_seg, masks, fullkey, ki, hist, shift, rbits);
+    k_upsweep<KeyT, true><<<ntiles, kSortThreads, up_smem, st>>>(segs, tile_seg, masks, fullkey, ki,
+                                                                  hist, shift, rbits);
     k_seg_scan<<<nsegs, kSortThreads, 0, st>>>(segs, hist, rbits);
-    kd<<<ntiles, kSortThreads, dn_smem, st>>>(segs, tile_seg, masks, fullkey, ki, vin, ko, vout, hist, shift, rbits);
+    k_downsweep<KeyT, true><<<ntiles, kSortThreads, dn_smem, st>>>(segs, tile_seg, ki, vin, ko, vout,
+                                                                    hist, shift, rbits);
   } else {
-    auto ku = k_upsweep<KeyT, false>;
-    auto kd = k_downsweep<KeyT, false>;
-    ku<<<ntiles, kSortThreads, up_smem, st>>>(segs, tile_seg, masks, fullkey, ki, hist, shift, rbits);
+    k_upsweep<KeyT, false><<<ntiles, kSortThreads, up_smem, st>>>(segs, tile_seg, masks, fullkey, ki,
+                                                                   hist, shift, rbits);
     k_seg_scan<<<nsegs, kSortThreads, 0, st>>>(segs, hist, rbits);
-    kd<<<ntiles, kSortThreads, dn_smem, st>>>(segs, tile_seg, masks, fullkey, ki, vin, ko, vout, hist, shift, rbits);
+    k_downsweep<KeyT, false><<<ntiles, kSortThreads, dn_smem, st>>>(segs, tile_seg, ki, vin, ko, vout,
+                                                                     hist, shift, rbits);
   }
 }
 
@@ -464,13 +547,13 @@ void rle_t(const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg,
 }  // namespace
 
 int prep_init() {
-  // Largest downsweep footprint: (warps + 1) x 2^kMaxRadixBits counters.
-  const int smem = (kWarps + 1) * (1 << kMaxRadixBits) * 4;
+  // Largest scatter footprint: the widest digit with 8-byte keys.
+  const int big = (int)downsweep_smem(kMaxRadixBits, 8);
   cudaError_t e = cudaSuccess;
-  e = e ? e : cudaFuncSetAttribute(k_downsweep<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  e = e ? e : cudaFuncSetAttribute(k_downsweep<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  e = e ? e : cudaFuncSetAttribute(k_downsweep<uint64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  e = e ? e : cudaFuncSetAttribute(k_downsweep<uint64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = e ? e : cudaFuncSetAttribute(k_downsweep<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  e = e ? e : cudaFuncSetAttribute(k_downsweep<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  e = e ? e : cudaFuncSetAttribute(k_downsweep<uint64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  e = e ? e : cudaFuncSetAttribute(k_downsweep<uint64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return (int)e;
 }
 
@@ -484,7 +567,7 @@ void launch_pack(const DsPack* d_ds, uint32_t nds, uint32_t nseq_total, int g,
 void launch_sort_pass(bool wide, bool first, const SegDesc* segs,
                       uint32_t nsegs, const uint32_t* tile_seg,
                       uint32_t ntiles, const MaskDesc* masks,
-                      const uint64_t* fullkey, const void* kin,
+                      const uint64_t* fullkey, void* kin,
                       const uint32_t* vin, void* kout, uint32_t* vout,
                       uint32_t* hist, int shift, int rbits, cudaStream_t st) {
   if (ntiles == 0) return;

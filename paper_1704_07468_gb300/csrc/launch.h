@@ -24,12 +24,13 @@ void launch_pack(const DsPack* d_ds, uint32_t nds, uint32_t nseq_total,
                  uint32_t* win2seq, uint32_t* status, cudaStream_t st);
 
 // One LSD radix-sort pass over every segment of a chunk.  For the first
-// pass the keys are cut out of the full g-mer keys (`fullkey`) and the
-// payload is the dataset-local window index; later passes read kin/vin.
+// pass the keys are cut out of the full g-mer keys (`fullkey`) into `kin`
+// (which must not alias `kout`) and the payload is the dataset-local window
+// index (`vin` unused); later passes read kin/vin.
 void launch_sort_pass(bool wide, bool first, const SegDesc* segs,
                       uint32_t nsegs, const uint32_t* tile_seg,
                       uint32_t ntiles, const MaskDesc* masks,
-                      const uint64_t* fullkey, const void* kin,
+                      const uint64_t* fullkey, void* kin,
                       const uint32_t* vin, void* kout, uint32_t* vout,
                       uint32_t* hist, int shift, int rbits, cudaStream_t st);
 

@@ -218,6 +218,12 @@ extern "C" int gakco_gram_device_noalloc(int sigma, int g, int k, const uint8_t*
       snprintf(msg, sizeof msg, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
       return set_err(err, err_len, GAKCO_E_CUDA, msg);
     }
+    e = (cudaError_t)prep_init();  // kernel attributes (shared-memory limits); no allocation
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      snprintf(msg, sizeof msg, "kernel attribute set-up: %s", cudaGetErrorString(e));
+      return set_err(err, err_len, GAKCO_E_CUDA, msg);
+    }
     d_scratch[dev] = (unsigned char*)p;
     d_ready[dev] = true;
   }
@@ -300,7 +306,7 @@ extern "C" int gakco_gram_device_noalloc(int sigma, int g, int k, const uint8_t*
       const bool w = kbits > 32;
       void* kbuf[2] = {S + o_keyA, S + o_keyB};
       uint32_t* vbuf[2] = {(uint32_t*)(S + o_valA), (uint32_t*)(S + o_valB)};
-      const void* kin = nullptr;
+      void* kin = kbuf[1];  // the first pass extracts the masked keys here
       const uint32_t* vin = nullptr;
       int cur = 0;
       for (int q = 0; q < np; ++q) {
