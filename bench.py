@@ -204,6 +204,72 @@ def alg_bytes_sort(ctx_sets, g, bits, radix_bits, masks_per_level):
     return total
 
 
+def run_serve(pkg, n_requests, warmup):
+    """Serving workload: the protein training set resident on the device, a
+    Poisson stream of test batches (mean 5 ms apart, 1-256 sequences each),
+    replayed in real time.  Continuous batching (submit / poll) against the
+    plain per-request path (each request alone, synchronously, in arrival
+    order).  Latency = completion - scheduled arrival."""
+    tr = synth.protein()
+    reqs = synth.serve_requests(warmup + n_requests, seed=9)
+    ntr = len(tr[1]) - 1
+
+    def summarize(lat, rows, span):
+        lat = np.sort(np.asarray(lat))
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "rows_per_s": rows / span,
+                "gram_entries_per_s": rows * ntr / span}
+
+    ctx = pkg.gakco_create(20, 8, 4)
+    ctx.fit(*tr)
+    # Warm the slots and the synchronous path.
+    for _, c, o in reqs[:3]:
+        ctx.cross_fitted(c, o)
+    t0 = time.perf_counter()
+    i, pending, lat, lib_lat, rows = 0, {}, [], [], 0
+    first = last = None
+    while i < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i][0] <= now:
+            pending[ctx.submit(reqs[i][1], reqs[i][2])] = (i, reqs[i][0])
+            i += 1
+        for t in list(pending):
+            out = ctx.poll(t, 0)
+            if out is None:
+                continue
+            idx, arr = pending.pop(t)
+            done = time.perf_counter() - t0
+            if idx >= warmup:
+                lat.append((done - arr) * 1e3)
+                lib_lat.append(out["latency_ms"])
+                rows += len(reqs[idx][2]) - 1
+                first = arr if first is None else min(first, arr)
+                last = done if last is None else max(last, done)
+        time.sleep(0.0001)
+    cb = summarize(lat, rows, last - first)
+    cb["submit_to_done_p50_ms"] = float(np.percentile(lib_lat, 50))
+    cb["batches"] = int(ctx.get_stat("served_batches"))
+    # Plain per-request path on the same arrivals.
+    t0 = time.perf_counter()
+    lat, rows, first, last = [], 0, None, None
+    for idx, (arr, c, o) in enumerate(reqs):
+        now = time.perf_counter() - t0
+        if now < arr:
+            time.sleep(arr - now)
+        ctx.cross_fitted(c, o)
+        done = time.perf_counter() - t0
+        if idx >= warmup:
+            lat.append((done - arr) * 1e3)
+            rows += len(o) - 1
+            first = arr if first is None else min(first, arr)
+            last = done
+    plain = summarize(lat, rows, last - first)
+    ctx.close()
+    return {"workload": f"protein train N={ntr} resident; {n_requests} requests after {warmup} warm-up, "
+                        "Poisson mean 5 ms, 1-256 sequences each, normalised K(test, train) rows",
+            "continuous_batching": cb, "plain_per_request": plain}
+
+
 def run_ours(args):
     import torch
 
@@ -350,6 +416,10 @@ def run_ours(args):
     roof["launch_ms"] = per_launch_ms
     roof["share_of_step"] = dom_ms / sum(v[0] for v in timings.values())
 
+    serve = None
+    if args.serve_requests > 0 and rank == 0:
+        serve = run_serve(pkg, args.serve_requests, args.serve_warmup)
+
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_rows > 0:
         import oracle
@@ -371,6 +441,7 @@ def run_ours(args):
         "mask_passes_per_s": len(sets) * n_masks * ws / (step_ms / 1000.0),
         "pair_updates_per_step": pairs,
         "plain_gpu": plain,
+        "serve": serve,
         "e2e": {"value": entries * ws / (e2e_step / 1000.0), "unit": UNIT,
                 "ms_per_step": e2e_step, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches * args.steps,
@@ -397,6 +468,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-rows", type=int, default=64)
     ap.add_argument("--ref-rows", type=int, default=16)
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-warmup", type=int, default=50)
     ap.add_argument("--dna-sizes", type=lambda v: [int(t) for t in v.split(",")], default=None,
                     help="subset of DNA dataset sizes (small cases for profiling)")
     args = ap.parse_args()

@@ -51,7 +51,8 @@
  *   - Errors: every call returns GAKCO_OK (0) or a negative code; the
  *     context's message is available from gakco_last_error.  After an error
  *     the context remains usable.
- *   - Threads: a context is used by one host thread at a time.
+ *   - Threads: a context is used by one host thread at a time, except that
+ *     gakco_submit / gakco_poll may be called concurrently (see below).
  */
 #ifndef GAKCO_H
 #define GAKCO_H
@@ -103,6 +104,10 @@ const char *gakco_last_error(const gakco_ctx *ctx);
 #define GAKCO_OPT_FAIL_ALLOC_AFTER 8 /* fault injection: fail the Nth next device
                                         allocation (0 = off); host side only */
 #define GAKCO_OPT_GROUP_BYTES 9     /* entry-array bytes per accumulation mask group */
+#define GAKCO_OPT_SERVE_SLOTS 10    /* serving: concurrent batches (streams), 1..16, default 3 */
+#define GAKCO_OPT_SERVE_MAX_SEQS 11 /* serving: test sequences per micro-batch (default 512) */
+#define GAKCO_OPT_SERVE_MAX_WINDOWS 12 /* serving: test windows per micro-batch (default 2^19) */
+#define GAKCO_OPT_SERVE_MEM_BYTES 13 /* serving: device-memory budget of busy slots (0 = none) */
 int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 
 /*
@@ -121,6 +126,8 @@ int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 #define GAKCO_STAT_PAIR_UPDATES 5     /* batched engine: c_x*c_y additions made */
 #define GAKCO_STAT_ENTRIES_VISITED 6  /* batched engine: (feature, sequence) entries visited */
 #define GAKCO_STAT_WINDOWS_VISITED 7  /* batched engine: (window, mask) slots read */
+#define GAKCO_STAT_SERVED_BATCHES 8   /* serving: micro-batches completed so far */
+#define GAKCO_STAT_SERVED_REQUESTS 9  /* serving: requests completed so far */
 int gakco_get_stat(const gakco_ctx *ctx, int key, double *value);
 
 /*
@@ -167,6 +174,65 @@ int gakco_gram_batch_device(gakco_ctx *ctx, int32_t ndata,
                             const int64_t *const *offsets, const int32_t *n,
                             int32_t *const *K, double *const *Khat,
                             int32_t *const *Nm, void *stream);
+
+/*
+ * Cross kernel K(test, train) (Section 3.1: the paper classifies with one
+ * kernel over training and test sequences together; K(test, train) is its
+ * test-rows x train-columns block, and K(t, t) depends on t alone).
+ *
+ * gakco_fit makes a training set resident: for every mask its features
+ * (distinct (g-m)-mers, in key order) with their entries, and the training
+ * diagonal.  Host buffers; synchronous.  The index stays until the next
+ * fit or gakco_destroy.  Fails with GAKCO_E_INVALID while served requests
+ * are in flight.  gakco_fit_device takes device codes on `stream`.
+ */
+int gakco_fit(gakco_ctx *ctx, const uint8_t *codes, const int64_t *offsets,
+              int32_t n);
+int gakco_fit_device(gakco_ctx *ctx, const uint8_t *codes,
+                     const int64_t *offsets, int32_t n, void *stream);
+
+/*
+ * K and Khat of a test batch (nt sequences) against the fitted training
+ * set: row-major nt x n_train int32 K and fp64 Khat (either may be NULL in
+ * the host form).  Khat(t, y) = K(t, y) / sqrt(K(t, t) K(y, y)).  The
+ * int32 bound uses the longest test and training sequences.
+ * gakco_cross_fitted: host buffers; _device: device codes and outputs (K
+ * required) on `stream`.  gakco_cross = gakco_fit(train) followed by
+ * gakco_cross_fitted(test).
+ */
+int gakco_cross_fitted(gakco_ctx *ctx, const uint8_t *codes,
+                       const int64_t *offsets, int32_t nt, int32_t *K,
+                       double *Khat);
+int gakco_cross_fitted_device(gakco_ctx *ctx, const uint8_t *codes,
+                              const int64_t *offsets, int32_t nt, int32_t *K,
+                              double *Khat, void *stream);
+int gakco_cross(gakco_ctx *ctx, const uint8_t *test_codes,
+                const int64_t *test_offsets, int32_t nt,
+                const uint8_t *train_codes, const int64_t *train_offsets,
+                int32_t ntrain, int32_t *K, double *Khat);
+
+/*
+ * Serving: asynchronous cross-kernel requests against the fitted training
+ * set, with continuous batching.  gakco_submit copies the request's host
+ * inputs, queues it and returns a ticket at once; K / Khat are the
+ * caller's host output buffers (nt x n_train, may be NULL), written before
+ * the request is reported done and untouched afterwards.  A dispatcher
+ * thread admits queued requests into free slots (one CUDA stream and
+ * working memory each) as micro-batches bounded by GAKCO_OPT_SERVE_MAX_SEQS
+ * / _MAX_WINDOWS and by the memory budget; batches in different slots
+ * overlap on the device, and requests arriving meanwhile are admitted as
+ * slots free up.  A request's results do not depend on the batch it ran in.
+ *
+ * gakco_poll waits up to timeout_ms (0: no wait, < 0: until done) and
+ * returns GAKCO_OK when the request is done (the ticket is then released
+ * and *latency_ms, if given, receives submit-to-done milliseconds),
+ * GAKCO_E_PENDING if it is not done yet, or the request's error.
+ * gakco_submit and gakco_poll may be called from several threads.
+ */
+int gakco_submit(gakco_ctx *ctx, const uint8_t *codes, const int64_t *offsets,
+                 int32_t nt, int32_t *K, double *Khat, uint64_t *ticket);
+int gakco_poll(gakco_ctx *ctx, uint64_t ticket, int timeout_ms,
+               double *latency_ms);
 
 /*
  * Gram kernel of one dataset that allocates nothing.  The paper has no

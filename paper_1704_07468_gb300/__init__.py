@@ -27,6 +27,7 @@ _LIB_PATH = os.path.join(_HERE, "_lib", "libgakco.so")
 _lib = None
 
 GAKCO_OK = 0
+GAKCO_E_PENDING = -6
 ERRORS = {
     -1: "GAKCO_E_INVALID", -2: "GAKCO_E_OOM", -3: "GAKCO_E_OVERFLOW",
     -4: "GAKCO_E_CUDA", -5: "GAKCO_E_TIMEOUT", -6: "GAKCO_E_PENDING",
@@ -34,10 +35,11 @@ ERRORS = {
 }
 OPT = {"engine": 1, "radix_bits": 2, "chunk_elems": 3, "graph": 4,
        "accum_threads": 5, "profile": 6, "smem_cols": 7,
-       "fail_alloc_after": 8, "group_bytes": 9}
+       "fail_alloc_after": 8, "group_bytes": 9, "serve_slots": 10,
+       "serve_max_seqs": 11, "serve_max_windows": 12, "serve_mem_bytes": 13}
 STAT = {"launches": 1, "mask_passes": 2, "device_bytes": 3,
         "graph_replay": 4, "pair_updates": 5, "entries_visited": 6,
-        "windows_visited": 7}
+        "windows_visited": 7, "served_batches": 8, "served_requests": 9}
 
 
 class GakcoError(RuntimeError):
@@ -79,6 +81,14 @@ def load_library(build_if_missing: bool = False):
         "gakco_gram_batch": ([p, i32, p, p, p, p, p, p], ctypes.c_int),
         "gakco_gram_device": ([p, p, p, i32, p, p, p, p], ctypes.c_int),
         "gakco_gram_batch_device": ([p, i32, p, p, p, p, p, p, p], ctypes.c_int),
+        "gakco_fit": ([p, p, p, i32], ctypes.c_int),
+        "gakco_fit_device": ([p, p, p, i32, p], ctypes.c_int),
+        "gakco_cross_fitted": ([p, p, p, i32, p, p], ctypes.c_int),
+        "gakco_cross_fitted_device": ([p, p, p, i32, p, p, p], ctypes.c_int),
+        "gakco_cross": ([p, p, p, i32, p, p, i32, p, p], ctypes.c_int),
+        "gakco_submit": ([p, p, p, i32, p, p, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "gakco_poll": ([p, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
+                       ctypes.c_int),
         "gakco_gram_device_noalloc": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, p, p, i32,
                                        p, p, p, p, ctypes.c_char_p, ctypes.c_int],
                                       ctypes.c_int),
@@ -119,6 +129,8 @@ class Context:
             raise GakcoError(rc, f"gakco_create(sigma={sigma}, g={g}, k={k}) failed")
         self._h = h
         self.sigma, self.g, self.k, self.M = int(sigma), int(g), int(k), int(g) - int(k)
+        self._ntrain = 0
+        self._inflight = {}
 
     # -- lifetime --------------------------------------------------------
     def close(self):
@@ -223,6 +235,80 @@ class Context:
         self._check(rc)
 
 
+def _add_cross_methods(cls):
+    """Cross-kernel and serving methods (C: gakco_fit, gakco_cross_fitted,
+    gakco_cross, gakco_submit, gakco_poll)."""
+
+    def fit(self, codes, offsets):
+        codes, offsets = _dataset(codes, offsets)
+        keep = codes if codes.size else np.zeros(1, np.uint8)
+        self._check(self._lib.gakco_fit(self._h, keep.ctypes.data, offsets.ctypes.data,
+                                        len(offsets) - 1))
+        self._ntrain = len(offsets) - 1
+        return self
+
+    def fit_device(self, codes_ptr, offsets, stream=None):
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        self._check(self._lib.gakco_fit_device(self._h, codes_ptr, offsets.ctypes.data,
+                                               len(offsets) - 1,
+                                               ctypes.c_void_p(stream) if stream else None))
+        self._ntrain = len(offsets) - 1
+        return self
+
+    def cross_fitted(self, codes, offsets, khat=True, K=True):
+        codes, offsets = _dataset(codes, offsets)
+        nt = len(offsets) - 1
+        out = {"K": np.empty((nt, self._ntrain), np.int32) if K else None,
+               "Khat": np.empty((nt, self._ntrain), np.float64) if khat else None}
+        keep = codes if codes.size else np.zeros(1, np.uint8)
+        self._check(self._lib.gakco_cross_fitted(
+            self._h, keep.ctypes.data, offsets.ctypes.data, nt,
+            _ptr(out["K"]), _ptr(out["Khat"])))
+        return out
+
+    def cross_fitted_device(self, codes_ptr, offsets, K_ptr, Khat_ptr=None, stream=None):
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        self._check(self._lib.gakco_cross_fitted_device(
+            self._h, codes_ptr, offsets.ctypes.data, len(offsets) - 1, K_ptr, Khat_ptr,
+            ctypes.c_void_p(stream) if stream else None))
+
+    def cross(self, test, train, khat=True):
+        """K(test, train) for host datasets (fit + cross_fitted)."""
+        self.fit(*train)
+        return self.cross_fitted(*test, khat=khat)
+
+    def submit(self, codes, offsets, khat=True, K=True):
+        """Queue a cross-kernel request; returns its ticket.  The output
+        arrays are kept alive by the context until poll() reports done."""
+        codes, offsets = _dataset(codes, offsets)
+        nt = len(offsets) - 1
+        out = {"K": np.empty((nt, self._ntrain), np.int32) if K else None,
+               "Khat": np.empty((nt, self._ntrain), np.float64) if khat else None}
+        keep = codes if codes.size else np.zeros(1, np.uint8)
+        t = ctypes.c_uint64()
+        rc = self._lib.gakco_submit(self._h, keep.ctypes.data, offsets.ctypes.data, nt,
+                                    _ptr(out["K"]), _ptr(out["Khat"]), ctypes.byref(t))
+        self._check(rc)
+        self._inflight[t.value] = out
+        return t.value
+
+    def poll(self, ticket, timeout_ms=0):
+        """None while pending; else the result dict with ``latency_ms``."""
+        lat = ctypes.c_double()
+        rc = self._lib.gakco_poll(self._h, ctypes.c_uint64(ticket), int(timeout_ms),
+                                  ctypes.byref(lat))
+        if rc == GAKCO_E_PENDING:
+            return None
+        out = self._inflight.pop(ticket, None)
+        self._check(rc)
+        out["latency_ms"] = lat.value
+        return out
+
+    for f in (fit, fit_device, cross_fitted, cross_fitted_device, cross, submit, poll):
+        setattr(cls, f.__name__, f)
+    return cls
+
+
 def gakco_gram_device_noalloc(sigma, g, k, codes_ptr, offsets, K_ptr, Khat_ptr=None,
                               Nm_ptr=None, stream=None):
     """Gram kernel without any allocation (C: ``gakco_gram_device_noalloc``).
@@ -241,6 +327,9 @@ def gakco_gram_device_noalloc(sigma, g, k, codes_ptr, offsets, K_ptr, Khat_ptr=N
                                        Khat_ptr, Nm_ptr, stream, err, 256)
     if rc != GAKCO_OK:
         raise GakcoError(rc, err.value.decode())
+
+
+_add_cross_methods(Context)
 
 
 def gakco_create(sigma: int, g: int, k: int) -> Context:

@@ -1,22 +1,35 @@
 // Host side of the engine: the C ABI of include/gakco.h, input validation,
-// the work plan, device memory, CUDA-graph replay and timing.
+// the work plan, device memory, CUDA-graph replay, timing, the resident
+// training index for cross kernels, and the serving loop.
 //
-// The work of one call (Alg. 1 of GaKCo, arXiv 1704.07468):
+// The work of one Gram call (Alg. 1 of GaKCo, arXiv 1704.07468):
 //   1. pack every window of every dataset into a full g-mer key;
 //   2. for every level m and mask, sort the masked keys and count runs
 //      (batched: all (dataset, mask) segments of a chunk per launch);
-//   3. accumulate C_0..C_M row by row on chip and apply Eq. 9 and Eq. 7;
-//   4. mirror the symmetric result and normalise.
+//   3. accumulate rows of C_0..C_M on chip, group by group of masks;
+//   4. apply Eq. 9 and Eq. 7, mirror the symmetric result and normalise.
 // The plain engine instead runs one (dataset, mask) segment per launch and
 // applies countAndUpdate with global atomics, as the paper states it.
+//
+// Every pipeline step runs on a Work: a stream plus the device buffers it
+// needs.  The context owns one for its synchronous calls; each serving slot
+// owns its own, so requests in different slots overlap on the device.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -79,6 +92,72 @@ uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
   return h;
 }
 
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+// Device buffers and stream of one pipeline instance.
+struct Work {
+  cudaStream_t cs = nullptr;
+  DevBuf fullkey, win2seq, ewin, eseq, efe, keyA, keyB, valA, valB, hist, tcnt, segtot, estart,
+      etseq, efid, fstart, tables, codes, outK, outKhat, outNm, rinv, status, Cplain, Cacc, ea, eb,
+      Cd, Cx;
+  void* h_tables = nullptr;
+  size_t h_tables_cap = 0;
+  void* h_status = nullptr;
+  void* h_io = nullptr;  // pinned staging of a serving slot
+  size_t h_io_cap = 0;
+  int64_t launches = 0;
+  std::string err;
+  double pairs = 0, entries = 0, windows = 0;
+
+  std::vector<DevBuf*> all() {
+    return {&fullkey, &win2seq, &ewin,   &eseq,  &efe,  &keyA,  &keyB,  &valA,    &valB,
+            &hist,    &tcnt,    &segtot, &estart, &etseq, &efid, &fstart, &tables, &codes,
+            &outK,    &outKhat, &outNm,  &rinv,  &status, &Cplain, &Cacc, &ea,    &eb,
+            &Cd,      &Cx};
+  }
+  size_t bytes() {
+    size_t s = 0;
+    for (DevBuf* b : all()) s += b->cap;
+    return s;
+  }
+};
+
+// Resident index of the fitted training set.
+struct Train {
+  bool ok = false;
+  int32_t n = 0;
+  uint64_t G = 0;
+  std::vector<uint32_t> woff;
+  DevBuf ukey, ufirst, eseq, nfeat, diagC, rinv;
+};
+
+struct Request {
+  uint64_t ticket = 0;
+  std::vector<uint8_t> codes;
+  std::vector<int64_t> off;
+  int32_t nt = 0;
+  uint64_t windows = 0;
+  int32_t* K = nullptr;     // caller host buffers
+  double* Khat = nullptr;
+  int rc = 1;               // 1 pending, 0 done, < 0 error
+  std::string err;
+  double t_submit = 0, t_done = 0;
+};
+
+struct Slot {
+  Work w;
+  std::vector<Request*> batch;
+  std::vector<int32_t> row0;
+  int32_t nt = 0;
+  bool busy = false;
+  std::atomic<bool> gpu_done{false};
+  size_t k_off = 0, kh_off = 0;  // output offsets in the pinned staging
+};
+
 }  // namespace
 
 struct gakco_ctx {
@@ -97,27 +176,23 @@ struct gakco_ctx {
   int accum_threads = 512;
   int profile = 0;
   int64_t smem_cols = 0;
-  int64_t fail_alloc_after = 0;
+  std::atomic<int64_t> fail_alloc_after{0};
   int64_t group_bytes = (int64_t)64 << 20;
+  int serve_slots = 3;
+  int64_t serve_max_seqs = 512;
+  int64_t serve_max_windows = (int64_t)1 << 19;
+  int64_t serve_mem_bytes = 0;  // 0: no budget
 
   std::string err;
   int device = 0;
   int nsm = 0;
   size_t smem_optin = 0;
-  cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-
-  DevBuf fullkey, win2seq, ewin, eseq, efe, keyA, keyB, valA, valB, hist, tcnt,
-      segtot, estart, etseq, efid, fstart, tables, codes, outK, outKhat, outNm,
-      rinv, status, Cplain, Cacc;
-  void* h_tables = nullptr;
-  size_t h_tables_cap = 0;
-  void* h_status = nullptr;
+  Work main;
 
   cudaGraphExec_t gexec = nullptr;
   uint64_t gkey = 0;
 
-  int64_t launches = 0;
   int64_t last_launches = 0, last_mask_passes = 0;
   int last_replay = 0;
   double last_pairs = 0, last_entries = 0, last_windows = 0;
@@ -125,6 +200,19 @@ struct gakco_ctx {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<std::pair<std::string, std::pair<double, int64_t>>> timings;
+
+  Train train;
+
+  // serving
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread dispatcher;
+  bool serving = false, stopping = false;
+  std::deque<Request*> pending;
+  std::unordered_map<uint64_t, Request*> requests;
+  std::vector<std::unique_ptr<Slot>> slots;
+  uint64_t next_ticket = 1;
+  int64_t served_batches = 0, served_requests = 0;
 };
 
 namespace {
@@ -139,15 +227,33 @@ int fail(gakco_ctx* c, int code, const char* fmt, ...) {
   return code;
 }
 
-int cuda_fail(gakco_ctx* c, cudaError_t e, const char* what) {
-  cudaGetLastError();
-  return fail(c, GAKCO_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+int wfail(Work& w, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  w.err = buf;
+  return code;
 }
 
-int ensure(gakco_ctx* c, DevBuf& b, size_t bytes, const char* what) {
+int wcuda(Work& w, cudaError_t e, const char* what) {
+  cudaGetLastError();
+  return wfail(w, GAKCO_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Copies a Work's error into the context's message.
+int ret(gakco_ctx* c, Work& w, int rc) {
+  if (rc != GAKCO_OK) c->err = w.err;
+  return rc;
+}
+
+int ensure(gakco_ctx* c, Work& w, DevBuf& b, size_t bytes, const char* what) {
   if (bytes <= b.cap) return GAKCO_OK;
-  if (c->fail_alloc_after > 0 && --c->fail_alloc_after == 0)
-    return fail(c, GAKCO_E_OOM, "injected allocation failure (%s, %zu bytes)", what, bytes);
+  int64_t left = c->fail_alloc_after.load();
+  while (left > 0 && !c->fail_alloc_after.compare_exchange_weak(left, left - 1)) {
+  }
+  if (left == 1) return wfail(w, GAKCO_E_OOM, "injected allocation failure (%s, %zu bytes)", what, bytes);
   if (b.p) {
     cudaFree(b.p);
     b.p = nullptr;
@@ -158,7 +264,7 @@ int ensure(gakco_ctx* c, DevBuf& b, size_t bytes, const char* what) {
   if (e != cudaSuccess) {
     cudaGetLastError();
     b.p = nullptr;
-    return fail(c, GAKCO_E_OOM, "cudaMalloc(%s, %zu bytes): %s", what, want, cudaGetErrorString(e));
+    return wfail(w, GAKCO_E_OOM, "cudaMalloc(%s, %zu bytes): %s", what, want, cudaGetErrorString(e));
   }
   b.cap = want;
   return GAKCO_OK;
@@ -170,21 +276,58 @@ void release(DevBuf& b) {
   b.cap = 0;
 }
 
+void release_work(Work& w) {
+  if (w.cs) cudaStreamSynchronize(w.cs);
+  for (DevBuf* b : w.all()) release(*b);
+  if (w.h_tables) cudaFreeHost(w.h_tables);
+  if (w.h_status) cudaFreeHost(w.h_status);
+  if (w.h_io) cudaFreeHost(w.h_io);
+  if (w.cs) cudaStreamDestroy(w.cs);
+  w.h_tables = w.h_status = w.h_io = nullptr;
+  w.cs = nullptr;
+}
+
+int init_work(Work& w) {
+  cudaError_t e = cudaStreamCreateWithFlags(&w.cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMallocHost(&w.h_status, 128);
+  if (e != cudaSuccess) return wcuda(w, e, "work set-up");
+  return GAKCO_OK;
+}
+
+int ensure_pinned(Work& w, void*& p, size_t& cap, size_t bytes, const char* what) {
+  if (bytes <= cap) return GAKCO_OK;
+  if (p) cudaFreeHost(p);
+  p = nullptr;
+  cap = 0;
+  const size_t want = align_up(std::max(bytes, (size_t)1 << 16), 1 << 16);
+  cudaError_t e = cudaMallocHost(&p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    return wfail(w, GAKCO_E_OOM, "cudaMallocHost(%s, %zu): %s", what, want, cudaGetErrorString(e));
+  }
+  cap = want;
+  return GAKCO_OK;
+}
+
 void drop_graph(gakco_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   c->gexec = nullptr;
   c->gkey = 0;
 }
 
-// Kernel-launch bracket: counts launches and, when profiling, records
-// events around them on the engine's stream.
+// Kernel-launch bracket: counts launches and, when profiling the context's
+// own Work, records events around them on its stream.
 struct Bracket {
   gakco_ctx* c;
+  Work& w;
   const char* name;
   size_t ia = 0;
-  Bracket(gakco_ctx* c_, const char* n_, int count) : c(c_), name(n_) {
-    c->launches += count;
-    if (c->profile) {
+  bool on;
+  Bracket(gakco_ctx* c_, Work& w_, const char* n_, int count)
+      : c(c_), w(w_), name(n_), on(c_->profile && &w_ == &c_->main) {
+    w.launches += count;
+    if (on) {
       while (c->ev_pool.size() < c->ev_used + 2) {
         cudaEvent_t e;
         cudaEventCreate(&e);
@@ -192,12 +335,12 @@ struct Bracket {
       }
       ia = c->ev_used;
       c->ev_used += 2;
-      cudaEventRecord(c->ev_pool[ia], c->cs);
+      cudaEventRecord(c->ev_pool[ia], w.cs);
     }
   }
   ~Bracket() {
-    if (c->profile) {
-      cudaEventRecord(c->ev_pool[ia + 1], c->cs);
+    if (on) {
+      cudaEventRecord(c->ev_pool[ia + 1], w.cs);
       c->timed.push_back({name, c->ev_pool[ia], c->ev_pool[ia + 1]});
     }
   }
@@ -226,12 +369,14 @@ struct Plan {
   std::vector<size_t> o_coff, o_woff;
 };
 
-// Validate datasets and compute window offsets; fills p.ds.
-int plan_datasets(gakco_ctx* c, Plan& p, int32_t nd, const uint8_t* const* codes,
+// Validate datasets and compute window offsets; fills p.ds.  `maxw_other`
+// (windows of the longest sequence on the other side of a cross kernel, 0
+// for a Gram) enters the int32 bound.
+int plan_datasets(gakco_ctx* c, Work& w, Plan& p, int32_t nd, const uint8_t* const* codes,
                   const int64_t* const* off, const int32_t* n, int32_t* const* K,
-                  double* const* Khat, int32_t* const* Nm, bool device) {
-  if (nd < 0) return fail(c, GAKCO_E_INVALID, "ndata must be >= 0");
-  if (nd > 0 && (!codes || !off || !n)) return fail(c, GAKCO_E_INVALID, "null dataset arrays");
+                  double* const* Khat, int32_t* const* Nm, bool device, uint64_t maxw_other = 0) {
+  if (nd < 0) return wfail(w, GAKCO_E_INVALID, "ndata must be >= 0");
+  if (nd > 0 && (!codes || !off || !n)) return wfail(w, GAKCO_E_INVALID, "null dataset arrays");
   uint64_t wmax = 0;
   p.ds.resize(nd);
   for (int32_t d = 0; d < nd; ++d) {
@@ -243,26 +388,25 @@ int plan_datasets(gakco_ctx* c, Plan& p, int32_t nd, const uint8_t* const* codes
     D.Khat = Khat ? Khat[d] : nullptr;
     D.Nm = Nm ? Nm[d] : nullptr;
     if (D.n < 0 || D.n > 65535)
-      return fail(c, GAKCO_E_INVALID, "dataset %d: n = %d outside [0, 65535]", d, D.n);
-    if (D.n > 0 && !D.off) return fail(c, GAKCO_E_INVALID, "dataset %d: null offsets", d);
+      return wfail(w, GAKCO_E_INVALID, "dataset %d: n = %d outside [0, 65535]", d, D.n);
+    if (D.n > 0 && !D.off) return wfail(w, GAKCO_E_INVALID, "dataset %d: null offsets", d);
     if (device && D.n > 0 && !D.K)
-      return fail(c, GAKCO_E_INVALID, "dataset %d: device calls need a K buffer", d);
+      return wfail(w, GAKCO_E_INVALID, "dataset %d: device calls need a K buffer", d);
     D.woff.assign(D.n + 1, 0);
     uint64_t acc = 0;
     int64_t total = 0;
     for (int32_t x = 0; x < D.n; ++x) {
       const int64_t len = D.off[x + 1] - D.off[x];
       if (D.off[x] < 0 || len < 0)
-        return fail(c, GAKCO_E_INVALID, "dataset %d: offsets must be non-negative and non-decreasing", d);
+        return wfail(w, GAKCO_E_INVALID, "dataset %d: offsets must be non-negative and non-decreasing", d);
       const uint64_t W = len >= c->g ? (uint64_t)(len - c->g + 1) : 0;
       wmax = std::max(wmax, W);
       acc += W;
       total += len;
-      if (acc >= 0xFFFFFFFFull)
-        return fail(c, GAKCO_E_OVERFLOW, "dataset %d: 2^32 or more windows", d);
+      if (acc >= 0xFFFFFFFFull) return wfail(w, GAKCO_E_OVERFLOW, "dataset %d: 2^32 or more windows", d);
       D.woff[x + 1] = (uint32_t)acc;
     }
-    if (D.n > 0 && total > 0 && !D.codes) return fail(c, GAKCO_E_INVALID, "dataset %d: null codes", d);
+    if (D.n > 0 && total > 0 && !D.codes) return wfail(w, GAKCO_E_INVALID, "dataset %d: null codes", d);
     D.G = acc;
     D.win0 = p.gtot;
     D.seq0 = p.nseq;
@@ -273,11 +417,12 @@ int plan_datasets(gakco_ctx* c, Plan& p, int32_t nd, const uint8_t* const* codes
     if (D.Khat) p.want_khat = true;
   }
   // Every C_m(x, y) <= C(g, m) W_x W_y must stay below 2^31.
-  const long double bound = (long double)c->maxC * (long double)wmax * (long double)wmax;
+  const uint64_t wo = maxw_other ? maxw_other : wmax;
+  const long double bound = (long double)c->maxC * (long double)wmax * (long double)wo;
   if (bound >= 2147483648.0L)
-    return fail(c, GAKCO_E_OVERFLOW,
-                "C(g,m) * W_max^2 = %.0Lf reaches 2^31 (W_max = %llu windows); int32 kernel would overflow",
-                bound, (unsigned long long)wmax);
+    return wfail(w, GAKCO_E_OVERFLOW,
+                 "C(g,m) * W_max^2 = %.0Lf reaches 2^31 (W_max = %llu windows); int32 kernel would overflow",
+                 bound, (unsigned long long)std::max(wmax, wo));
   return GAKCO_OK;
 }
 
@@ -341,58 +486,72 @@ void plan_chunks(gakco_ctx* c, Plan& p, bool plain) {
   }
 }
 
-// Work items of the accumulation kernel: (dataset, level, first mask, mask
-// count, row, c0, c1).  The masks of a level are cut into groups whose
-// entry arrays (about 12 bytes per window per mask) fit `group_bytes`, so
-// the rows processed together share an L2-resident working set; items go
-// out group by group, most expensive rows first within a group.
-void plan_items(gakco_ctx* c, Plan& p) {
-  size_t avail = c->smem_optin > 2048 ? c->smem_optin - 1024 : 0;
+std::vector<uint32_t> level_firsts(gakco_ctx* c) {
+  std::vector<uint32_t> lf(c->M + 2, 0);
+  for (uint32_t mu = 0; mu < c->masks.size(); ++mu) lf[c->mask_level[mu] + 1] = mu + 1;
+  for (int m = 1; m <= c->M + 1; ++m) lf[m] = std::max(lf[m], lf[m - 1]);
+  return lf;
+}
+
+uint32_t smem_columns(gakco_ctx* c, uint32_t n) {
+  const size_t avail = c->smem_optin > 2048 ? c->smem_optin - 1024 : 0;
   uint32_t ncols = (uint32_t)std::min<size_t>(avail / 4 - 1, 65535);
   if (c->smem_cols > 0) ncols = std::min<uint32_t>(ncols, (uint32_t)c->smem_cols);
-  ncols = std::max<uint32_t>(1, std::min<uint32_t>(ncols, std::max<uint32_t>(p.nmax, 1)));
-  p.ncols = ncols;
-  p.acc_smem = 4 * ((size_t)ncols + 1);  // + the trash slot
-  std::vector<uint32_t> level_first(c->M + 2, 0);
-  for (uint32_t mu = 0; mu < c->masks.size(); ++mu) level_first[c->mask_level[mu] + 1] = mu + 1;
-  for (int m = 1; m <= c->M + 1; ++m) level_first[m] = std::max(level_first[m], level_first[m - 1]);
+  return std::max<uint32_t>(1, std::min<uint32_t>(ncols, std::max<uint32_t>(n, 1)));
+}
+
+// Work items of the accumulation kernels: (dataset, level, first mask, mask
+// count, row, c0, c1).  The masks of a level are cut into groups whose
+// entry arrays (`per_mask_bytes` each) fit `group_bytes`, so the rows
+// processed together share an L2-resident working set; items go out group
+// by group, most expensive rows first within a group.  `triangle` keeps
+// only columns y >= x (Gram); `ncols_total` is the column count.
+void add_items(gakco_ctx* c, std::vector<uint32_t>& items, uint32_t d, const std::vector<uint32_t>& woff,
+               uint32_t nrows, uint32_t ncols_total, uint32_t ncols, double per_mask_bytes,
+               bool triangle) {
   struct Row {
     double cost;
     uint32_t x, c0, c1;
   };
+  std::vector<Row> rows;
+  for (uint32_t x = 0; x < nrows; ++x) {
+    const double W = (double)(woff[x + 1] - woff[x]);
+    if (W == 0) continue;  // its row of C stays zero (memset)
+    for (uint32_t t0 = 0; t0 < ncols_total; t0 += ncols) {
+      const uint32_t t1 = std::min<uint32_t>(ncols_total, t0 + ncols);
+      if (triangle && t1 <= x) continue;
+      const uint32_t c0 = triangle ? std::max<uint32_t>(x, t0) : t0;
+      rows.push_back({W * (double)(t1 - c0) + W + (double)(t1 - c0), x, c0, t1});
+    }
+  }
+  std::stable_sort(rows.begin(), rows.end(), [](const Row& a, const Row& b) { return a.cost > b.cost; });
+  const std::vector<uint32_t> lf = level_firsts(c);
+  const uint32_t gmax =
+      (uint32_t)std::max(1.0, std::floor((double)c->group_bytes / std::max(per_mask_bytes, 1.0)));
+  for (int m = 0; m <= c->M; ++m) {
+    const uint32_t mf = lf[m], mc = lf[m + 1] - lf[m];
+    const uint32_t ng = (mc + gmax - 1) / gmax;
+    for (uint32_t gi = 0; gi < ng; ++gi) {
+      const uint32_t a = mf + (uint32_t)((uint64_t)mc * gi / ng);
+      const uint32_t b = mf + (uint32_t)((uint64_t)mc * (gi + 1) / ng);
+      for (const Row& r : rows) {
+        const uint32_t it[kItemWords] = {d, (uint32_t)m, a, b - a, r.x, r.c0, r.c1, 0};
+        items.insert(items.end(), it, it + kItemWords);
+      }
+    }
+  }
+}
+
+void plan_items(gakco_ctx* c, Plan& p) {
+  const uint32_t ncols = smem_columns(c, p.nmax);
+  p.ncols = ncols;
+  p.acc_smem = 4 * ((size_t)ncols + 1);  // + the trash slot
   p.items.clear();
   for (size_t d = 0; d < p.ds.size(); ++d) {
     const DsHost& D = p.ds[d];
     if (D.n == 0) continue;
-    std::vector<Row> rows;
-    for (int32_t x = 0; x < D.n; ++x) {
-      const double W = (double)(D.woff[x + 1] - D.woff[x]);
-      for (uint32_t t0 = 0; t0 < (uint32_t)D.n; t0 += ncols) {
-        const uint32_t t1 = std::min<uint32_t>((uint32_t)D.n, t0 + ncols);
-        if (t1 <= (uint32_t)x) continue;
-        const uint32_t c0 = std::max<uint32_t>((uint32_t)x, t0);
-        rows.push_back({W * (double)(t1 - c0) + W + (double)(t1 - c0), (uint32_t)x, c0, t1});
-      }
-    }
-    std::stable_sort(rows.begin(), rows.end(),
-                     [](const Row& a, const Row& b) { return a.cost > b.cost; });
-    // Rows without windows still need their (zero) row of C: they are
-    // covered by the memset; only rows with windows get items.
-    const double per_mask = 12.0 * (double)std::max<uint64_t>(D.G, 1);
-    const uint32_t gmax = (uint32_t)std::max(1.0, std::floor((double)c->group_bytes / per_mask));
-    for (int m = 0; m <= c->M; ++m) {
-      const uint32_t mf = level_first[m], mc = level_first[m + 1] - level_first[m];
-      const uint32_t ng = (mc + gmax - 1) / gmax;
-      for (uint32_t gi = 0; gi < ng; ++gi) {
-        const uint32_t a = mf + (uint32_t)((uint64_t)mc * gi / ng);
-        const uint32_t b = mf + (uint32_t)((uint64_t)mc * (gi + 1) / ng);
-        for (const Row& r : rows) {
-          if (D.woff[r.x + 1] == D.woff[r.x]) continue;
-          const uint32_t it[kItemWords] = {(uint32_t)d, (uint32_t)m, a, b - a, r.x, r.c0, r.c1, 0};
-          p.items.insert(p.items.end(), it, it + kItemWords);
-        }
-      }
-    }
+    add_items(c, p.items, (uint32_t)d, D.woff, (uint32_t)D.n, (uint32_t)D.n, ncols,
+              12.0 * (double)std::max<uint64_t>(D.G, 1), true);
   }
 }
 
@@ -411,21 +570,28 @@ struct Tables {
   }
 };
 
-// Device memory for the plan; then serialise and upload the tables.
-int plan_memory_and_tables(gakco_ctx* c, Plan& p, bool plain) {
-  const uint64_t G = p.gtot;
-  const uint64_t nm = c->masks.size();
-  int rc;
-#define ENSURE(buf, bytes)                                         \
-  do {                                                             \
-    if ((rc = ensure(c, c->buf, (size_t)(bytes), #buf)) != GAKCO_OK) return rc; \
+// Copy host tables into the Work's device table area through pinned memory.
+int upload_tables(gakco_ctx* c, Work& w, Tables& t) {
+  int rc = ensure(c, w, w.tables, t.buf.size(), "tables");
+  if (rc != GAKCO_OK) return rc;
+  if ((rc = ensure_pinned(w, w.h_tables, w.h_tables_cap, t.buf.size(), "tables")) != GAKCO_OK) return rc;
+  // The pinned staging area may still feed an earlier copy.
+  cudaError_t e = cudaStreamSynchronize(w.cs);
+  if (e != cudaSuccess) return wcuda(w, e, "stream sync before table upload");
+  memcpy(w.h_tables, t.buf.data(), t.buf.size());
+  e = cudaMemcpyAsync(w.tables.p, w.h_tables, t.buf.size(), cudaMemcpyHostToDevice, w.cs);
+  if (e != cudaSuccess) return wcuda(w, e, "table upload");
+  return GAKCO_OK;
+}
+
+#define ENSURE(buf, bytes)                                                          \
+  do {                                                                              \
+    if ((rc = ensure(c, w, w.buf, (size_t)(bytes), #buf)) != GAKCO_OK) return rc; \
   } while (0)
-  ENSURE(fullkey, G * 8);
-  ENSURE(win2seq, G * 4);
-  const uint64_t pool = plain ? G : nm * G;
-  ENSURE(ewin, pool * 4);
-  ENSURE(eseq, pool * 4);
-  ENSURE(efe, pool * 4);
+
+// Sort / run-length buffers for the plan's largest chunk.
+int ensure_sort_buffers(gakco_ctx* c, Work& w, const Plan& p) {
+  int rc;
   const uint64_t ce = p.max_chunk_elems;
   const size_t kbytes = p.any_wide ? 8 : 4;
   ENSURE(keyA, ce * kbytes);
@@ -440,17 +606,13 @@ int plan_memory_and_tables(gakco_ctx* c, Plan& p, bool plain) {
   ENSURE(etseq, te * 4);
   ENSURE(efid, te * 4);
   ENSURE(fstart, te * 4);
-  uint64_t nsum = 0;
-  for (auto& D : p.ds) nsum += (uint64_t)D.n;
-  ENSURE(rinv, nsum * 8);
   ENSURE(status, 128);
-  if (plain) ENSURE(Cplain, (uint64_t)(c->M + 1) * p.nmax * p.nmax * 4);
-  uint64_t csum = 0;
-  for (auto& D : p.ds) csum += (uint64_t)(c->M + 1) * D.n * D.n;
-  p.c_elems = csum;
-  if (!plain) ENSURE(Cacc, csum * 4);
+  return GAKCO_OK;
+}
 
-  Tables t;
+// Common tables: masks, levels, segments, tiles, items, per-dataset offsets
+// and room for the DsPack / DsInfo records.
+void add_common_tables(gakco_ctx* c, Plan& p, Tables& t) {
   p.o_masks = t.add(c->masks.data(), c->masks.size() * sizeof(MaskDesc));
   p.o_level = t.add(c->mask_level.data(), c->mask_level.size() * 4);
   p.o_segs = t.add(p.segs.data(), p.segs.size() * sizeof(SegDesc));
@@ -465,9 +627,13 @@ int plan_memory_and_tables(gakco_ctx* c, Plan& p, bool plain) {
   }
   p.o_pack = t.reserve(p.ds.size() * sizeof(DsPack));
   p.o_info = t.reserve(p.ds.size() * sizeof(DsInfo));
-  ENSURE(tables, t.buf.size());
-  uint8_t* base = (uint8_t*)c->tables.p;
-  double* rinv = (double*)c->rinv.p;
+}
+
+// Fill the DsPack / DsInfo records once the table area's device address
+// is known; returns the finishing-tile count.
+uint32_t fill_records(gakco_ctx* c, Work& w, Plan& p, Tables& t, bool plain) {
+  uint8_t* base = (uint8_t*)w.tables.p;
+  double* rinv = (double*)w.rinv.p;
   uint64_t cacc = 0;
   uint32_t ftile = 0;
   for (size_t d = 0; d < p.ds.size(); ++d) {
@@ -486,8 +652,8 @@ int plan_memory_and_tables(gakco_ctx* c, Plan& p, bool plain) {
     in.Nm = D.Nm;
     in.Khat = D.Khat;
     in.rinv = rinv;
-    rinv += D.n;
-    in.C = plain ? nullptr : (uint32_t*)c->Cacc.p + cacc;
+    if (rinv) rinv += D.n;
+    in.C = (plain || !w.Cacc.p) ? nullptr : (uint32_t*)w.Cacc.p + cacc;
     cacc += (uint64_t)(c->M + 1) * D.n * D.n;
     in.seq0 = D.seq0;
     in.win0 = D.win0;
@@ -498,32 +664,38 @@ int plan_memory_and_tables(gakco_ctx* c, Plan& p, bool plain) {
     ftile += nt * nt;
     memcpy(t.buf.data() + p.o_info + d * sizeof(DsInfo), &in, sizeof in);
   }
-  p.ftiles = ftile;
-  if (t.buf.size() > c->h_tables_cap) {
-    if (c->h_tables) cudaFreeHost(c->h_tables);
-    c->h_tables = nullptr;
-    c->h_tables_cap = 0;
-    size_t want = align_up(t.buf.size(), 1 << 16);
-    cudaError_t e = cudaMallocHost(&c->h_tables, want);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      c->h_tables = nullptr;
-      return fail(c, GAKCO_E_OOM, "cudaMallocHost(tables, %zu): %s", want, cudaGetErrorString(e));
-    }
-    c->h_tables_cap = want;
-  }
-  // The pinned staging area may still feed an earlier copy.
-  cudaError_t e = cudaStreamSynchronize(c->cs);
-  if (e != cudaSuccess) return cuda_fail(c, e, "stream sync before table upload");
-  memcpy(c->h_tables, t.buf.data(), t.buf.size());
-  e = cudaMemcpyAsync(c->tables.p, c->h_tables, t.buf.size(), cudaMemcpyHostToDevice, c->cs);
-  if (e != cudaSuccess) return cuda_fail(c, e, "table upload");
-#undef ENSURE
-  return GAKCO_OK;
+  return ftile;
 }
 
-AccParams acc_params(gakco_ctx* c, const Plan& p, uint32_t* counter) {
-  uint8_t* base = (uint8_t*)c->tables.p;
+// Device memory for a Gram plan; then serialise and upload the tables.
+int plan_memory_and_tables(gakco_ctx* c, Work& w, Plan& p, bool plain) {
+  const uint64_t G = p.gtot;
+  const uint64_t nm = c->masks.size();
+  int rc;
+  ENSURE(fullkey, G * 8);
+  ENSURE(win2seq, G * 4);
+  const uint64_t pool = plain ? G : nm * G;
+  ENSURE(ewin, pool * 4);
+  ENSURE(eseq, pool * 4);
+  ENSURE(efe, pool * 4);
+  if ((rc = ensure_sort_buffers(c, w, p)) != GAKCO_OK) return rc;
+  uint64_t nsum = 0;
+  for (auto& D : p.ds) nsum += (uint64_t)D.n;
+  ENSURE(rinv, nsum * 8);
+  if (plain) ENSURE(Cplain, (uint64_t)(c->M + 1) * p.nmax * p.nmax * 4);
+  uint64_t csum = 0;
+  for (auto& D : p.ds) csum += (uint64_t)(c->M + 1) * D.n * D.n;
+  p.c_elems = plain ? 0 : csum;
+  if (!plain) ENSURE(Cacc, csum * 4);
+  Tables t;
+  add_common_tables(c, p, t);
+  if ((rc = ensure(c, w, w.tables, t.buf.size(), "tables")) != GAKCO_OK) return rc;
+  p.ftiles = fill_records(c, w, p, t, plain);
+  return upload_tables(c, w, t);
+}
+
+AccParams acc_params(gakco_ctx* c, Work& w, const Plan& p, uint32_t* counter) {
+  uint8_t* base = (uint8_t*)w.tables.p;
   AccParams a{};
   a.ds = (const DsInfo*)(base + p.o_info);
   a.items = (const uint32_t*)(base + p.o_items);
@@ -531,68 +703,87 @@ AccParams acc_params(gakco_ctx* c, const Plan& p, uint32_t* counter) {
   a.counter = counter;
   a.M = (uint32_t)c->M;
   a.gtot = p.gtot;
-  a.ewin = (const uint32_t*)c->ewin.p;
-  a.eseq = (const uint32_t*)c->eseq.p;
-  a.efe = (const uint32_t*)c->efe.p;
+  a.ewin = (const uint32_t*)w.ewin.p;
+  a.eseq = (const uint32_t*)w.eseq.p;
+  a.efe = (const uint32_t*)w.efe.p;
   a.ncols = p.ncols;
-  a.status = (uint32_t*)c->status.p;
-  a.work = (unsigned long long*)((uint8_t*)c->status.p + 64);
+  a.status = (uint32_t*)w.status.p;
+  a.work = (unsigned long long*)((uint8_t*)w.status.p + 64);
   memcpy(a.h, c->h, sizeof a.h);
   memcpy(a.ie, c->ie, sizeof a.ie);
   return a;
 }
 
-// Sort and run-length pass over one chunk.
-void enqueue_chunk(gakco_ctx* c, const Plan& p, const Chunk& ch) {
-  uint8_t* base = (uint8_t*)c->tables.p;
+enum class Tail { kGram, kFit, kCross };
+
+// Sort and run-length pass over one chunk, then the entry finalisation of
+// the given kind.
+void enqueue_chunk(gakco_ctx* c, Work& w, const Plan& p, const Chunk& ch, Tail tail,
+                   const TrainIndex* tr = nullptr, const CrossOut* xo = nullptr) {
+  uint8_t* base = (uint8_t*)w.tables.p;
   const SegDesc* segs = (const SegDesc*)(base + p.o_segs) + ch.seg_first;
   const uint32_t* tseg = (const uint32_t*)(base + p.o_tiles) + ch.tile_first;
   const MaskDesc* masks = (const MaskDesc*)(base + p.o_masks);
-  void* kbuf[2] = {c->keyA.p, c->keyB.p};
-  uint32_t* vbuf[2] = {(uint32_t*)c->valA.p, (uint32_t*)c->valB.p};
+  const uint32_t* levels = (const uint32_t*)(base + p.o_level);
+  void* kbuf[2] = {w.keyA.p, w.keyB.p};
+  uint32_t* vbuf[2] = {(uint32_t*)w.valA.p, (uint32_t*)w.valB.p};
   void* kin = kbuf[1];  // the first pass extracts the masked keys here
   uint32_t* vin = nullptr;
   int cur = 0;
   for (size_t q = 0; q < ch.passes.size(); ++q) {
-    Bracket b(c, "sort_pass", 3);
+    Bracket b(c, w, "sort_pass", 3);
     launch_sort_pass(ch.wide, q == 0, segs, ch.nseg, tseg, ch.ntiles, masks,
-                     (const uint64_t*)c->fullkey.p, kin, vin, kbuf[cur], vbuf[cur],
-                     (uint32_t*)c->hist.p, ch.passes[q].first, ch.passes[q].second, c->cs);
+                     (const uint64_t*)w.fullkey.p, kin, vin, kbuf[cur], vbuf[cur],
+                     (uint32_t*)w.hist.p, ch.passes[q].first, ch.passes[q].second, w.cs);
     kin = kbuf[cur];
     vin = vbuf[cur];
     cur ^= 1;
   }
-  Bracket b(c, "run_length", 4);
-  launch_rle(ch.wide, segs, ch.nseg, tseg, ch.ntiles, kin, vin, (const uint32_t*)c->win2seq.p,
-             (uint32_t*)c->tcnt.p, (uint32_t*)c->segtot.p, (uint32_t*)c->estart.p,
-             (uint32_t*)c->etseq.p, (uint32_t*)c->efid.p, (uint32_t*)c->fstart.p,
-             (uint32_t*)c->ewin.p, (uint32_t*)c->eseq.p, (uint32_t*)c->efe.p, c->cs);
+  Bracket b(c, w, "run_length", tail == Tail::kFit ? 5 : 4);
+  launch_rle_head(ch.wide, segs, ch.nseg, tseg, ch.ntiles, kin, vin, (const uint32_t*)w.win2seq.p,
+                  (uint32_t*)w.tcnt.p, (uint32_t*)w.segtot.p, (uint32_t*)w.estart.p,
+                  (uint32_t*)w.etseq.p, (uint32_t*)w.efid.p, (uint32_t*)w.fstart.p,
+                  (uint32_t*)w.ewin.p, w.cs);
+  if (tail == Tail::kCross) {
+    launch_cross_final(ch.wide, segs, tseg, ch.ntiles, (const uint32_t*)w.segtot.p, kin,
+                       (const uint32_t*)w.estart.p, (const uint32_t*)w.etseq.p, levels, *tr, *xo, w.cs);
+    return;
+  }
+  launch_rle_final(segs, tseg, ch.ntiles, (const uint32_t*)w.segtot.p, (const uint32_t*)w.estart.p,
+                   (const uint32_t*)w.etseq.p, (const uint32_t*)w.efid.p, (const uint32_t*)w.fstart.p,
+                   (uint32_t*)w.eseq.p, (uint32_t*)w.efe.p, w.cs);
+  if (tail == Tail::kFit)
+    launch_train_index(ch.wide, segs, tseg, ch.ntiles, (const uint32_t*)w.segtot.p, kin,
+                       (const uint32_t*)w.estart.p, (const uint32_t*)w.fstart.p,
+                       (const uint32_t*)w.eseq.p, levels, *tr, w.cs);
 }
 
-// Everything after the table upload, on c->cs.
-int enqueue_work(gakco_ctx* c, const Plan& p, bool plain) {
-  uint8_t* base = (uint8_t*)c->tables.p;
-  uint32_t* status = (uint32_t*)c->status.p;
-  cudaMemsetAsync(status, 0, 128, c->cs);
+// Everything of a Gram call after the table upload, on w.cs.
+int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
+  uint8_t* base = (uint8_t*)w.tables.p;
+  uint32_t* status = (uint32_t*)w.status.p;
+  cudaMemsetAsync(status, 0, 128, w.cs);
   {
-    Bracket b(c, "pack", 1);
+    Bracket b(c, w, "pack", 1);
     launch_pack((const DsPack*)(base + p.o_pack), (uint32_t)p.ds.size(), p.nseq, c->g, c->bits,
-                c->sigma, (uint64_t*)c->fullkey.p, (uint32_t*)c->win2seq.p, status, c->cs);
+                c->sigma, (uint64_t*)w.fullkey.p, (uint32_t*)w.win2seq.p, status, w.cs);
   }
+  AccParams a = acc_params(c, w, p, status + 8);
   if (!plain) {
-    for (const Chunk& ch : p.chunks) enqueue_chunk(c, p, ch);
-    AccParams a = acc_params(c, p, status + 8);
-    if (p.c_elems) cudaMemsetAsync(c->Cacc.p, 0, p.c_elems * 4, c->cs);
+    for (const Chunk& ch : p.chunks) enqueue_chunk(c, w, p, ch, Tail::kGram);
+    if (p.c_elems) cudaMemsetAsync(w.Cacc.p, 0, p.c_elems * 4, w.cs);
     {
-      Bracket b(c, "accumulate", 1);
-      launch_accum(a, c->accum_threads, p.acc_blocks, p.acc_smem, c->cs);
+      Bracket b(c, w, "accumulate", 1);
+      launch_accum(a, c->accum_threads, p.acc_blocks, p.acc_smem, w.cs);
     }
     {
-      Bracket b(c, "diag", 1);
-      launch_diag((const DsInfo*)(base + p.o_info), (uint32_t)p.ds.size(), p.nseq, a, c->cs);
+      Bracket b(c, w, "diag", 1);
+      launch_diag((const DsInfo*)(base + p.o_info), (uint32_t)p.ds.size(), p.nseq, a, w.cs);
     }
+    Bracket b(c, w, "combine", 1);
+    launch_combine((const DsInfo*)(base + p.o_info), (uint32_t)p.ds.size(), p.ftiles, a, p.want_nm,
+                   p.want_khat, w.cs);
   } else {
-    AccParams a = acc_params(c, p, status + 8);
     const DsInfo* infos = (const DsInfo*)(base + p.o_info);
     // Chunks are one segment each and ordered by level, then mask, then
     // dataset; handle one dataset at a time so C_m fits one buffer.
@@ -600,32 +791,25 @@ int enqueue_work(gakco_ctx* c, const Plan& p, bool plain) {
       const DsHost& D = p.ds[d];
       if (D.n == 0) continue;
       const uint64_t nn = (uint64_t)D.n * D.n;
-      cudaMemsetAsync(c->Cplain.p, 0, (size_t)(c->M + 1) * nn * 4, c->cs);
+      cudaMemsetAsync(w.Cplain.p, 0, (size_t)(c->M + 1) * nn * 4, w.cs);
       for (const Chunk& ch : p.chunks) {
         if (p.seg_ds[ch.seg_first] != d) continue;
         const SegDesc& s = p.segs[ch.seg_first];
-        enqueue_chunk(c, p, ch);
-        Bracket b(c, "pairs_global", 1);
-        launch_pairs_global((const uint32_t*)c->segtot.p, (const uint32_t*)c->eseq.p + s.pool,
-                            (const uint32_t*)c->efe.p + s.pool, s.G,
-                            (uint32_t*)c->Cplain.p + (uint64_t)ch.level * nn, (uint32_t)D.n,
-                            status, c->cs);
+        enqueue_chunk(c, w, p, ch, Tail::kGram);
+        Bracket b(c, w, "pairs_global", 1);
+        launch_pairs_global((const uint32_t*)w.segtot.p, (const uint32_t*)w.eseq.p + s.pool,
+                            (const uint32_t*)w.efe.p + s.pool, s.G,
+                            (uint32_t*)w.Cplain.p + (uint64_t)ch.level * nn, (uint32_t)D.n, status,
+                            w.cs);
       }
-      Bracket b(c, "ie_combine", 1);
-      launch_ie_combine(infos + d, (const uint32_t*)c->Cplain.p, (uint32_t)D.n, a, c->cs);
+      Bracket b(c, w, "ie_combine", 1);
+      launch_ie_combine(infos + d, (const uint32_t*)w.Cplain.p, (uint32_t)D.n, a, w.cs);
     }
-  }
-  if (plain) {
-    Bracket b(c, "finish", 1);
-    launch_finish((const DsInfo*)(base + p.o_info), (uint32_t)p.ds.size(), p.ftiles, (uint32_t)c->M,
-                  p.want_nm, p.want_khat, c->cs);
-  } else {
-    Bracket b(c, "combine", 1);
-    launch_combine((const DsInfo*)(base + p.o_info), (uint32_t)p.ds.size(), p.ftiles,
-                   acc_params(c, p, status + 8), p.want_nm, p.want_khat, c->cs);
+    Bracket b(c, w, "finish", 1);
+    launch_finish(infos, (uint32_t)p.ds.size(), p.ftiles, (uint32_t)c->M, p.want_nm, p.want_khat, w.cs);
   }
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+  if (e != cudaSuccess) return wcuda(w, e, "kernel launch");
   return GAKCO_OK;
 }
 
@@ -643,11 +827,25 @@ uint64_t plan_key(gakco_ctx* c, const Plan& p, bool plain) {
   return h;
 }
 
-int finish_call(gakco_ctx* c) {
-  cudaError_t e = cudaMemcpyAsync(c->h_status, c->status.p, 128, cudaMemcpyDeviceToHost, c->cs);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->cs);
-  if (e != cudaSuccess) return cuda_fail(c, e, "engine run");
-  if (c->profile) {
+// Device status word -> error code (after the status has reached h_status).
+int check_status(gakco_ctx* c, Work& w) {
+  const uint32_t st = ((const uint32_t*)w.h_status)[0];
+  const unsigned long long* wk = (const unsigned long long*)((const uint8_t*)w.h_status + 64);
+  w.pairs = (double)wk[0];
+  w.entries = (double)wk[1];
+  w.windows = (double)wk[2];
+  if (st & kErrBadCode) return wfail(w, GAKCO_E_INVALID, "input holds a symbol >= sigma (%d)", c->sigma);
+  if (st & kErrKneCM) return wfail(w, GAKCO_E_INTERNAL, "internal check failed: sum h_m N_m != C_M");
+  if (st & kErrBadEntry) return wfail(w, GAKCO_E_INTERNAL, "internal check failed: entry out of range");
+  if (st) return wfail(w, GAKCO_E_INTERNAL, "device status 0x%x", st);
+  return GAKCO_OK;
+}
+
+int sync_and_check(gakco_ctx* c, Work& w) {
+  cudaError_t e = cudaMemcpyAsync(w.h_status, w.status.p, 128, cudaMemcpyDeviceToHost, w.cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(w.cs);
+  if (e != cudaSuccess) return wcuda(w, e, "engine run");
+  if (c->profile && &w == &c->main) {
     c->timings.clear();
     for (const Timed& t : c->timed) {
       float ms = 0;
@@ -662,22 +860,14 @@ int finish_call(gakco_ctx* c) {
       if (!found) c->timings.push_back({t.name, {ms, 1}});
     }
   }
-  const uint32_t st = ((const uint32_t*)c->h_status)[0];
-  const unsigned long long* wk = (const unsigned long long*)((const uint8_t*)c->h_status + 64);
-  c->last_pairs = (double)wk[0];
-  c->last_entries = (double)wk[1];
-  c->last_windows = (double)wk[2];
-  if (st & kErrBadCode) return fail(c, GAKCO_E_INVALID, "input holds a symbol >= sigma (%d)", c->sigma);
-  if (st & kErrKneCM) return fail(c, GAKCO_E_INTERNAL, "internal check failed: sum h_m N_m != C_M");
-  if (st & kErrBadEntry) return fail(c, GAKCO_E_INTERNAL, "internal check failed: entry out of range");
-  if (st) return fail(c, GAKCO_E_INTERNAL, "device status 0x%x", st);
-  return GAKCO_OK;
+  return check_status(c, w);
 }
 
-// The batched / plain engine on device buffers.
-int run(gakco_ctx* c, Plan& p, cudaStream_t user) {
+// The batched / plain Gram engine on device buffers, on the context's Work.
+int run_gram(gakco_ctx* c, Plan& p, cudaStream_t user) {
+  Work& w = c->main;
   const bool plain = c->engine == 1;
-  c->launches = 0;
+  w.launches = 0;
   c->timed.clear();
   c->ev_used = 0;
   c->last_replay = 0;
@@ -689,17 +879,17 @@ int run(gakco_ctx* c, Plan& p, cudaStream_t user) {
     return GAKCO_OK;
   }
   cudaError_t e = cudaEventRecord(c->ev_in, user);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cs, c->ev_in, 0);
-  if (e != cudaSuccess) return cuda_fail(c, e, "stream ordering");
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(w.cs, c->ev_in, 0);
+  if (e != cudaSuccess) return wcuda(w, e, "stream ordering");
 
   const bool graph = c->use_graph && !c->profile && !plain;
   const uint64_t key = graph ? plan_key(c, p, plain) : 0;
   int rc;
   if (graph && c->gexec && key == c->gkey) {
     // Same plan as the cached graph: tables and buffers are unchanged.
-    e = cudaGraphLaunch(c->gexec, c->cs);
-    if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
-    c->launches = c->last_launches;
+    e = cudaGraphLaunch(c->gexec, w.cs);
+    if (e != cudaSuccess) return wcuda(w, e, "graph launch");
+    w.launches = c->last_launches;
     c->last_replay = 1;
   } else {
     drop_graph(c);
@@ -708,46 +898,50 @@ int run(gakco_ctx* c, Plan& p, cudaStream_t user) {
     if (!plain) {
       const int nb = accum_blocks_per_sm(c->accum_threads, p.acc_smem);
       if (nb <= 0)
-        return fail(c, GAKCO_E_CUDA, "accumulation kernel does not fit (%zu B shared)", p.acc_smem);
+        return wfail(w, GAKCO_E_CUDA, "accumulation kernel does not fit (%zu B shared)", p.acc_smem);
       p.acc_blocks = nb * c->nsm;
     }
-    if ((rc = plan_memory_and_tables(c, p, plain)) != GAKCO_OK) return rc;
+    if ((rc = plan_memory_and_tables(c, w, p, plain)) != GAKCO_OK) return rc;
     if (graph) {
       cudaGraph_t gr = nullptr;
-      e = cudaStreamBeginCapture(c->cs, cudaStreamCaptureModeThreadLocal);
-      if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
-      rc = enqueue_work(c, p, plain);
-      e = cudaStreamEndCapture(c->cs, &gr);
+      e = cudaStreamBeginCapture(w.cs, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return wcuda(w, e, "begin capture");
+      rc = enqueue_gram(c, w, p, plain);
+      e = cudaStreamEndCapture(w.cs, &gr);
       if (rc != GAKCO_OK) {
         if (gr) cudaGraphDestroy(gr);
         return rc;
       }
-      if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+      if (e != cudaSuccess) return wcuda(w, e, "end capture");
       e = cudaGraphInstantiate(&c->gexec, gr, 0);
       cudaGraphDestroy(gr);
       if (e != cudaSuccess) {
         c->gexec = nullptr;
-        return cuda_fail(c, e, "graph instantiate");
+        return wcuda(w, e, "graph instantiate");
       }
       c->gkey = key;
-      e = cudaGraphLaunch(c->gexec, c->cs);
-      if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+      e = cudaGraphLaunch(c->gexec, w.cs);
+      if (e != cudaSuccess) return wcuda(w, e, "graph launch");
     } else {
-      if ((rc = enqueue_work(c, p, plain)) != GAKCO_OK) return rc;
+      if ((rc = enqueue_gram(c, w, p, plain)) != GAKCO_OK) return rc;
     }
   }
-  c->last_launches = c->launches;
-  rc = finish_call(c);
-  e = cudaEventRecord(c->ev_out, c->cs);
+  c->last_launches = w.launches;
+  rc = sync_and_check(c, w);
+  c->last_pairs = w.pairs;
+  c->last_entries = w.entries;
+  c->last_windows = w.windows;
+  e = cudaEventRecord(c->ev_out, w.cs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(user, c->ev_out, 0);
-  if (e != cudaSuccess && rc == GAKCO_OK) rc = cuda_fail(c, e, "stream ordering");
+  if (e != cudaSuccess && rc == GAKCO_OK) rc = wcuda(w, e, "stream ordering");
   return rc;
 }
 
 int gram_host(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64_t* const* off,
               const int32_t* n, int32_t* const* K, double* const* Khat, int32_t* const* Nm) {
+  Work& w = c->main;
   Plan p;
-  int rc = plan_datasets(c, p, nd, codes, off, n, K, Khat, Nm, false);
+  int rc = plan_datasets(c, w, p, nd, codes, off, n, K, Khat, Nm, false);
   if (rc != GAKCO_OK) return rc;
   // Stage codes and outputs in the context's device buffers.
   uint64_t cbytes = 0, kel = 0, nmel = 0;
@@ -765,36 +959,418 @@ int gram_host(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64
     want_khat |= D.Khat != nullptr;
     want_nm |= D.Nm != nullptr;
   }
-  if ((rc = ensure(c, c->codes, cbytes + 16, "codes")) != GAKCO_OK) return rc;
-  if ((rc = ensure(c, c->outK, kel * 4 + 16, "K")) != GAKCO_OK) return rc;
-  if (want_khat && (rc = ensure(c, c->outKhat, kel * 8 + 16, "Khat")) != GAKCO_OK) return rc;
-  if (want_nm && (rc = ensure(c, c->outNm, nmel * 4 + 16, "Nm")) != GAKCO_OK) return rc;
+  ENSURE(codes, cbytes + 16);
+  ENSURE(outK, kel * 4 + 16);
+  if (want_khat) ENSURE(outKhat, kel * 8 + 16);
+  if (want_nm) ENSURE(outNm, nmel * 4 + 16);
   cudaError_t e = cudaSuccess;
   for (int32_t d = 0; d < nd && e == cudaSuccess; ++d) {
     DsHost& D = p.ds[d];
-    const uint8_t* dc = (const uint8_t*)c->codes.p + coff[d];
+    const uint8_t* dc = (const uint8_t*)w.codes.p + coff[d];
     if (D.n > 0 && D.off[D.n] > 0)
-      e = cudaMemcpyAsync((void*)dc, D.codes, (size_t)D.off[D.n], cudaMemcpyHostToDevice, c->cs);
+      e = cudaMemcpyAsync((void*)dc, D.codes, (size_t)D.off[D.n], cudaMemcpyHostToDevice, w.cs);
     D.codes = dc;
-    D.K = (int32_t*)c->outK.p + koff[d];
-    D.Khat = D.Khat ? (double*)c->outKhat.p + koff[d] : nullptr;
-    D.Nm = D.Nm ? (int32_t*)c->outNm.p + nmoff[d] : nullptr;
+    D.K = (int32_t*)w.outK.p + koff[d];
+    D.Khat = D.Khat ? (double*)w.outKhat.p + koff[d] : nullptr;
+    D.Nm = D.Nm ? (int32_t*)w.outNm.p + nmoff[d] : nullptr;
   }
-  if (e != cudaSuccess) return cuda_fail(c, e, "copy codes to device");
-  rc = run(c, p, c->cs);
+  if (e != cudaSuccess) return wcuda(w, e, "copy codes to device");
+  rc = run_gram(c, p, w.cs);
   if (rc != GAKCO_OK) return rc;
   for (int32_t d = 0; d < nd && e == cudaSuccess; ++d) {
     const DsHost& D = p.ds[d];
     const size_t nn = (size_t)D.n * D.n;
-    if (K && K[d] && nn) e = cudaMemcpyAsync(K[d], D.K, nn * 4, cudaMemcpyDeviceToHost, c->cs);
+    if (K && K[d] && nn) e = cudaMemcpyAsync(K[d], D.K, nn * 4, cudaMemcpyDeviceToHost, w.cs);
     if (e == cudaSuccess && Khat && Khat[d] && nn)
-      e = cudaMemcpyAsync(Khat[d], D.Khat, nn * 8, cudaMemcpyDeviceToHost, c->cs);
+      e = cudaMemcpyAsync(Khat[d], D.Khat, nn * 8, cudaMemcpyDeviceToHost, w.cs);
     if (e == cudaSuccess && Nm && Nm[d] && nn)
-      e = cudaMemcpyAsync(Nm[d], D.Nm, (size_t)(c->M + 1) * nn * 4, cudaMemcpyDeviceToHost, c->cs);
+      e = cudaMemcpyAsync(Nm[d], D.Nm, (size_t)(c->M + 1) * nn * 4, cudaMemcpyDeviceToHost, w.cs);
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->cs);
-  if (e != cudaSuccess) return cuda_fail(c, e, "copy results to host");
+  if (e == cudaSuccess) e = cudaStreamSynchronize(w.cs);
+  if (e != cudaSuccess) return wcuda(w, e, "copy results to host");
   return GAKCO_OK;
+}
+
+// --------------------------------------------------------- training index --
+
+TrainIndex train_index(gakco_ctx* c) {
+  Train& T = c->train;
+  TrainIndex tr{};
+  tr.ukey = (uint64_t*)T.ukey.p;
+  tr.ufirst = (uint32_t*)T.ufirst.p;
+  tr.eseq = (uint32_t*)T.eseq.p;
+  tr.nfeat = (uint32_t*)T.nfeat.p;
+  tr.diagC = (uint32_t*)T.diagC.p;
+  tr.rinv = (double*)T.rinv.p;
+  tr.stride = T.G + 1;
+  tr.n = (uint32_t)T.n;
+  return tr;
+}
+
+CrossParams cross_params(gakco_ctx* c, Work& w) {
+  CrossParams x{};
+  x.tr = train_index(c);
+  x.M = (uint32_t)c->M;
+  x.status = (uint32_t*)w.status.p;
+  memcpy(x.h, c->h, sizeof x.h);
+  memcpy(x.ie, c->ie, sizeof x.ie);
+  return x;
+}
+
+// Build the resident index of a training set (device codes, host offsets).
+int fit(gakco_ctx* c, const uint8_t* d_codes, const int64_t* off, int32_t n) {
+  Work& w = c->main;
+  Train& T = c->train;
+  T.ok = false;
+  Plan p;
+  int rc = plan_datasets(c, w, p, 1, &d_codes, &off, &n, nullptr, nullptr, nullptr, false);
+  if (rc != GAKCO_OK) return rc;
+  const DsHost& D = p.ds[0];
+  plan_chunks(c, p, false);
+  const uint64_t G = p.gtot, nm = c->masks.size(), stride = G + 1;
+  const uint64_t n1 = (uint64_t)std::max(n, 1);
+  ENSURE(fullkey, G * 8);
+  ENSURE(win2seq, G * 4);
+  ENSURE(ewin, nm * G * 4);
+  ENSURE(eseq, nm * G * 4);
+  ENSURE(efe, nm * G * 4);
+  if ((rc = ensure_sort_buffers(c, w, p)) != GAKCO_OK) return rc;
+  if ((rc = ensure(c, w, T.ukey, nm * stride * 8, "train keys")) != GAKCO_OK) return rc;
+  if ((rc = ensure(c, w, T.ufirst, nm * stride * 4, "train features")) != GAKCO_OK) return rc;
+  if ((rc = ensure(c, w, T.eseq, nm * stride * 4, "train entries")) != GAKCO_OK) return rc;
+  if ((rc = ensure(c, w, T.nfeat, nm * 4, "train feature counts")) != GAKCO_OK) return rc;
+  if ((rc = ensure(c, w, T.diagC, (uint64_t)(c->M + 1) * n1 * 4, "train diagonal")) != GAKCO_OK) return rc;
+  if ((rc = ensure(c, w, T.rinv, n1 * 8, "train norms")) != GAKCO_OK) return rc;
+  T.n = n;
+  T.G = G;
+  T.woff = D.woff;
+  Tables t;
+  add_common_tables(c, p, t);
+  if ((rc = ensure(c, w, w.tables, t.buf.size(), "tables")) != GAKCO_OK) return rc;
+  fill_records(c, w, p, t, true);
+  if ((rc = upload_tables(c, w, t)) != GAKCO_OK) return rc;
+  w.launches = 0;
+  uint8_t* base = (uint8_t*)w.tables.p;
+  uint32_t* status = (uint32_t*)w.status.p;
+  cudaMemsetAsync(status, 0, 128, w.cs);
+  cudaMemsetAsync(T.diagC.p, 0, (size_t)(c->M + 1) * n1 * 4, w.cs);
+  cudaMemsetAsync(T.nfeat.p, 0, nm * 4, w.cs);
+  cudaMemsetAsync(T.ufirst.p, 0, nm * stride * 4, w.cs);
+  launch_pack((const DsPack*)(base + p.o_pack), 1, p.nseq, c->g, c->bits, c->sigma,
+              (uint64_t*)w.fullkey.p, (uint32_t*)w.win2seq.p, status, w.cs);
+  const TrainIndex tr = train_index(c);
+  for (const Chunk& ch : p.chunks) enqueue_chunk(c, w, p, ch, Tail::kFit, &tr);
+  CrossParams x = cross_params(c, w);
+  launch_vec_diag(tr.diagC, (uint32_t)n, x, tr.rinv, w.cs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return wcuda(w, e, "kernel launch");
+  if ((rc = sync_and_check(c, w)) != GAKCO_OK) return rc;
+  T.ok = true;
+  return GAKCO_OK;
+}
+
+// Enqueue the cross kernel of one test batch on w (device codes, host
+// offsets; K / Khat device outputs of nt x n_train).  Does not wait.
+int enqueue_cross(gakco_ctx* c, Work& w, const uint8_t* d_codes, const int64_t* off, int32_t nt,
+                  int32_t* dK, double* dKhat) {
+  Train& T = c->train;
+  if (!T.ok) return wfail(w, GAKCO_E_INVALID, "no training set: call gakco_fit first");
+  uint64_t twmax = 1;
+  for (size_t y = 0; y + 1 < T.woff.size(); ++y) twmax = std::max<uint64_t>(twmax, T.woff[y + 1] - T.woff[y]);
+  Plan p;
+  int rc = plan_datasets(c, w, p, 1, &d_codes, &off, &nt, nullptr, nullptr, nullptr, false, twmax);
+  if (rc != GAKCO_OK) return rc;
+  const DsHost& D = p.ds[0];
+  plan_chunks(c, p, false);
+  const uint64_t G = p.gtot, nm = c->masks.size();
+  const uint32_t ntr = (uint32_t)T.n;
+  const uint32_t ncols = smem_columns(c, ntr);
+  add_items(c, p.items, 0, D.woff, (uint32_t)nt, ntr, ncols, 4.0 * (double)(T.G + 1) + 16.0 * (double)G,
+            false);
+  const size_t smem = 4 * ((size_t)ncols + 1);
+  ENSURE(fullkey, G * 8);
+  ENSURE(win2seq, G * 4);
+  ENSURE(ewin, nm * G * 4);
+  ENSURE(eseq, nm * G * 4);
+  ENSURE(ea, nm * G * 4);
+  ENSURE(eb, nm * G * 4);
+  if ((rc = ensure_sort_buffers(c, w, p)) != GAKCO_OK) return rc;
+  const uint64_t cd = (uint64_t)(c->M + 1) * std::max(nt, 1);
+  const uint64_t cx = cd * std::max<uint32_t>(ntr, 1);
+  ENSURE(Cd, cd * 4);
+  ENSURE(Cx, cx * 4);
+  ENSURE(rinv, (uint64_t)std::max(nt, 1) * 8);
+  Tables t;
+  add_common_tables(c, p, t);
+  if ((rc = ensure(c, w, w.tables, t.buf.size(), "tables")) != GAKCO_OK) return rc;
+  fill_records(c, w, p, t, true);
+  if ((rc = upload_tables(c, w, t)) != GAKCO_OK) return rc;
+  const int nb = cross_accum_blocks_per_sm(smem);
+  if (nb <= 0) return wfail(w, GAKCO_E_CUDA, "cross accumulation does not fit (%zu B shared)", smem);
+  uint8_t* base = (uint8_t*)w.tables.p;
+  uint32_t* status = (uint32_t*)w.status.p;
+  CrossParams x = cross_params(c, w);
+  x.xo.eseq = (uint32_t*)w.eseq.p;
+  x.xo.ea = (uint32_t*)w.ea.p;
+  x.xo.eb = (uint32_t*)w.eb.p;
+  x.xo.Cd = (uint32_t*)w.Cd.p;
+  x.xo.Cx = (uint32_t*)w.Cx.p;
+  x.xo.rinv = (double*)w.rinv.p;
+  x.xo.nt = (uint32_t)nt;
+  x.items = (const uint32_t*)(base + p.o_items);
+  x.nitems = (uint32_t)(p.items.size() / kItemWords);
+  x.counter = status + 8;
+  x.woff = (const uint32_t*)(base + p.o_woff[0]);
+  x.ewin = (const uint32_t*)w.ewin.p;
+  x.gt = G;
+  cudaMemsetAsync(status, 0, 128, w.cs);
+  cudaMemsetAsync(w.Cd.p, 0, cd * 4, w.cs);
+  cudaMemsetAsync(w.Cx.p, 0, cx * 4, w.cs);
+  launch_pack((const DsPack*)(base + p.o_pack), 1, p.nseq, c->g, c->bits, c->sigma,
+              (uint64_t*)w.fullkey.p, (uint32_t*)w.win2seq.p, status, w.cs);
+  const TrainIndex tr = x.tr;
+  for (const Chunk& ch : p.chunks) enqueue_chunk(c, w, p, ch, Tail::kCross, &tr, &x.xo);
+  launch_cross_accum(x, nb * c->nsm, smem, w.cs);
+  launch_vec_diag(x.xo.Cd, (uint32_t)nt, x, x.xo.rinv, w.cs);
+  launch_cross_combine(x, dK, dKhat, w.cs);
+  w.launches += 5;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return wcuda(w, e, "kernel launch");
+  return GAKCO_OK;
+}
+
+// Synchronous cross kernel on host buffers, on the context's Work.
+int cross_host(gakco_ctx* c, const uint8_t* codes, const int64_t* off, int32_t nt, int32_t* K,
+               double* Khat) {
+  Work& w = c->main;
+  int rc;
+  if (nt < 0 || nt > 65535) return wfail(w, GAKCO_E_INVALID, "nt = %d outside [0, 65535]", nt);
+  if (nt > 0 && !off) return wfail(w, GAKCO_E_INVALID, "null offsets");
+  if (!c->train.ok) return wfail(w, GAKCO_E_INVALID, "no training set: call gakco_fit first");
+  if (nt == 0) return GAKCO_OK;
+  const uint64_t cbytes = (uint64_t)off[nt];
+  const uint64_t nel = (uint64_t)nt * c->train.n;
+  ENSURE(codes, cbytes + 16);
+  ENSURE(outK, nel * 4 + 16);
+  ENSURE(outKhat, nel * 8 + 16);
+  cudaError_t e = cudaSuccess;
+  if (cbytes) e = cudaMemcpyAsync(w.codes.p, codes, cbytes, cudaMemcpyHostToDevice, w.cs);
+  if (e != cudaSuccess) return wcuda(w, e, "copy codes to device");
+  if ((rc = enqueue_cross(c, w, (const uint8_t*)w.codes.p, off, nt, (int32_t*)w.outK.p,
+                          (double*)w.outKhat.p)) != GAKCO_OK)
+    return rc;
+  if ((rc = sync_and_check(c, w)) != GAKCO_OK) return rc;
+  if (K && nel) e = cudaMemcpyAsync(K, w.outK.p, nel * 4, cudaMemcpyDeviceToHost, w.cs);
+  if (e == cudaSuccess && Khat && nel)
+    e = cudaMemcpyAsync(Khat, w.outKhat.p, nel * 8, cudaMemcpyDeviceToHost, w.cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(w.cs);
+  if (e != cudaSuccess) return wcuda(w, e, "copy results to host");
+  return GAKCO_OK;
+}
+
+// ---------------------------------------------------------------- serving --
+//
+// Requests are admitted into slots (a Work each: stream, device buffers,
+// pinned staging).  A free slot takes the longest prefix of the queue that
+// fits its limits (sequences, windows) as one micro-batch; the memory budget
+// holds a batch back while other slots are busy.  Each batch runs
+// asynchronously on its slot's stream and a host callback marks it done, so
+// several batches overlap on the device and requests that arrive meanwhile
+// are admitted as slots free up.  Results are exact integers and elementwise
+// fp64, so a request's rows do not depend on the batch it ran in.
+
+void CUDART_CB on_slot_done(void* arg) {
+  // Runs on a driver thread after the slot's copies: only raise the flag;
+  // the dispatcher polls it at least every 50 microseconds.
+  ((Slot*)arg)->gpu_done.store(true);
+}
+
+uint64_t req_windows(const gakco_ctx* c, const Request* r) {
+  uint64_t W = 0;
+  for (int32_t x = 0; x < r->nt; ++x) {
+    const int64_t len = r->off[x + 1] - r->off[x];
+    if (len >= c->g) W += (uint64_t)(len - c->g + 1);
+  }
+  return W;
+}
+
+// Launch one micro-batch on a slot (no lock held).
+int launch_batch(gakco_ctx* c, Slot& s) {
+  Work& w = s.w;
+  int rc;
+  std::vector<int64_t> off(1, 0);
+  size_t cbytes = 0;
+  s.row0.clear();
+  int32_t nt = 0;
+  for (Request* r : s.batch) {
+    s.row0.push_back(nt);
+    for (int32_t x = 0; x < r->nt; ++x) off.push_back(off.back() + (r->off[x + 1] - r->off[x]));
+    nt += r->nt;
+    cbytes += (size_t)(r->off[r->nt] - r->off[0]);
+  }
+  s.nt = nt;
+  const uint32_t ntr = (uint32_t)c->train.n;
+  const size_t nel = (size_t)nt * ntr;
+  s.k_off = align_up(cbytes, 256);
+  s.kh_off = align_up(s.k_off + nel * 4, 256);
+  if ((rc = ensure_pinned(w, w.h_io, w.h_io_cap, s.kh_off + nel * 8 + 256, "serve staging")) != GAKCO_OK)
+    return rc;
+  uint8_t* hio = (uint8_t*)w.h_io;
+  size_t pos = 0;
+  for (Request* r : s.batch) {
+    const size_t b = (size_t)(r->off[r->nt] - r->off[0]);
+    if (b) memcpy(hio + pos, r->codes.data() + r->off[0], b);
+    pos += b;
+  }
+  ENSURE(codes, cbytes + 16);
+  ENSURE(outK, nel * 4 + 16);
+  ENSURE(outKhat, nel * 8 + 16);
+  cudaError_t e = cudaSuccess;
+  if (cbytes) e = cudaMemcpyAsync(w.codes.p, hio, cbytes, cudaMemcpyHostToDevice, w.cs);
+  if (e != cudaSuccess) return wcuda(w, e, "copy codes to device");
+  if ((rc = enqueue_cross(c, w, (const uint8_t*)w.codes.p, off.data(), nt, (int32_t*)w.outK.p,
+                          (double*)w.outKhat.p)) != GAKCO_OK)
+    return rc;
+  e = cudaMemcpyAsync(hio + s.k_off, w.outK.p, nel * 4, cudaMemcpyDeviceToHost, w.cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hio + s.kh_off, w.outKhat.p, nel * 8, cudaMemcpyDeviceToHost, w.cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.h_status, w.status.p, 128, cudaMemcpyDeviceToHost, w.cs);
+  if (e == cudaSuccess) e = cudaLaunchHostFunc(w.cs, on_slot_done, &s);
+  if (e != cudaSuccess) return wcuda(w, e, "enqueue results");
+  return GAKCO_OK;
+}
+
+// Completion of a slot's batch (no lock held): check, then copy each
+// request's rows out of the pinned staging into the caller's buffers.
+int complete_batch(gakco_ctx* c, Slot& s) {
+  Work& w = s.w;
+  cudaError_t e = cudaStreamSynchronize(w.cs);  // returns at once: the callback ran
+  if (e != cudaSuccess) return wcuda(w, e, "serving batch");
+  int rc = check_status(c, w);
+  if (rc != GAKCO_OK) return rc;
+  const size_t ntr = (size_t)c->train.n;
+  const uint8_t* hio = (const uint8_t*)w.h_io;
+  for (size_t i = 0; i < s.batch.size(); ++i) {
+    Request* r = s.batch[i];
+    const size_t rows = (size_t)r->nt;
+    if (r->K) memcpy(r->K, hio + s.k_off + (size_t)s.row0[i] * ntr * 4, rows * ntr * 4);
+    if (r->Khat) memcpy(r->Khat, hio + s.kh_off + (size_t)s.row0[i] * ntr * 8, rows * ntr * 8);
+  }
+  return GAKCO_OK;
+}
+
+void finish_requests(gakco_ctx* c, Slot& s, int rc, const std::string& err) {
+  const double t = now_ms();
+  for (Request* r : s.batch) {
+    r->rc = rc;
+    r->err = err;
+    r->t_done = t;
+  }
+  c->served_batches += 1;
+  c->served_requests += (int64_t)s.batch.size();
+  s.batch.clear();
+  s.busy = false;
+  s.gpu_done.store(false);
+}
+
+void dispatcher_main(gakco_ctx* c) {
+  cudaSetDevice(c->device);
+  std::unique_lock<std::mutex> lk(c->mu);
+  for (;;) {
+    bool progressed = false;
+    // Completions.
+    for (auto& sp : c->slots) {
+      Slot& s = *sp;
+      if (s.busy && s.gpu_done.load()) {
+        lk.unlock();
+        const int rc = complete_batch(c, s);
+        lk.lock();
+        finish_requests(c, s, rc, rc == GAKCO_OK ? std::string() : s.w.err);
+        progressed = true;
+      }
+    }
+    if (progressed) c->cv.notify_all();
+    // Admissions.
+    for (auto& sp : c->slots) {
+      Slot& s = *sp;
+      if (s.busy || c->pending.empty()) continue;
+      size_t busy_bytes = 0;
+      bool any_busy = false;
+      for (auto& o : c->slots)
+        if (o->busy) {
+          busy_bytes += o->w.bytes();
+          any_busy = true;
+        }
+      int64_t seqs = 0, wins = 0;
+      std::vector<Request*> batch;
+      while (!c->pending.empty()) {
+        Request* r = c->pending.front();
+        if (!batch.empty() &&
+            (seqs + r->nt > c->serve_max_seqs || wins + (int64_t)r->windows > c->serve_max_windows))
+          break;
+        batch.push_back(r);
+        seqs += r->nt;
+        wins += (int64_t)r->windows;
+        c->pending.pop_front();
+      }
+      // Memory admission: estimated device bytes of this batch.
+      const double est = (double)wins * (double)c->masks.size() * 24.0 +
+                         (double)seqs * (double)c->train.n * (4.0 * (c->M + 1) + 12.0);
+      if (c->serve_mem_bytes > 0 && any_busy && (double)busy_bytes + est > (double)c->serve_mem_bytes) {
+        for (auto it = batch.rbegin(); it != batch.rend(); ++it) c->pending.push_front(*it);
+        break;  // wait for a slot to free memory
+      }
+      s.batch = batch;
+      s.busy = true;
+      s.gpu_done.store(false);
+      lk.unlock();
+      const int rc = launch_batch(c, s);
+      lk.lock();
+      if (rc != GAKCO_OK) {
+        finish_requests(c, s, rc, s.w.err);
+        c->cv.notify_all();
+      }
+      progressed = true;
+    }
+    if (c->stopping) {
+      bool busy = false;
+      for (auto& sp : c->slots) busy |= sp->busy;
+      if (!busy) break;
+    }
+    if (!progressed) c->cv.wait_for(lk, std::chrono::microseconds(50));
+  }
+}
+
+int start_serving(gakco_ctx* c) {
+  if (c->serving) return GAKCO_OK;
+  for (int i = 0; i < c->serve_slots; ++i) {
+    std::unique_ptr<Slot> s(new Slot());
+    if (init_work(s->w) != GAKCO_OK) return fail(c, GAKCO_E_CUDA, "serving slot: %s", s->w.err.c_str());
+    c->slots.push_back(std::move(s));
+  }
+  c->stopping = false;
+  c->dispatcher = std::thread(dispatcher_main, c);
+  c->serving = true;
+  return GAKCO_OK;
+}
+
+void stop_serving(gakco_ctx* c) {
+  if (!c->serving) return;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->stopping = true;
+    for (Request* r : c->pending) {
+      r->rc = GAKCO_E_INVALID;
+      r->err = "context destroyed before the request ran";
+    }
+    c->pending.clear();
+  }
+  c->cv.notify_all();
+  c->dispatcher.join();
+  for (auto& sp : c->slots) release_work(sp->w);
+  c->slots.clear();
+  for (auto& kv : c->requests) delete kv.second;
+  c->requests.clear();
+  c->serving = false;
 }
 
 }  // namespace
@@ -859,7 +1435,7 @@ int gakco_create(int sigma, int g, int k, gakco_ctx** out) {
     }
   }
   for (int m = 0; m <= M; ++m) {
-    c->h[m] = (uint32_t)binom(g - m, k);                       // Eq. 6
+    c->h[m] = (uint32_t)binom(g - m, k);                                       // Eq. 6
     for (int j = 0; j < m; ++j) c->ie[m][j] = (uint32_t)binom(g - j, m - j);  // Eq. 9
     c->maxC = std::max<uint32_t>(c->maxC, (uint32_t)binom(g, m));
   }
@@ -869,11 +1445,10 @@ int gakco_create(int sigma, int g, int k, gakco_ctx** out) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
   c->smem_optin = (size_t)v;
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMallocHost(&c->h_status, 128);
   if (e == cudaSuccess) e = (cudaError_t)prep_init();
+  if (e == cudaSuccess && init_work(c->main) != GAKCO_OK) e = cudaErrorMemoryAllocation;
   if (e != cudaSuccess) {
     cudaGetLastError();
     gakco_destroy(c);
@@ -885,20 +1460,16 @@ int gakco_create(int sigma, int g, int k, gakco_ctx** out) {
 
 void gakco_destroy(gakco_ctx* c) {
   if (!c) return;
-  if (c->cs) cudaStreamSynchronize(c->cs);
+  stop_serving(c);
+  if (c->main.cs) cudaStreamSynchronize(c->main.cs);
   drop_graph(c);
-  DevBuf* bufs[] = {&c->fullkey, &c->win2seq, &c->ewin, &c->eseq, &c->efe, &c->keyA,
-                    &c->keyB,    &c->valA,    &c->valB, &c->hist, &c->tcnt, &c->segtot,
-                    &c->estart,  &c->etseq,   &c->efid, &c->fstart, &c->tables, &c->codes,
-                    &c->outK,    &c->outKhat, &c->outNm, &c->rinv, &c->status, &c->Cplain,
-                    &c->Cacc};
-  for (DevBuf* b : bufs) release(*b);
+  release_work(c->main);
+  Train& T = c->train;
+  DevBuf* tb[] = {&T.ukey, &T.ufirst, &T.eseq, &T.nfeat, &T.diagC, &T.rinv};
+  for (DevBuf* b : tb) release(*b);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
-  if (c->h_tables) cudaFreeHost(c->h_tables);
-  if (c->h_status) cudaFreeHost(c->h_status);
-  if (c->cs) cudaStreamDestroy(c->cs);
   delete c;
 }
 
@@ -933,13 +1504,30 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
       if (v < 0) return fail(c, GAKCO_E_INVALID, "column cap must be >= 0");
       c->smem_cols = v;
       break;
+    case GAKCO_OPT_FAIL_ALLOC_AFTER:
+      if (v < 0) return fail(c, GAKCO_E_INVALID, "allocation countdown must be >= 0");
+      c->fail_alloc_after = v;
+      break;
     case GAKCO_OPT_GROUP_BYTES:
       if (v < 1) return fail(c, GAKCO_E_INVALID, "group bytes must be >= 1");
       c->group_bytes = v;
       break;
-    case GAKCO_OPT_FAIL_ALLOC_AFTER:
-      if (v < 0) return fail(c, GAKCO_E_INVALID, "allocation countdown must be >= 0");
-      c->fail_alloc_after = v;
+    case GAKCO_OPT_SERVE_SLOTS:
+      if (v < 1 || v > 16) return fail(c, GAKCO_E_INVALID, "serving slots must be 1..16");
+      if (c->serving) return fail(c, GAKCO_E_INVALID, "serving already started");
+      c->serve_slots = (int)v;
+      break;
+    case GAKCO_OPT_SERVE_MAX_SEQS:
+      if (v < 1 || v > 65535) return fail(c, GAKCO_E_INVALID, "batch sequences must be 1..65535");
+      c->serve_max_seqs = v;
+      break;
+    case GAKCO_OPT_SERVE_MAX_WINDOWS:
+      if (v < 1) return fail(c, GAKCO_E_INVALID, "batch windows must be >= 1");
+      c->serve_max_windows = v;
+      break;
+    case GAKCO_OPT_SERVE_MEM_BYTES:
+      if (v < 0) return fail(c, GAKCO_E_INVALID, "memory budget must be >= 0");
+      c->serve_mem_bytes = v;
       break;
     default:
       return fail(c, GAKCO_E_INVALID, "unknown option %d", key);
@@ -950,6 +1538,7 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
 
 int gakco_get_stat(const gakco_ctx* c, int key, double* v) {
   if (!c || !v) return GAKCO_E_INVALID;
+  gakco_ctx* cc = const_cast<gakco_ctx*>(c);
   switch (key) {
     case GAKCO_STAT_LAUNCHES:
       *v = (double)c->last_launches;
@@ -958,13 +1547,11 @@ int gakco_get_stat(const gakco_ctx* c, int key, double* v) {
       *v = (double)c->last_mask_passes;
       return GAKCO_OK;
     case GAKCO_STAT_DEVICE_BYTES: {
-      const DevBuf* bufs[] = {&c->fullkey, &c->win2seq, &c->ewin, &c->eseq, &c->efe, &c->keyA,
-                              &c->keyB,    &c->valA,    &c->valB, &c->hist, &c->tcnt, &c->segtot,
-                              &c->estart,  &c->etseq,   &c->efid, &c->fstart, &c->tables, &c->codes,
-                              &c->outK,    &c->outKhat, &c->outNm, &c->rinv, &c->status, &c->Cplain,
-                              &c->Cacc};
-      double s = 0;
-      for (const DevBuf* b : bufs) s += (double)b->cap;
+      double s = (double)cc->main.bytes();
+      const Train& T = c->train;
+      s += (double)(T.ukey.cap + T.ufirst.cap + T.eseq.cap + T.nfeat.cap + T.diagC.cap + T.rinv.cap);
+      std::lock_guard<std::mutex> lk(cc->mu);
+      for (auto& sp : cc->slots) s += (double)sp->w.bytes();
       *v = s;
       return GAKCO_OK;
     }
@@ -980,6 +1567,16 @@ int gakco_get_stat(const gakco_ctx* c, int key, double* v) {
     case GAKCO_STAT_WINDOWS_VISITED:
       *v = c->last_windows;
       return GAKCO_OK;
+    case GAKCO_STAT_SERVED_BATCHES: {
+      std::lock_guard<std::mutex> lk(cc->mu);
+      *v = (double)c->served_batches;
+      return GAKCO_OK;
+    }
+    case GAKCO_STAT_SERVED_REQUESTS: {
+      std::lock_guard<std::mutex> lk(cc->mu);
+      *v = (double)c->served_requests;
+      return GAKCO_OK;
+    }
   }
   return GAKCO_E_INVALID;
 }
@@ -998,7 +1595,7 @@ int gakco_gram(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32
                double* Khat, int32_t* Nm) {
   if (!c) return GAKCO_E_INVALID;
   c->err.clear();
-  return gram_host(c, 1, &codes, &offsets, &n, &K, &Khat, &Nm);
+  return ret(c, c->main, gram_host(c, 1, &codes, &offsets, &n, &K, &Khat, &Nm));
 }
 
 int gakco_gram_batch(gakco_ctx* c, int32_t nd, const uint8_t* const* codes,
@@ -1006,7 +1603,7 @@ int gakco_gram_batch(gakco_ctx* c, int32_t nd, const uint8_t* const* codes,
                      double* const* Khat, int32_t* const* Nm) {
   if (!c) return GAKCO_E_INVALID;
   c->err.clear();
-  return gram_host(c, nd, codes, offsets, n, K, Khat, Nm);
+  return ret(c, c->main, gram_host(c, nd, codes, offsets, n, K, Khat, Nm));
 }
 
 int gakco_gram_batch_device(gakco_ctx* c, int32_t nd, const uint8_t* const* codes,
@@ -1015,14 +1612,138 @@ int gakco_gram_batch_device(gakco_ctx* c, int32_t nd, const uint8_t* const* code
   if (!c) return GAKCO_E_INVALID;
   c->err.clear();
   Plan p;
-  int rc = plan_datasets(c, p, nd, codes, offsets, n, K, Khat, Nm, true);
-  if (rc != GAKCO_OK) return rc;
-  return run(c, p, (cudaStream_t)stream);
+  int rc = plan_datasets(c, c->main, p, nd, codes, offsets, n, K, Khat, Nm, true);
+  if (rc == GAKCO_OK) rc = run_gram(c, p, (cudaStream_t)stream);
+  return ret(c, c->main, rc);
 }
 
 int gakco_gram_device(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t n,
                       int32_t* K, double* Khat, int32_t* Nm, void* stream) {
   return gakco_gram_batch_device(c, 1, &codes, &offsets, &n, &K, &Khat, &Nm, stream);
+}
+
+int gakco_fit(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t n) {
+  if (!c) return GAKCO_E_INVALID;
+  c->err.clear();
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    bool busy = !c->pending.empty();
+    for (auto& sp : c->slots) busy |= sp->busy;
+    if (busy) return fail(c, GAKCO_E_INVALID, "requests are in flight; wait for them before fitting");
+  }
+  Work& w = c->main;
+  if (n < 0 || n > 65535 || (n > 0 && !offsets)) return fail(c, GAKCO_E_INVALID, "bad training set");
+  const uint64_t cbytes = n > 0 ? (uint64_t)offsets[n] : 0;
+  int rc = ensure(c, w, w.codes, cbytes + 16, "codes");
+  if (rc != GAKCO_OK) return ret(c, w, rc);
+  if (cbytes) {
+    cudaError_t e = cudaMemcpyAsync(w.codes.p, codes, cbytes, cudaMemcpyHostToDevice, w.cs);
+    if (e != cudaSuccess) return ret(c, w, wcuda(w, e, "copy codes to device"));
+  }
+  return ret(c, w, fit(c, (const uint8_t*)w.codes.p, offsets, n));
+}
+
+int gakco_fit_device(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t n,
+                     void* stream) {
+  if (!c) return GAKCO_E_INVALID;
+  c->err.clear();
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    bool busy = !c->pending.empty();
+    for (auto& sp : c->slots) busy |= sp->busy;
+    if (busy) return fail(c, GAKCO_E_INVALID, "requests are in flight; wait for them before fitting");
+  }
+  Work& w = c->main;
+  cudaError_t e = cudaEventRecord(c->ev_in, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(w.cs, c->ev_in, 0);
+  if (e != cudaSuccess) return ret(c, w, wcuda(w, e, "stream ordering"));
+  return ret(c, w, fit(c, codes, offsets, n));
+}
+
+int gakco_cross_fitted(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t nt,
+                       int32_t* K, double* Khat) {
+  if (!c) return GAKCO_E_INVALID;
+  c->err.clear();
+  return ret(c, c->main, cross_host(c, codes, offsets, nt, K, Khat));
+}
+
+int gakco_cross_fitted_device(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets,
+                              int32_t nt, int32_t* K, double* Khat, void* stream) {
+  if (!c) return GAKCO_E_INVALID;
+  c->err.clear();
+  Work& w = c->main;
+  if (nt < 0 || nt > 65535 || (nt > 0 && (!offsets || !K))) return fail(c, GAKCO_E_INVALID, "bad test batch");
+  if (nt == 0) return GAKCO_OK;
+  cudaError_t e = cudaEventRecord(c->ev_in, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(w.cs, c->ev_in, 0);
+  if (e != cudaSuccess) return ret(c, w, wcuda(w, e, "stream ordering"));
+  int rc = enqueue_cross(c, w, codes, offsets, nt, K, Khat);
+  if (rc == GAKCO_OK) rc = sync_and_check(c, w);
+  if (rc == GAKCO_OK) {
+    e = cudaEventRecord(c->ev_out, w.cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)stream, c->ev_out, 0);
+    if (e != cudaSuccess) rc = wcuda(w, e, "stream ordering");
+  }
+  return ret(c, w, rc);
+}
+
+int gakco_cross(gakco_ctx* c, const uint8_t* test_codes, const int64_t* test_off, int32_t nt,
+                const uint8_t* train_codes, const int64_t* train_off, int32_t ntr, int32_t* K,
+                double* Khat) {
+  int rc = gakco_fit(c, train_codes, train_off, ntr);
+  if (rc != GAKCO_OK) return rc;
+  return gakco_cross_fitted(c, test_codes, test_off, nt, K, Khat);
+}
+
+int gakco_submit(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t nt,
+                 int32_t* K, double* Khat, uint64_t* ticket) {
+  if (!c || !ticket) return GAKCO_E_INVALID;
+  if (nt < 1 || nt > 65535 || !offsets) return GAKCO_E_INVALID;
+  if (!c->train.ok) return GAKCO_E_INVALID;
+  std::unique_ptr<Request> r(new Request());
+  r->nt = nt;
+  r->off.assign(offsets, offsets + nt + 1);
+  for (int32_t x = 0; x < nt; ++x)
+    if (r->off[x] < 0 || r->off[x + 1] < r->off[x]) return GAKCO_E_INVALID;
+  if (r->off[nt] > 0 && !codes) return GAKCO_E_INVALID;
+  if (r->off[nt] > 0) r->codes.assign(codes, codes + r->off[nt]);
+  r->windows = req_windows(c, r.get());
+  r->K = K;
+  r->Khat = Khat;
+  r->t_submit = now_ms();
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (!c->serving) {
+    const int rc = start_serving(c);
+    if (rc != GAKCO_OK) return rc;
+  }
+  r->ticket = c->next_ticket++;
+  *ticket = r->ticket;
+  c->requests[r->ticket] = r.get();
+  c->pending.push_back(r.release());
+  c->cv.notify_all();
+  return GAKCO_OK;
+}
+
+int gakco_poll(gakco_ctx* c, uint64_t ticket, int timeout_ms, double* latency_ms) {
+  if (!c) return GAKCO_E_INVALID;
+  std::unique_lock<std::mutex> lk(c->mu);
+  auto it = c->requests.find(ticket);
+  if (it == c->requests.end()) return GAKCO_E_INVALID;
+  Request* r = it->second;
+  if (r->rc > 0 && timeout_ms != 0) {
+    auto done = [&] { return r->rc <= 0; };
+    if (timeout_ms < 0)
+      c->cv.wait(lk, done);
+    else
+      c->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), done);
+  }
+  if (r->rc > 0) return GAKCO_E_PENDING;
+  const int rc = r->rc;
+  if (latency_ms) *latency_ms = r->t_done - r->t_submit;
+  if (rc != GAKCO_OK) c->err = r->err;
+  c->requests.erase(it);
+  delete r;
+  return rc;
 }
 
 }  // extern "C"

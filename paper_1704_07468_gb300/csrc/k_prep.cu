@@ -529,19 +529,16 @@ void sort_pass_t(bool first, const SegDesc* segs, uint32_t nsegs,
 }
 
 template <typename KeyT>
-void rle_t(const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg,
-           uint32_t ntiles, const void* keys, const uint32_t* vals,
-           const uint32_t* win2seq, uint32_t* tcnt, uint32_t* segtot,
-           uint32_t* estart, uint32_t* etseq, uint32_t* efid,
-           uint32_t* fstart, uint32_t* ewin, uint32_t* eseq, uint32_t* efe,
-           cudaStream_t st) {
+void rle_head_t(const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg,
+                uint32_t ntiles, const void* keys, const uint32_t* vals,
+                const uint32_t* win2seq, uint32_t* tcnt, uint32_t* segtot,
+                uint32_t* estart, uint32_t* etseq, uint32_t* efid,
+                uint32_t* fstart, uint32_t* ewin, cudaStream_t st) {
   const KeyT* k = (const KeyT*)keys;
   k_rle_count<KeyT><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, k, vals, win2seq, tcnt);
   k_rle_scan<<<nsegs, kSortThreads, 0, st>>>(segs, tcnt, segtot);
   k_rle_emit<KeyT><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, k, vals, win2seq, tcnt,
                                                     estart, etseq, efid, fstart, ewin);
-  k_rle_final<<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, segtot, estart, etseq, efid,
-                                               fstart, eseq, efe);
 }
 
 }  // namespace
@@ -579,19 +576,39 @@ void launch_sort_pass(bool wide, bool first, const SegDesc* segs,
                           vout, hist, shift, rbits, st);
 }
 
+void launch_rle_head(bool wide, const SegDesc* segs, uint32_t nsegs,
+                     const uint32_t* tile_seg, uint32_t ntiles, const void* keys,
+                     const uint32_t* vals, const uint32_t* win2seq, uint32_t* tcnt,
+                     uint32_t* segtot, uint32_t* estart, uint32_t* etseq,
+                     uint32_t* efid, uint32_t* fstart, uint32_t* ewin, cudaStream_t st) {
+  if (ntiles == 0) return;
+  if (wide)
+    rle_head_t<uint64_t>(segs, nsegs, tile_seg, ntiles, keys, vals, win2seq, tcnt, segtot, estart,
+                         etseq, efid, fstart, ewin, st);
+  else
+    rle_head_t<uint32_t>(segs, nsegs, tile_seg, ntiles, keys, vals, win2seq, tcnt, segtot, estart,
+                         etseq, efid, fstart, ewin, st);
+}
+
+void launch_rle_final(const SegDesc* segs, const uint32_t* tile_seg, uint32_t ntiles,
+                      const uint32_t* segtot, const uint32_t* estart,
+                      const uint32_t* etseq, const uint32_t* efid,
+                      const uint32_t* fstart, uint32_t* eseq, uint32_t* efe,
+                      cudaStream_t st) {
+  if (ntiles == 0) return;
+  k_rle_final<<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, segtot, estart, etseq, efid,
+                                               fstart, eseq, efe);
+}
+
 void launch_rle(bool wide, const SegDesc* segs, uint32_t nsegs,
                 const uint32_t* tile_seg, uint32_t ntiles, const void* keys,
                 const uint32_t* vals, const uint32_t* win2seq, uint32_t* tcnt,
                 uint32_t* segtot, uint32_t* estart, uint32_t* etseq,
                 uint32_t* efid, uint32_t* fstart, uint32_t* ewin,
                 uint32_t* eseq, uint32_t* efe, cudaStream_t st) {
-  if (ntiles == 0) return;
-  if (wide)
-    rle_t<uint64_t>(segs, nsegs, tile_seg, ntiles, keys, vals, win2seq, tcnt, segtot, estart,
-                    etseq, efid, fstart, ewin, eseq, efe, st);
-  else
-    rle_t<uint32_t>(segs, nsegs, tile_seg, ntiles, keys, vals, win2seq, tcnt, segtot, estart,
-                    etseq, efid, fstart, ewin, eseq, efe, st);
+  launch_rle_head(wide, segs, nsegs, tile_seg, ntiles, keys, vals, win2seq, tcnt, segtot, estart,
+                  etseq, efid, fstart, ewin, st);
+  launch_rle_final(segs, tile_seg, ntiles, segtot, estart, etseq, efid, fstart, eseq, efe, st);
 }
 
 }  // namespace gk

@@ -84,6 +84,78 @@ void launch_combine(const DsInfo* d_ds, uint32_t nds, uint32_t ntiles,
                     const AccParams& coef, bool want_nm, bool want_khat,
                     cudaStream_t st);
 
+// Run-length pass split in two: count/scan/emit, and the final entry
+// packing of the Gram engine (launch_rle = both).
+void launch_rle_head(bool wide, const SegDesc* segs, uint32_t nsegs,
+                     const uint32_t* tile_seg, uint32_t ntiles, const void* keys,
+                     const uint32_t* vals, const uint32_t* win2seq,
+                     uint32_t* tcnt, uint32_t* segtot, uint32_t* estart,
+                     uint32_t* etseq, uint32_t* efid, uint32_t* fstart,
+                     uint32_t* ewin, cudaStream_t st);
+void launch_rle_final(const SegDesc* segs, const uint32_t* tile_seg, uint32_t ntiles,
+                      const uint32_t* segtot, const uint32_t* estart,
+                      const uint32_t* etseq, const uint32_t* efid,
+                      const uint32_t* fstart, uint32_t* eseq, uint32_t* efe,
+                      cudaStream_t st);
+
+// k_cross.cu ------------------------------------------------------------
+// Resident index of a training set: per mask (stride entries each) the
+// features' keys in ascending order, their first entries (+ one past the
+// last), and the entries; the per-level diagonal and 1/sqrt(K(y, y)).
+struct TrainIndex {
+  uint64_t* ukey;
+  uint32_t* ufirst;
+  uint32_t* eseq;
+  uint32_t* nfeat;      // features per mask
+  uint32_t* diagC;      // (M+1) x n: C_m(y, y)
+  double* rinv;         // n
+  uint64_t stride;      // windows of the training set + 1
+  uint32_t n;
+  uint32_t pad;
+};
+
+// Per test batch: entries per mask (stride = test windows), their joined
+// training ranges, the test diagonal and the cross accumulators.
+struct CrossOut {
+  uint32_t* eseq;
+  uint32_t* ea;
+  uint32_t* eb;
+  uint32_t* Cd;         // (M+1) x nt
+  uint32_t* Cx;         // (M+1) x nt x n_train
+  double* rinv;         // nt
+  uint32_t nt;
+  uint32_t pad;
+};
+
+struct CrossParams {
+  TrainIndex tr;
+  CrossOut xo;
+  const uint32_t* items;  // kItemWords per item (dataset word unused)
+  uint32_t nitems;
+  uint32_t* counter;
+  const uint32_t* woff;   // nt + 1 test window offsets
+  const uint32_t* ewin;   // masks x gt
+  uint64_t gt;            // test windows
+  uint32_t M;
+  uint32_t* status;
+  uint32_t h[kMaxLevels];
+  uint32_t ie[kMaxLevels][kMaxLevels];
+};
+
+void launch_train_index(bool wide, const SegDesc* segs, const uint32_t* tile_seg, uint32_t ntiles,
+                        const uint32_t* segtot, const void* keys, const uint32_t* estart,
+                        const uint32_t* fstart, const uint32_t* eseq, const uint32_t* mask_level,
+                        const TrainIndex& tr, cudaStream_t st);
+void launch_cross_final(bool wide, const SegDesc* segs, const uint32_t* tile_seg, uint32_t ntiles,
+                        const uint32_t* segtot, const void* keys, const uint32_t* estart,
+                        const uint32_t* etseq, const uint32_t* mask_level, const TrainIndex& tr,
+                        const CrossOut& xo, cudaStream_t st);
+int cross_accum_blocks_per_sm(size_t smem);
+void launch_cross_accum(const CrossParams& p, int blocks, size_t smem, cudaStream_t st);
+void launch_vec_diag(const uint32_t* Cd, uint32_t n, const CrossParams& p, double* rinv,
+                     cudaStream_t st);
+void launch_cross_combine(const CrossParams& p, int32_t* K, double* Khat, cudaStream_t st);
+
 // Plain per-mask path (Alg. 1 as written: countAndUpdate straight into the
 // global C_m with atomics, then inclusion-exclusion).
 void launch_pairs_global(const uint32_t* segtot_E, const uint32_t* eseq,
