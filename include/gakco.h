@@ -139,6 +139,21 @@ int gakco_kernel_timing(const gakco_ctx *ctx, int idx, char *name,
                         int name_len, double *total_ms, int64_t *launches);
 
 /*
+ * Autotuner: times the stages of gakco_gram_batch_device on the given
+ * datasets (device codes, host offsets) for a few values of the sort digit
+ * width (6, 8, 10 bits), the sort chunk size (2^22..2^26 elements), the
+ * accumulation block size (256, 512 threads) and the mask-group size
+ * (32..128 MiB), one parameter at a time, and sets the fastest on the
+ * context.  Results are cached per (sigma, g, k, SM count, size buckets)
+ * for the life of the process, so a second call for a similar workload
+ * returns at once.  `report` (may be NULL) receives the choice.  The
+ * options only change speed, never results.
+ */
+int gakco_autotune(gakco_ctx *ctx, int32_t ndata, const uint8_t *const *codes,
+                   const int64_t *const *offsets, const int32_t *n,
+                   void *stream, char *report, int report_len);
+
+/*
  * Gram kernel of one dataset, host buffers (Alg. 1 CALCULATEKERNEL).
  *   codes, offsets, n : the dataset (host)
  *   K      : n*n int32 kernel, or NULL

@@ -81,6 +81,7 @@ def load_library(build_if_missing: bool = False):
         "gakco_gram_batch": ([p, i32, p, p, p, p, p, p], ctypes.c_int),
         "gakco_gram_device": ([p, p, p, i32, p, p, p, p], ctypes.c_int),
         "gakco_gram_batch_device": ([p, i32, p, p, p, p, p, p, p], ctypes.c_int),
+        "gakco_autotune": ([p, i32, p, p, p, p, ctypes.c_char_p, ctypes.c_int], ctypes.c_int),
         "gakco_fit": ([p, p, p, i32], ctypes.c_int),
         "gakco_fit_device": ([p, p, p, i32, p], ctypes.c_int),
         "gakco_cross_fitted": ([p, p, p, i32, p, p], ctypes.c_int),
@@ -210,6 +211,18 @@ class Context:
             _ptr_array([o["Nm"].ctypes.data if o["Nm"] is not None else None for o in outs]))
         self._check(rc)
         return outs
+
+    def autotune_device(self, codes_ptrs, offsets, stream=None):
+        """Tune speed options on these datasets (device codes); returns the
+        library's report of the choice."""
+        offs = [np.ascontiguousarray(o, dtype=np.int64) for o in offsets]
+        ns = np.array([len(o) - 1 for o in offs], dtype=np.int32)
+        rep = ctypes.create_string_buffer(256)
+        self._check(self._lib.gakco_autotune(
+            self._h, len(offs), _ptr_array(codes_ptrs), _ptr_array([o.ctypes.data for o in offs]),
+            ns.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(stream) if stream else None,
+            rep, 256))
+        return rep.value.decode()
 
     # -- device-buffer calls ---------------------------------------------
     def gram_device(self, codes_ptr, offsets, K_ptr, Khat_ptr=None, Nm_ptr=None,

@@ -1373,6 +1373,134 @@ void stop_serving(gakco_ctx* c) {
   c->serving = false;
 }
 
+// -------------------------------------------------------------- autotuner --
+//
+// Picks the sort digit width, the sort chunk size, the accumulation block
+// size and the mask-group size for a workload by timing the stages they
+// drive (each candidate run once with per-kernel events), one parameter at
+// a time.  Choices are cached per (sigma, g, k, SM count, window and
+// sequence-count buckets) for the life of the process.
+
+struct TuneChoice {
+  int radix_bits;
+  int64_t chunk_elems;
+  int accum_threads;
+  int64_t group_bytes;
+};
+
+std::mutex g_tune_mu;
+std::unordered_map<uint64_t, TuneChoice> g_tune_cache;
+
+double stage_ms(gakco_ctx* c, const char* a, const char* b = nullptr) {
+  double t = 0;
+  for (auto& kv : c->timings)
+    if (kv.first == a || (b && kv.first == b)) t += kv.second.first;
+  return t;
+}
+
+int autotune(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64_t* const* off,
+             const int32_t* n, cudaStream_t user, std::string& report) {
+  Work& w = c->main;
+  uint64_t G = 0, nmax = 0, nn = 0;
+  for (int32_t d = 0; d < nd; ++d) {
+    nmax = std::max<uint64_t>(nmax, (uint64_t)n[d]);
+    nn += (uint64_t)n[d] * n[d];
+    for (int32_t x = 0; x < n[d]; ++x) {
+      const int64_t len = off[d][x + 1] - off[d][x];
+      if (len >= c->g) G += (uint64_t)(len - c->g + 1);
+    }
+  }
+  auto bucket = [](uint64_t v) {
+    int b = 0;
+    while (v > 1) {
+      v >>= 1;
+      ++b;
+    }
+    return (uint64_t)b;
+  };
+  const uint64_t key = ((uint64_t)c->sigma << 56) ^ ((uint64_t)c->g << 48) ^ ((uint64_t)c->k << 40) ^
+                       ((uint64_t)c->nsm << 28) ^ (bucket(G) << 20) ^ (bucket(nmax) << 12) ^ (uint64_t)nd;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      c->radix_bits = it->second.radix_bits;
+      c->chunk_elems = it->second.chunk_elems;
+      c->accum_threads = it->second.accum_threads;
+      c->group_bytes = it->second.group_bytes;
+      drop_graph(c);
+      report = "cached";
+      return GAKCO_OK;
+    }
+  }
+  int rc;
+  ENSURE(outK, nn * 4 + 16);
+  std::vector<int32_t*> Kp(nd);
+  uint64_t o = 0;
+  for (int32_t d = 0; d < nd; ++d) {
+    Kp[d] = (int32_t*)w.outK.p + o;
+    o += (uint64_t)n[d] * n[d];
+  }
+  const int saved_profile = c->profile, saved_engine = c->engine;
+  c->profile = 1;
+  c->engine = 0;
+  auto trial = [&](const char* s1, const char* s2, double& ms) -> int {
+    Plan p;
+    int r = plan_datasets(c, w, p, nd, codes, off, n, Kp.data(), nullptr, nullptr, true);
+    if (r == GAKCO_OK) r = run_gram(c, p, user);
+    ms = r == GAKCO_OK ? stage_ms(c, s1, s2) : 1e30;
+    return r;
+  };
+  char buf[256];
+  double best, t;
+  // Sort digit width (sort + run-length time).
+  int best_rb = c->radix_bits;
+  best = 1e30;
+  for (int rb : {6, 8, 10}) {
+    c->radix_bits = rb;
+    if ((rc = trial("sort_pass", "run_length", t)) != GAKCO_OK) break;
+    if (t < best) best = t, best_rb = rb;
+  }
+  c->radix_bits = best_rb;
+  // Sort chunk size.
+  int64_t best_ch = c->chunk_elems;
+  best = 1e30;
+  for (int64_t ch : {(int64_t)1 << 22, (int64_t)1 << 24, (int64_t)1 << 26}) {
+    if (rc != GAKCO_OK) break;
+    c->chunk_elems = ch;
+    if ((rc = trial("sort_pass", "run_length", t)) != GAKCO_OK) break;
+    if (t < best) best = t, best_ch = ch;
+  }
+  c->chunk_elems = best_ch;
+  // Accumulation block size and mask-group bytes.
+  int best_th = c->accum_threads;
+  int64_t best_gb = c->group_bytes;
+  best = 1e30;
+  for (int th : {256, 512}) {
+    for (int64_t gb : {(int64_t)32 << 20, (int64_t)64 << 20, (int64_t)128 << 20}) {
+      if (rc != GAKCO_OK) break;
+      c->accum_threads = th;
+      c->group_bytes = gb;
+      if ((rc = trial("accumulate", nullptr, t)) != GAKCO_OK) break;
+      if (t < best) best = t, best_th = th, best_gb = gb;
+    }
+  }
+  c->accum_threads = best_th;
+  c->group_bytes = best_gb;
+  c->profile = saved_profile;
+  c->engine = saved_engine;
+  drop_graph(c);
+  if (rc != GAKCO_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = {best_rb, best_ch, best_th, best_gb};
+  }
+  snprintf(buf, sizeof buf, "radix_bits=%d chunk_elems=%lld accum_threads=%d group_bytes=%lld", best_rb,
+           (long long)best_ch, best_th, (long long)best_gb);
+  report = buf;
+  return GAKCO_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ C ABI --
@@ -1620,6 +1748,18 @@ int gakco_gram_batch_device(gakco_ctx* c, int32_t nd, const uint8_t* const* code
 int gakco_gram_device(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t n,
                       int32_t* K, double* Khat, int32_t* Nm, void* stream) {
   return gakco_gram_batch_device(c, 1, &codes, &offsets, &n, &K, &Khat, &Nm, stream);
+}
+
+int gakco_autotune(gakco_ctx* c, int32_t nd, const uint8_t* const* codes,
+                   const int64_t* const* offsets, const int32_t* n, void* stream, char* report,
+                   int report_len) {
+  if (!c) return GAKCO_E_INVALID;
+  c->err.clear();
+  if (nd < 1 || !codes || !offsets || !n) return fail(c, GAKCO_E_INVALID, "autotune needs datasets");
+  std::string rep;
+  const int rc = autotune(c, nd, codes, offsets, n, (cudaStream_t)stream, rep);
+  if (report && report_len > 0) snprintf(report, (size_t)report_len, "%s", rep.c_str());
+  return ret(c, c->main, rc);
 }
 
 int gakco_fit(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t n) {
