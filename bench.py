@@ -68,6 +68,16 @@ def make_workload(name, rank=0, dna_sizes=None):
     raise SystemExit(f"unknown workload {name}")
 
 
+def reduce_max(value, device=None):
+    """Max of a float over all ranks (one all-reduce, outside timed regions)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -347,9 +357,7 @@ def run_ours(args):
     replay = int(ctx.get_stat("graph_replay"))
     pairs = ctx.get_stat("pair_updates")
     if ws > 1:
-        t = torch.tensor([step_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
+        step_ms = reduce_max(step_ms, dev)
         torch.distributed.barrier()
     value = entries * ws / (step_ms / 1000.0)
 

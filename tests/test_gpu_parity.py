@@ -182,3 +182,19 @@ def test_device_api_with_torch_buffers_and_stream():
     s.synchronize()
     ref = oracle.gram(codes, off, g, k)
     _check({"K": K.cpu().numpy(), "Nm": Nm.cpu().numpy(), "Khat": Kh.cpu().numpy()}, ref)
+
+
+def test_autotune_keeps_results_and_caches_its_choice():
+    import torch
+
+    sets = [synth.random_small(64 + i, n, 4, 80, 200) for i, n in enumerate([60, 90])]
+    dev = torch.device("cuda:0")
+    d_codes = [torch.from_numpy(c).to(dev) for c, _ in sets]
+    with pkg.gakco_create(4, 8, 5) as ctx:
+        rep = ctx.autotune_device([t.data_ptr() for t in d_codes], [o for _, o in sets])
+        assert "radix_bits=" in rep or rep == "cached"
+        outs = ctx.gram_batch(sets, khat=True, nm=True)
+    with pkg.gakco_create(4, 8, 5) as ctx:
+        assert ctx.autotune_device([t.data_ptr() for t in d_codes], [o for _, o in sets]) == "cached"
+    for (c, o), out in zip(sets, outs):
+        _check(out, oracle.gram(c, o, 8, 5))
