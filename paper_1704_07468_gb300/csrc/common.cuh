@@ -56,7 +56,7 @@ struct SegDesc {
   uint32_t mask;     // mask index
   uint32_t tile0;    // first tile (chunk-global numbering)
   uint32_t ntiles;
-  uint32_t pad;
+  uint32_t ds;       // dataset index (into the DsPack records)
 };
 
 // Per-dataset description used by the accumulation and finishing kernels.

@@ -101,7 +101,7 @@ double now_ms() {
 // Device buffers and stream of one pipeline instance.
 struct Work {
   cudaStream_t cs = nullptr;
-  DevBuf fullkey, win2seq, ewin, eseq, efe, keyA, keyB, valA, valB, hist, tcnt, segtot, estart,
+  DevBuf fullkey, wid, ewin, eseq, efe, keyA, keyB, valA, valB, hist, tcnt, segtot, estart,
       etseq, efid, fstart, tables, codes, outK, outKhat, outNm, rinv, status, Cplain, Cacc, ea, eb,
       Cd, Cx;
   void* h_tables = nullptr;
@@ -114,7 +114,7 @@ struct Work {
   double pairs = 0, entries = 0, windows = 0;
 
   std::vector<DevBuf*> all() {
-    return {&fullkey, &win2seq, &ewin,   &eseq,  &efe,  &keyA,  &keyB,  &valA,    &valB,
+    return {&fullkey, &wid, &ewin,   &eseq,  &efe,  &keyA,  &keyB,  &valA,    &valB,
             &hist,    &tcnt,    &segtot, &estart, &etseq, &efid, &fstart, &tables, &codes,
             &outK,    &outKhat, &outNm,  &rinv,  &status, &Cplain, &Cacc, &ea,    &eb,
             &Cd,      &Cx};
@@ -171,13 +171,13 @@ struct gakco_ctx {
   // options
   int engine = 0;
   int radix_bits = 8;
-  int64_t chunk_elems = (int64_t)1 << 24;
+  int64_t chunk_elems = (int64_t)1 << 26;
   int use_graph = 1;
-  int accum_threads = 512;
+  int accum_threads = 256;
   int profile = 0;
   int64_t smem_cols = 0;
   std::atomic<int64_t> fail_alloc_after{0};
-  int64_t group_bytes = (int64_t)64 << 20;
+  int64_t group_bytes = (int64_t)128 << 20;
   int serve_slots = 3;
   int64_t serve_max_seqs = 512;
   int64_t serve_max_windows = (int64_t)1 << 19;
@@ -400,6 +400,9 @@ int plan_datasets(gakco_ctx* c, Work& w, Plan& p, int32_t nd, const uint8_t* con
       if (D.off[x] < 0 || len < 0)
         return wfail(w, GAKCO_E_INVALID, "dataset %d: offsets must be non-negative and non-decreasing", d);
       const uint64_t W = len >= c->g ? (uint64_t)(len - c->g + 1) : 0;
+      if (W > 65535)
+        return wfail(w, GAKCO_E_OVERFLOW, "dataset %d: sequence %d has %llu windows (at most 65535)", d, x,
+                     (unsigned long long)W);
       wmax = std::max(wmax, W);
       acc += W;
       total += len;
@@ -473,6 +476,7 @@ void plan_chunks(gakco_ctx* c, Plan& p, bool plain) {
         s.mask = mu;
         s.tile0 = cur.ntiles;
         s.ntiles = (uint32_t)((D.G + kTile - 1) / kTile);
+        s.ds = (uint32_t)d;
         for (uint32_t t = 0; t < s.ntiles; ++t) p.tile_seg.push_back(cur.nseg);
         cur.ntiles += s.ntiles;
         cur.hist_elems += ((uint64_t)1 << rb) * s.ntiles;
@@ -673,10 +677,10 @@ int plan_memory_and_tables(gakco_ctx* c, Work& w, Plan& p, bool plain) {
   const uint64_t nm = c->masks.size();
   int rc;
   ENSURE(fullkey, G * 8);
-  ENSURE(win2seq, G * 4);
+  ENSURE(wid, G * 4);
   const uint64_t pool = plain ? G : nm * G;
   ENSURE(ewin, pool * 4);
-  ENSURE(eseq, pool * 4);
+  ENSURE(eseq, pool * 4 + 16);  // 16-byte vector reads may run past the last entry
   ENSURE(efe, pool * 4);
   if ((rc = ensure_sort_buffers(c, w, p)) != GAKCO_OK) return rc;
   uint64_t nsum = 0;
@@ -728,7 +732,7 @@ void enqueue_chunk(gakco_ctx* c, Work& w, const Plan& p, const Chunk& ch, Tail t
   void* kbuf[2] = {w.keyA.p, w.keyB.p};
   uint32_t* vbuf[2] = {(uint32_t*)w.valA.p, (uint32_t*)w.valB.p};
   void* kin = kbuf[1];  // the first pass extracts the masked keys here
-  uint32_t* vin = nullptr;
+  const uint32_t* vin = (const uint32_t*)w.wid.p;  // first-pass payload: window ids
   int cur = 0;
   for (size_t q = 0; q < ch.passes.size(); ++q) {
     Bracket b(c, w, "sort_pass", 3);
@@ -740,7 +744,7 @@ void enqueue_chunk(gakco_ctx* c, Work& w, const Plan& p, const Chunk& ch, Tail t
     cur ^= 1;
   }
   Bracket b(c, w, "run_length", tail == Tail::kFit ? 5 : 4);
-  launch_rle_head(ch.wide, segs, ch.nseg, tseg, ch.ntiles, kin, vin, (const uint32_t*)w.win2seq.p,
+  launch_rle_head(ch.wide, segs, ch.nseg, tseg, ch.ntiles, kin, vin, (const DsPack*)(base + p.o_pack),
                   (uint32_t*)w.tcnt.p, (uint32_t*)w.segtot.p, (uint32_t*)w.estart.p,
                   (uint32_t*)w.etseq.p, (uint32_t*)w.efid.p, (uint32_t*)w.fstart.p,
                   (uint32_t*)w.ewin.p, w.cs);
@@ -766,7 +770,7 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
   {
     Bracket b(c, w, "pack", 1);
     launch_pack((const DsPack*)(base + p.o_pack), (uint32_t)p.ds.size(), p.nseq, c->g, c->bits,
-                c->sigma, (uint64_t*)w.fullkey.p, (uint32_t*)w.win2seq.p, status, w.cs);
+                c->sigma, (uint64_t*)w.fullkey.p, (uint32_t*)w.wid.p, status, w.cs);
   }
   AccParams a = acc_params(c, w, p, status + 8);
   if (!plain) {
@@ -1030,7 +1034,7 @@ int fit(gakco_ctx* c, const uint8_t* d_codes, const int64_t* off, int32_t n) {
   const uint64_t G = p.gtot, nm = c->masks.size(), stride = G + 1;
   const uint64_t n1 = (uint64_t)std::max(n, 1);
   ENSURE(fullkey, G * 8);
-  ENSURE(win2seq, G * 4);
+  ENSURE(wid, G * 4);
   ENSURE(ewin, nm * G * 4);
   ENSURE(eseq, nm * G * 4);
   ENSURE(efe, nm * G * 4);
@@ -1057,7 +1061,7 @@ int fit(gakco_ctx* c, const uint8_t* d_codes, const int64_t* off, int32_t n) {
   cudaMemsetAsync(T.nfeat.p, 0, nm * 4, w.cs);
   cudaMemsetAsync(T.ufirst.p, 0, nm * stride * 4, w.cs);
   launch_pack((const DsPack*)(base + p.o_pack), 1, p.nseq, c->g, c->bits, c->sigma,
-              (uint64_t*)w.fullkey.p, (uint32_t*)w.win2seq.p, status, w.cs);
+              (uint64_t*)w.fullkey.p, (uint32_t*)w.wid.p, status, w.cs);
   const TrainIndex tr = train_index(c);
   for (const Chunk& ch : p.chunks) enqueue_chunk(c, w, p, ch, Tail::kFit, &tr);
   CrossParams x = cross_params(c, w);
@@ -1089,7 +1093,7 @@ int enqueue_cross(gakco_ctx* c, Work& w, const uint8_t* d_codes, const int64_t* 
             false);
   const size_t smem = 4 * ((size_t)ncols + 1);
   ENSURE(fullkey, G * 8);
-  ENSURE(win2seq, G * 4);
+  ENSURE(wid, G * 4);
   ENSURE(ewin, nm * G * 4);
   ENSURE(eseq, nm * G * 4);
   ENSURE(ea, nm * G * 4);
@@ -1127,7 +1131,7 @@ int enqueue_cross(gakco_ctx* c, Work& w, const uint8_t* d_codes, const int64_t* 
   cudaMemsetAsync(w.Cd.p, 0, cd * 4, w.cs);
   cudaMemsetAsync(w.Cx.p, 0, cx * 4, w.cs);
   launch_pack((const DsPack*)(base + p.o_pack), 1, p.nseq, c->g, c->bits, c->sigma,
-              (uint64_t*)w.fullkey.p, (uint32_t*)w.win2seq.p, status, w.cs);
+              (uint64_t*)w.fullkey.p, (uint32_t*)w.wid.p, status, w.cs);
   const TrainIndex tr = x.tr;
   for (const Chunk& ch : p.chunks) enqueue_chunk(c, w, p, ch, Tail::kCross, &tr, &x.xo);
   launch_cross_accum(x, nb * c->nsm, smem, w.cs);

@@ -114,7 +114,8 @@ k_accum(const AccParams p) {
       }
       n_pairs += cnt;
       n_ent += e != kNone;
-      // Long entry ranges: the whole warp walks one range at a time, four
+      // Long entry ranges: the whole warp walks one range at a time, lanes on
+      // consecutive entries (every atomic instruction fully populated), four
       // loads in flight per lane.  Column indices are clamped to the trash
       // slot acc[width]; anything landing there is reported after the item.
       uint32_t longm = __ballot_sync(kFull, cnt >= kLong);
@@ -135,20 +136,30 @@ k_accum(const AccParams p) {
         }
       }
       if (cnt >= kLong) cnt = 0;
-      // Short ranges: expand all pairs of the 32 lanes, 64 at a time.
-      uint32_t incl = cnt;
+      // Short ranges: up to four pairs per lane directly, the rest of the
+      // range by a warp-wide expansion.
+      {
+        const uint32_t s4 = min(cnt, 4u);
+        uint32_t v[4];
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += t;
+        for (int u = 0; u < 4; ++u) v[u] = (uint32_t)u < s4 ? es[lo + u] : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if ((uint32_t)u < s4) atomicAdd(&acc[min((v[u] >> 16) - c0, width)], c * (v[u] & 0xFFFFu));
+        lo += s4;
+        cnt -= s4;
       }
-      const uint32_t total = __shfl_sync(kFull, incl, 31);
-      const uint32_t excl = incl - cnt;
-      for (uint32_t p0 = 0; p0 < total; p0 += 64) {
-        uint32_t v[2], cw[2];
+      if (__any_sync(kFull, cnt != 0)) {
+        uint32_t incl = cnt;
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const uint32_t pp = p0 + 32 * u + lane;
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        const uint32_t excl = incl - cnt;
+        for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+          const uint32_t pp = p0 + lane;
           uint32_t o = 0;  // owner lane: first lane whose inclusive count > pp
 #pragma unroll
           for (int step = 16; step >= 1; step >>= 1) {
@@ -157,12 +168,12 @@ k_accum(const AccParams p) {
           }
           const uint32_t lo_o = __shfl_sync(kFull, lo, o);
           const uint32_t ex_o = __shfl_sync(kFull, excl, o);
-          cw[u] = __shfl_sync(kFull, c, o);
-          v[u] = pp < total ? es[lo_o + (pp - ex_o)] : kNone;
+          const uint32_t c_o = __shfl_sync(kFull, c, o);
+          if (pp < total) {
+            const uint32_t v = es[lo_o + (pp - ex_o)];
+            atomicAdd(&acc[min((v >> 16) - c0, width)], c_o * (v & 0xFFFFu));
+          }
         }
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-          if (v[u] != kNone) atomicAdd(&acc[min((v[u] >> 16) - c0, width)], cw[u] * (v[u] & 0xFFFFu));
       }
     }
     if (p.work) {

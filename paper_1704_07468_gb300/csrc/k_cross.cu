@@ -201,28 +201,43 @@ k_cross_accum(const CrossParams p) {
         }
       }
       if (cnt >= kLong) cnt = 0;
-      uint32_t incl = cnt;
+      // Short ranges: up to four pairs per lane directly, the rest by a
+      // warp-wide expansion.
+      {
+        const uint32_t s4 = min(cnt, 4u);
+        uint32_t v[4];
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += t;
+        for (int u = 0; u < 4; ++u) v[u] = (uint32_t)u < s4 ? tes[lo + u] : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if ((uint32_t)u < s4) atomicAdd(&acc[min((v[u] >> 16) - c0, width)], c * (v[u] & 0xFFFFu));
+        lo += s4;
+        cnt -= s4;
       }
-      const uint32_t total = __shfl_sync(kFull, incl, 31);
-      const uint32_t excl = incl - cnt;
-      for (uint32_t p0 = 0; p0 < total; p0 += 32) {
-        const uint32_t pp = p0 + lane;
-        uint32_t o = 0;
+      if (__any_sync(kFull, cnt != 0)) {
+        uint32_t incl = cnt;
 #pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-          const uint32_t t = __shfl_sync(kFull, incl, o + step - 1);
-          if (t <= pp) o += step;
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += t;
         }
-        const uint32_t lo_o = __shfl_sync(kFull, lo, o);
-        const uint32_t ex_o = __shfl_sync(kFull, excl, o);
-        const uint32_t c_o = __shfl_sync(kFull, c, o);
-        if (pp < total) {
-          const uint32_t v = tes[lo_o + (pp - ex_o)];
-          atomicAdd(&acc[min((v >> 16) - c0, width)], c_o * (v & 0xFFFFu));
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        const uint32_t excl = incl - cnt;
+        for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+          const uint32_t pp = p0 + lane;
+          uint32_t o = 0;
+#pragma unroll
+          for (int step = 16; step >= 1; step >>= 1) {
+            const uint32_t t = __shfl_sync(kFull, incl, o + step - 1);
+            if (t <= pp) o += step;
+          }
+          const uint32_t lo_o = __shfl_sync(kFull, lo, o);
+          const uint32_t ex_o = __shfl_sync(kFull, excl, o);
+          const uint32_t c_o = __shfl_sync(kFull, c, o);
+          if (pp < total) {
+            const uint32_t v = tes[lo_o + (pp - ex_o)];
+            atomicAdd(&acc[min((v >> 16) - c0, width)], c_o * (v & 0xFFFFu));
+          }
         }
       }
     }

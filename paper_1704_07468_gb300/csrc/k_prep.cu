@@ -23,12 +23,13 @@ constexpr int kWarps = kSortThreads / 32;
 // ---------------------------------------------------------------- packing --
 
 // One block per sequence.  Writes the full g-mer key of every window (first
-// symbol in the most significant bits, b bits per symbol) and the sequence
-// index of every window.  Symbols >= sigma raise kErrBadCode.
+// symbol in the most significant bits, b bits per symbol) and its window id
+// (sequence << 16 | position of the window in the sequence; both fit 16
+// bits, which the host checks).  Symbols >= sigma raise kErrBadCode.
 __global__ void __launch_bounds__(128)
 k_pack(const DsPack* __restrict__ ds, uint32_t nds, int g, int bits,
        int sigma, uint64_t* __restrict__ fullkey,
-       uint32_t* __restrict__ win2seq, uint32_t* __restrict__ status) {
+       uint32_t* __restrict__ wid, uint32_t* __restrict__ status) {
   const uint32_t gs = blockIdx.x;
   uint32_t d = 0;
   while (d + 1 < nds && ds[d + 1].seq0 <= gs) ++d;
@@ -49,7 +50,7 @@ k_pack(const DsPack* __restrict__ ds, uint32_t nds, int g, int bits,
     uint64_t key = 0;
     for (int p = 0; p < g; ++p) key = (key << bits) | s[i + p];
     fullkey[base + i] = key;
-    win2seq[base + i] = x;
+    wid[base + i] = (x << 16) | i;
   }
 }
 
@@ -228,7 +229,7 @@ k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
   for (int j = 0; j < kSortIpt; ++j) {
     const uint32_t idx = (uint32_t)w * 32 * kSortIpt + j * 32 + lane;
     keys[j] = idx < cnt ? kin[sd.base + beg + idx] : (KeyT)0;
-    vals[j] = idx < cnt ? (kFirst ? (uint32_t)(beg + idx) : vin[sd.base + beg + idx]) : 0u;
+    vals[j] = idx < cnt ? (kFirst ? vin[sd.win0 + beg + idx] : vin[sd.base + beg + idx]) : 0u;
   }
 #pragma unroll
   for (int j = 0; j < kSortIpt; ++j) {
@@ -302,7 +303,6 @@ __device__ __forceinline__ void rle_load_flags(const SegDesc& sd, uint64_t beg, 
                                                int w, int lane,
                                                const KeyT* __restrict__ keys,
                                                const uint32_t* __restrict__ vals,
-                                               const uint32_t* __restrict__ win2seq,
                                                uint32_t (&vv)[kSortIpt], uint32_t (&sq)[kSortIpt],
                                                uint32_t& ne_bits, uint32_t& nf_bits) {
   // Predecessor of the warp's first element.
@@ -311,7 +311,7 @@ __device__ __forceinline__ void rle_load_flags(const SegDesc& sd, uint64_t beg, 
   uint32_t s_prev = kNone;
   if (lane == 0 && first > 0 && first - beg < cnt) {
     k_prev = keys[sd.base + first - 1];
-    s_prev = win2seq[sd.win0 + vals[sd.base + first - 1]];
+    s_prev = vals[sd.base + first - 1] >> 16;
   }
   ne_bits = nf_bits = 0;
 #pragma unroll
@@ -323,7 +323,7 @@ __device__ __forceinline__ void rle_load_flags(const SegDesc& sd, uint64_t beg, 
     if (idx < cnt) {
       kj = keys[sd.base + beg + idx];
       vv[j] = vals[sd.base + beg + idx];
-      sq[j] = win2seq[sd.win0 + vv[j]];
+      sq[j] = vv[j] >> 16;
     }
     KeyT kp = __shfl_up_sync(0xffffffffu, kj, 1);
     uint32_t sp = __shfl_up_sync(0xffffffffu, sq[j], 1);
@@ -349,7 +349,7 @@ template <typename KeyT>
 __global__ void __launch_bounds__(kSortThreads)
 k_rle_count(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg,
             const KeyT* __restrict__ keys, const uint32_t* __restrict__ vals,
-            const uint32_t* __restrict__ win2seq, uint32_t* __restrict__ tcnt) {
+            uint32_t* __restrict__ tcnt) {
   __shared__ uint32_t sw[2][kWarps];
   const uint32_t t = blockIdx.x;
   const SegDesc sd = segs[tile_seg[t]];
@@ -358,7 +358,7 @@ k_rle_count(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
   const uint32_t cnt = (uint32_t)min((uint64_t)kTile, sd.G - beg);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t vv[kSortIpt], sq[kSortIpt], ne_bits, nf_bits;
-  rle_load_flags<KeyT>(sd, beg, cnt, w, lane, keys, vals, win2seq, vv, sq, ne_bits, nf_bits);
+  rle_load_flags<KeyT>(sd, beg, cnt, w, lane, keys, vals, vv, sq, ne_bits, nf_bits);
   uint32_t ce = __popc(ne_bits), cf = __popc(nf_bits);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -417,7 +417,7 @@ template <typename KeyT>
 __global__ void __launch_bounds__(kSortThreads, 3)
 k_rle_emit(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg,
            const KeyT* __restrict__ keys, const uint32_t* __restrict__ vals,
-           const uint32_t* __restrict__ win2seq, const uint32_t* __restrict__ tcnt,
+           const DsPack* __restrict__ dsp, const uint32_t* __restrict__ tcnt,
            uint32_t* __restrict__ estart, uint32_t* __restrict__ etseq,
            uint32_t* __restrict__ efid, uint32_t* __restrict__ fstart,
            uint32_t* __restrict__ ewin) {
@@ -430,8 +430,9 @@ k_rle_emit(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_s
   const uint32_t cnt = (uint32_t)min((uint64_t)kTile, sd.G - beg);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t lt_mask = lanemask_lt();
+  const uint32_t* __restrict__ woff = dsp[sd.ds].woff;
   uint32_t vv[kSortIpt], sq[kSortIpt], ne_bits, nf_bits;
-  rle_load_flags<KeyT>(sd, beg, cnt, w, lane, keys, vals, win2seq, vv, sq, ne_bits, nf_bits);
+  rle_load_flags<KeyT>(sd, beg, cnt, w, lane, keys, vals, vv, sq, ne_bits, nf_bits);
   uint32_t we = __popc(ne_bits), wf = __popc(nf_bits);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -460,7 +461,7 @@ k_rle_emit(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_s
       const uint32_t i = (uint32_t)(beg + idx);
       const uint32_t e = re + __popc(be & lt_mask) - (ne ? 0u : 1u);
       const uint32_t f = rf + __popc(bf & lt_mask) - (nf ? 0u : 1u);
-      ewin[sd.pool + vv[j]] = ne ? e : kNone;
+      ewin[sd.pool + woff[vv[j] >> 16] + (vv[j] & 0xFFFFu)] = ne ? e : kNone;
       if (ne) {
         estart[tb + e] = i;
         etseq[tb + e] = sq[j];
@@ -531,13 +532,13 @@ void sort_pass_t(bool first, const SegDesc* segs, uint32_t nsegs,
 template <typename KeyT>
 void rle_head_t(const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg,
                 uint32_t ntiles, const void* keys, const uint32_t* vals,
-                const uint32_t* win2seq, uint32_t* tcnt, uint32_t* segtot,
+                const DsPack* dsp, uint32_t* tcnt, uint32_t* segtot,
                 uint32_t* estart, uint32_t* etseq, uint32_t* efid,
                 uint32_t* fstart, uint32_t* ewin, cudaStream_t st) {
   const KeyT* k = (const KeyT*)keys;
-  k_rle_count<KeyT><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, k, vals, win2seq, tcnt);
+  k_rle_count<KeyT><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, k, vals, tcnt);
   k_rle_scan<<<nsegs, kSortThreads, 0, st>>>(segs, tcnt, segtot);
-  k_rle_emit<KeyT><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, k, vals, win2seq, tcnt,
+  k_rle_emit<KeyT><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, k, vals, dsp, tcnt,
                                                     estart, etseq, efid, fstart, ewin);
 }
 
@@ -555,10 +556,10 @@ int prep_init() {
 }
 
 void launch_pack(const DsPack* d_ds, uint32_t nds, uint32_t nseq_total, int g,
-                 int bits, int sigma, uint64_t* fullkey, uint32_t* win2seq,
+                 int bits, int sigma, uint64_t* fullkey, uint32_t* wid,
                  uint32_t* status, cudaStream_t st) {
   if (nseq_total == 0) return;
-  k_pack<<<nseq_total, 128, 0, st>>>(d_ds, nds, g, bits, sigma, fullkey, win2seq, status);
+  k_pack<<<nseq_total, 128, 0, st>>>(d_ds, nds, g, bits, sigma, fullkey, wid, status);
 }
 
 void launch_sort_pass(bool wide, bool first, const SegDesc* segs,
@@ -578,15 +579,15 @@ void launch_sort_pass(bool wide, bool first, const SegDesc* segs,
 
 void launch_rle_head(bool wide, const SegDesc* segs, uint32_t nsegs,
                      const uint32_t* tile_seg, uint32_t ntiles, const void* keys,
-                     const uint32_t* vals, const uint32_t* win2seq, uint32_t* tcnt,
+                     const uint32_t* vals, const DsPack* dsp, uint32_t* tcnt,
                      uint32_t* segtot, uint32_t* estart, uint32_t* etseq,
                      uint32_t* efid, uint32_t* fstart, uint32_t* ewin, cudaStream_t st) {
   if (ntiles == 0) return;
   if (wide)
-    rle_head_t<uint64_t>(segs, nsegs, tile_seg, ntiles, keys, vals, win2seq, tcnt, segtot, estart,
+    rle_head_t<uint64_t>(segs, nsegs, tile_seg, ntiles, keys, vals, dsp, tcnt, segtot, estart,
                          etseq, efid, fstart, ewin, st);
   else
-    rle_head_t<uint32_t>(segs, nsegs, tile_seg, ntiles, keys, vals, win2seq, tcnt, segtot, estart,
+    rle_head_t<uint32_t>(segs, nsegs, tile_seg, ntiles, keys, vals, dsp, tcnt, segtot, estart,
                          etseq, efid, fstart, ewin, st);
 }
 
@@ -602,11 +603,11 @@ void launch_rle_final(const SegDesc* segs, const uint32_t* tile_seg, uint32_t nt
 
 void launch_rle(bool wide, const SegDesc* segs, uint32_t nsegs,
                 const uint32_t* tile_seg, uint32_t ntiles, const void* keys,
-                const uint32_t* vals, const uint32_t* win2seq, uint32_t* tcnt,
+                const uint32_t* vals, const DsPack* dsp, uint32_t* tcnt,
                 uint32_t* segtot, uint32_t* estart, uint32_t* etseq,
                 uint32_t* efid, uint32_t* fstart, uint32_t* ewin,
                 uint32_t* eseq, uint32_t* efe, cudaStream_t st) {
-  launch_rle_head(wide, segs, nsegs, tile_seg, ntiles, keys, vals, win2seq, tcnt, segtot, estart,
+  launch_rle_head(wide, segs, nsegs, tile_seg, ntiles, keys, vals, dsp, tcnt, segtot, estart,
                   etseq, efid, fstart, ewin, st);
   launch_rle_final(segs, tile_seg, ntiles, segtot, estart, etseq, efid, fstart, eseq, efe, st);
 }

@@ -21,12 +21,13 @@ struct DsPack {
 int prep_init();  // one-time kernel attributes; returns a cudaError_t
 void launch_pack(const DsPack* d_ds, uint32_t nds, uint32_t nseq_total,
                  int g, int bits, int sigma, uint64_t* fullkey,
-                 uint32_t* win2seq, uint32_t* status, cudaStream_t st);
+                 uint32_t* wid, uint32_t* status, cudaStream_t st);
 
 // One LSD radix-sort pass over every segment of a chunk.  For the first
 // pass the keys are cut out of the full g-mer keys (`fullkey`) into `kin`
-// (which must not alias `kout`) and the payload is the dataset-local window
-// index (`vin` unused); later passes read kin/vin.
+// (which must not alias `kout`) and the payload is the window id read from
+// `vin` (the packing kernel's output, indexed by global window); later
+// passes read kin/vin.
 void launch_sort_pass(bool wide, bool first, const SegDesc* segs,
                       uint32_t nsegs, const uint32_t* tile_seg,
                       uint32_t ntiles, const MaskDesc* masks,
@@ -39,7 +40,7 @@ void launch_sort_pass(bool wide, bool first, const SegDesc* segs,
 // efe into the pools.
 void launch_rle(bool wide, const SegDesc* segs, uint32_t nsegs,
                 const uint32_t* tile_seg, uint32_t ntiles, const void* keys,
-                const uint32_t* vals, const uint32_t* win2seq,
+                const uint32_t* vals, const DsPack* dsp,
                 uint32_t* tcnt, uint32_t* segtot, uint32_t* estart,
                 uint32_t* etseq, uint32_t* efid, uint32_t* fstart,
                 uint32_t* ewin, uint32_t* eseq, uint32_t* efe,
@@ -88,7 +89,7 @@ void launch_combine(const DsInfo* d_ds, uint32_t nds, uint32_t ntiles,
 // packing of the Gram engine (launch_rle = both).
 void launch_rle_head(bool wide, const SegDesc* segs, uint32_t nsegs,
                      const uint32_t* tile_seg, uint32_t ntiles, const void* keys,
-                     const uint32_t* vals, const uint32_t* win2seq,
+                     const uint32_t* vals, const DsPack* dsp,
                      uint32_t* tcnt, uint32_t* segtot, uint32_t* estart,
                      uint32_t* etseq, uint32_t* efid, uint32_t* fstart,
                      uint32_t* ewin, cudaStream_t st);

@@ -143,6 +143,7 @@ extern "C" int gakco_gram_device_noalloc(int sigma, int g, int k, const uint8_t*
     if (offsets[x] < 0 || len < 0)
       return set_err(err, err_len, GAKCO_E_INVALID, "offsets must be non-negative and non-decreasing");
     const uint64_t W = len >= g ? (uint64_t)(len - g + 1) : 0;
+    if (W > 65535) return set_err(err, err_len, GAKCO_E_OVERFLOW, "a sequence has more than 65535 windows");
     if (W > wmax) wmax = W;
     G += W;
   }
@@ -180,7 +181,7 @@ extern "C" int gakco_gram_device_noalloc(int sigma, int g, int k, const uint8_t*
     return set_err(err, err_len, GAKCO_E_OVERFLOW, "input too large for this entry point's table area (1 MiB)");
   const size_t o_tables = take(t);
   const size_t o_fullkey = take(G * 8);
-  const size_t o_win2seq = take(G * 4);
+  const size_t o_wid = take(G * 4);
   const size_t o_ewin = take(G * 4);
   const size_t o_eseq = take(G * 4);
   const size_t o_efe = take(G * 4);
@@ -244,6 +245,7 @@ extern "C" int gakco_gram_device_noalloc(int sigma, int g, int k, const uint8_t*
     s.mask = (uint32_t)mu;
     s.tile0 = 0;
     s.ntiles = ntiles;
+    s.ds = 0;
     segs[mu] = s;
   }
   memset(h_tables + t_tiles, 0, (size_t)ntiles * 4 + 4);  // every tile is segment 0
@@ -293,7 +295,7 @@ extern "C" int gakco_gram_device_noalloc(int sigma, int g, int k, const uint8_t*
   }
   uint32_t* status = (uint32_t*)(S + o_status);
   launch_pack((const DsPack*)(S + o_tables + t_pack), 1, (uint32_t)n, g, bits, sigma,
-              (uint64_t*)(S + o_fullkey), (uint32_t*)(S + o_win2seq), status, st);
+              (uint64_t*)(S + o_fullkey), (uint32_t*)(S + o_wid), status, st);
   const SegDesc* d_segs = (const SegDesc*)(S + o_tables + t_segs);
   const uint32_t* d_tiles = (const uint32_t*)(S + o_tables + t_tiles);
   const MaskDesc* d_masks = (const MaskDesc*)(S + o_tables + t_masks);
@@ -307,7 +309,7 @@ extern "C" int gakco_gram_device_noalloc(int sigma, int g, int k, const uint8_t*
       void* kbuf[2] = {S + o_keyA, S + o_keyB};
       uint32_t* vbuf[2] = {(uint32_t*)(S + o_valA), (uint32_t*)(S + o_valB)};
       void* kin = kbuf[1];  // the first pass extracts the masked keys here
-      const uint32_t* vin = nullptr;
+      const uint32_t* vin = (const uint32_t*)(S + o_wid);  // first-pass payload: window ids
       int cur = 0;
       for (int q = 0; q < np; ++q) {
         const int shift = q * rb;
@@ -319,7 +321,7 @@ extern "C" int gakco_gram_device_noalloc(int sigma, int g, int k, const uint8_t*
         vin = vbuf[cur];
         cur ^= 1;
       }
-      launch_rle(w, d_segs + mu, 1, d_tiles, ntiles, kin, vin, (const uint32_t*)(S + o_win2seq),
+      launch_rle(w, d_segs + mu, 1, d_tiles, ntiles, kin, vin, (const DsPack*)(S + o_tables + t_pack),
                  (uint32_t*)(S + o_tcnt), (uint32_t*)(S + o_segtot), (uint32_t*)(S + o_estart),
                  (uint32_t*)(S + o_etseq), (uint32_t*)(S + o_efid), (uint32_t*)(S + o_fstart),
                  (uint32_t*)(S + o_ewin), (uint32_t*)(S + o_eseq), (uint32_t*)(S + o_efe), st);

@@ -190,3 +190,18 @@ def test_protein_serving_full_size_sampled():
         ref = oracle.cross(c, o, tr[0], tr[1], 8, 4, rows=rows, threads=len(rows))
         np.testing.assert_array_equal(out["K"][rows], ref["K"])
         assert _close(out["Khat"][rows], ref["Khat"])
+
+
+def test_sequence_window_limit_on_the_cross_path():
+    """Counts and window positions are 16-bit fields: a test sequence with
+    more than 65535 windows is rejected even where the int32 bound (which
+    multiplies by the short training sequences) would allow it."""
+    tr = synth.pack([np.zeros(6, np.uint8), np.ones(7, np.uint8)])
+    te = synth.pack([np.zeros(70000, np.uint8)])
+    with pkg.gakco_create(4, 4, 3) as ctx:
+        ctx.fit(*tr)
+        with pytest.raises(pkg.GakcoError) as ei:
+            ctx.cross_fitted(*te)
+        assert ei.value.name == "GAKCO_E_OVERFLOW"
+        ok = ctx.cross_fitted(*synth.pack([np.zeros(60, np.uint8)]))
+        assert ok["K"].shape == (1, 2)
