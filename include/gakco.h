@@ -108,6 +108,17 @@ const char *gakco_last_error(const gakco_ctx *ctx);
 #define GAKCO_OPT_SERVE_MAX_SEQS 11 /* serving: test sequences per micro-batch (default 512) */
 #define GAKCO_OPT_SERVE_MAX_WINDOWS 12 /* serving: test windows per micro-batch (default 2^19) */
 #define GAKCO_OPT_SERVE_MEM_BYTES 13 /* serving: device-memory budget of busy slots (0 = none) */
+/* Dense levels (batched Gram engine only).  For a level m whose masked
+ * keys have at most 16 bits, and a dataset in which no sequence has more
+ * than 511 windows, countAndUpdate (Section 2.2, Alg. 1) can run as a
+ * dense contraction C_m += A A^T on the tensor cores, A holding the count
+ * of every (mask, (g-m)-mer) per sequence.  Results are identical (exact
+ * integer arithmetic).  0 = never (default), 1 = where a cost model
+ * expects it to be faster, 2 = every qualifying level. */
+#define GAKCO_OPT_DENSE 14
+#define GAKCO_OPT_DENSE_BYTES 15    /* device bytes of the A matrices of one dense wave
+                                       (default 2 GiB); a level whose one-mask A exceeds
+                                       it stays sparse */
 int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 
 /*
@@ -128,6 +139,8 @@ int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 #define GAKCO_STAT_WINDOWS_VISITED 7  /* batched engine: (window, mask) slots read */
 #define GAKCO_STAT_SERVED_BATCHES 8   /* serving: micro-batches completed so far */
 #define GAKCO_STAT_SERVED_REQUESTS 9  /* serving: requests completed so far */
+#define GAKCO_STAT_DENSE_PROBLEMS 10  /* Gram: (dataset, level, mask run) contractions on the tensor cores */
+#define GAKCO_STAT_DENSE_FLOPS 11     /* Gram: tensor-core flops issued (2 per multiply-add, padding included) */
 int gakco_get_stat(const gakco_ctx *ctx, int key, double *value);
 
 /*

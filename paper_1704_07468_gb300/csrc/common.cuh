@@ -79,6 +79,7 @@ enum : uint32_t {
   kErrKneCM = 1u,          // sum_m h_m N_m != C_M (must never happen)
   kErrBadEntry = 2u,       // entry index out of range
   kErrBadCode = 4u,        // a symbol >= sigma in the input
+  kErrTimeout = 8u,        // a bounded wait in a pipelined kernel ran out
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {

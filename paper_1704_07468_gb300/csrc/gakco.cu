@@ -103,7 +103,7 @@ struct Work {
   cudaStream_t cs = nullptr;
   DevBuf fullkey, wid, ewin, eseq, efe, keyA, keyB, valA, valB, hist, tcnt, segtot, estart,
       etseq, efid, fstart, tables, codes, outK, outKhat, outNm, rinv, status, Cplain, Cacc, ea, eb,
-      Cd, Cx;
+      Cd, Cx, Adense, dmaxc;
   void* h_tables = nullptr;
   size_t h_tables_cap = 0;
   void* h_status = nullptr;
@@ -117,7 +117,7 @@ struct Work {
     return {&fullkey, &wid, &ewin,   &eseq,  &efe,  &keyA,  &keyB,  &valA,    &valB,
             &hist,    &tcnt,    &segtot, &estart, &etseq, &efid, &fstart, &tables, &codes,
             &outK,    &outKhat, &outNm,  &rinv,  &status, &Cplain, &Cacc, &ea,    &eb,
-            &Cd,      &Cx};
+            &Cd,      &Cx,      &Adense, &dmaxc};
   }
   size_t bytes() {
     size_t s = 0;
@@ -182,6 +182,8 @@ struct gakco_ctx {
   int64_t serve_max_seqs = 512;
   int64_t serve_max_windows = (int64_t)1 << 19;
   int64_t serve_mem_bytes = 0;  // 0: no budget
+  int dense = 0;                            // 0 off, 1 cost model, 2 every eligible level
+  int64_t dense_bytes = (int64_t)2 << 30;   // A matrices per dense wave
 
   std::string err;
   int device = 0;
@@ -196,6 +198,8 @@ struct gakco_ctx {
   int64_t last_launches = 0, last_mask_passes = 0;
   int last_replay = 0;
   double last_pairs = 0, last_entries = 0, last_windows = 0;
+  double last_dense_probs = 0, last_dense_flops = 0;
+  double plan_dense_probs = 0, plan_dense_flops = 0;  // of the last plan (kept for graph replays)
   std::vector<Timed> timed;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -346,6 +350,19 @@ struct Bracket {
   }
 };
 
+// One dense problem (see DenseProb) before its device addresses are known.
+struct DenseHost {
+  uint32_t ds, level, mfirst, mcount, n, n_pad, key_bits, row0;
+  uint64_t ld, a_off;  // columns; element offset of A in the A buffer
+};
+
+struct DenseWave {
+  uint32_t p0, np;       // problems
+  uint32_t t0, nt;       // tiles
+  uint32_t rows, colblocks;
+  uint64_t elems;        // A elements of the wave
+};
+
 struct Plan {
   std::vector<DsHost> ds;
   uint64_t gtot = 0;
@@ -364,9 +381,21 @@ struct Plan {
   uint64_t c_elems = 0;
   std::vector<uint32_t> seg_ds;  // dataset of each segment
   bool want_nm = false, want_khat = false;
+  // Dense (tensor-core) levels: flags per (dataset, level), problems,
+  // waves of problems whose A matrices share the A buffer, GEMM tiles.
+  std::vector<uint8_t> dense;
+  std::vector<DenseHost> dprobs;
+  std::vector<DenseWave> dwaves;
+  std::vector<uint32_t> dtiles;
+  uint64_t dense_abytes = 0;
+  double dense_flops = 0;
   // device table offsets
-  size_t o_masks, o_level, o_pack, o_info, o_segs, o_tiles, o_items;
+  size_t o_masks, o_level, o_pack, o_info, o_segs, o_tiles, o_items, o_dprobs = 0, o_dtiles = 0, o_tmaps = 0;
   std::vector<size_t> o_coff, o_woff;
+
+  bool is_dense(size_t d, int m, int M) const {
+    return !dense.empty() && dense[d * (size_t)(M + 1) + (size_t)m];
+  }
 };
 
 // Validate datasets and compute window offsets; fills p.ds.  `maxw_other`
@@ -462,7 +491,7 @@ void plan_chunks(gakco_ctx* c, Plan& p, bool plain) {
       if ((int)c->mask_level[mu] != m) continue;
       for (size_t d = 0; d < p.ds.size(); ++d) {
         const DsHost& D = p.ds[d];
-        if (D.G == 0) continue;
+        if (D.G == 0 || p.is_dense(d, m, c->M)) continue;
         if (cur.nseg > 0 && (plain || cur.elems + D.G > limit)) {
           flush();
           fresh();
@@ -512,7 +541,7 @@ uint32_t smem_columns(gakco_ctx* c, uint32_t n) {
 // only columns y >= x (Gram); `ncols_total` is the column count.
 void add_items(gakco_ctx* c, std::vector<uint32_t>& items, uint32_t d, const std::vector<uint32_t>& woff,
                uint32_t nrows, uint32_t ncols_total, uint32_t ncols, double per_mask_bytes,
-               bool triangle) {
+               bool triangle, const Plan* skip = nullptr) {
   struct Row {
     double cost;
     uint32_t x, c0, c1;
@@ -533,6 +562,7 @@ void add_items(gakco_ctx* c, std::vector<uint32_t>& items, uint32_t d, const std
   const uint32_t gmax =
       (uint32_t)std::max(1.0, std::floor((double)c->group_bytes / std::max(per_mask_bytes, 1.0)));
   for (int m = 0; m <= c->M; ++m) {
+    if (skip && skip->is_dense(d, m, c->M)) continue;  // done on the tensor cores
     const uint32_t mf = lf[m], mc = lf[m + 1] - lf[m];
     const uint32_t ng = (mc + gmax - 1) / gmax;
     for (uint32_t gi = 0; gi < ng; ++gi) {
@@ -555,20 +585,120 @@ void plan_items(gakco_ctx* c, Plan& p) {
     const DsHost& D = p.ds[d];
     if (D.n == 0) continue;
     add_items(c, p.items, (uint32_t)d, D.woff, (uint32_t)D.n, (uint32_t)D.n, ncols,
-              12.0 * (double)std::max<uint64_t>(D.G, 1), true);
+              12.0 * (double)std::max<uint64_t>(D.G, 1), true, &p);
   }
+}
+
+// Per-mask time estimates (seconds) of one level of one dataset on the
+// sparse route (sort, run-length, pair updates) and on the dense route
+// (scatter into A, tensor-core GEMM), from effective rates of the kernels.
+bool dense_is_cheaper(gakco_ctx* c, const DsHost& D, uint32_t n_pad, int kb) {
+  const double hbm = 6.0e12, updates = 1.0e12, tensor = 1.0e15;
+  const double G = (double)D.G, S = std::ldexp(1.0, kb);
+  const double passes = std::ceil((double)kb / (double)c->radix_bits);
+  const double sparse = G * (passes * 16.0 + 48.0) / hbm + 0.5 * (G * G / S + G) / updates;
+  const double rb = n_pad / 128.0, cb = std::ceil(n_pad / 256.0);
+  const double tiles = rb * cb - std::floor(rb / 2.0) * std::ceil(rb / 2.0);
+  const double dense = tiles * 128.0 * 256.0 * 2.0 * std::max(S, 64.0) / tensor + 4.0 * n_pad * S / hbm;
+  return dense < sparse;
+}
+
+// Marks the (dataset, level) pairs that run on the tensor cores and cuts
+// them into problems (runs of masks whose A fits the wave budget), waves
+// and upper-triangle output tiles.  A level qualifies when every count is
+// at most kDenseMaxCount (no sequence has more windows), its masked keys
+// have at most 16 bits, and one mask's A fits the budget.
+void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
+  const int L = c->M + 1;
+  p.dense.assign(p.ds.size() * (size_t)L, 0);
+  p.dprobs.clear();
+  p.dwaves.clear();
+  p.dtiles.clear();
+  p.dense_abytes = 0;
+  p.dense_flops = 0;
+  if (plain || c->dense == 0) return;
+  const std::vector<uint32_t> lf = level_firsts(c);
+  const uint64_t budget = (uint64_t)std::max<int64_t>(c->dense_bytes, 1);
+  for (size_t d = 0; d < p.ds.size(); ++d) {
+    const DsHost& D = p.ds[d];
+    if (D.n == 0 || D.G == 0) continue;
+    uint32_t wmax = 0;
+    for (int32_t x = 0; x < D.n; ++x) wmax = std::max(wmax, D.woff[x + 1] - D.woff[x]);
+    if (wmax > kDenseMaxCount) continue;
+    const uint32_t n_pad = (uint32_t)align_up((size_t)D.n, 128);
+    for (int m = 0; m <= c->M; ++m) {
+      const int kb = c->bits * (c->g - m);
+      if (kb > 16) continue;
+      const uint64_t S = (uint64_t)1 << kb;
+      const uint64_t per_mask = (uint64_t)n_pad * S * 2;
+      if (per_mask > budget) continue;
+      if (c->dense == 1 && !dense_is_cheaper(c, D, n_pad, kb)) continue;
+      p.dense[d * L + m] = 1;
+      const uint32_t mf = lf[m], mc = lf[m + 1] - lf[m];
+      const uint32_t gmax = (uint32_t)std::min<uint64_t>(mc, std::max<uint64_t>(1, budget / per_mask));
+      const uint32_t ng = (mc + gmax - 1) / gmax;
+      for (uint32_t gi = 0; gi < ng; ++gi) {
+        const uint32_t a = mf + (uint32_t)((uint64_t)mc * gi / ng);
+        const uint32_t b = mf + (uint32_t)((uint64_t)mc * (gi + 1) / ng);
+        DenseHost h{};
+        h.ds = (uint32_t)d;
+        h.level = (uint32_t)m;
+        h.mfirst = a;
+        h.mcount = b - a;
+        h.n = (uint32_t)D.n;
+        h.n_pad = n_pad;
+        h.key_bits = (uint32_t)kb;
+        h.ld = align_up((size_t)h.mcount * S, 64);
+        p.dprobs.push_back(h);
+      }
+    }
+  }
+  // Waves: consecutive problems whose A matrices fit the budget together.
+  DenseWave wv{};
+  auto close = [&]() {
+    if (wv.np == 0) return;
+    wv.nt = (uint32_t)(p.dtiles.size() / 3) - wv.t0;
+    p.dense_abytes = std::max<uint64_t>(p.dense_abytes, wv.elems * 2);
+    p.dwaves.push_back(wv);
+  };
+  for (uint32_t i = 0; i < (uint32_t)p.dprobs.size(); ++i) {
+    DenseHost& h = p.dprobs[i];
+    const uint64_t el = (uint64_t)h.n_pad * h.ld;
+    if (wv.np > 0 && (wv.elems + el) * 2 > budget) {
+      close();
+      wv = DenseWave{};
+    }
+    if (wv.np == 0) {
+      wv.p0 = i;
+      wv.t0 = (uint32_t)(p.dtiles.size() / 3);
+    }
+    h.a_off = wv.elems;
+    h.row0 = wv.rows;
+    wv.elems += el;
+    wv.rows += h.n_pad;
+    wv.colblocks = std::max<uint32_t>(wv.colblocks, (uint32_t)((h.ld + kDenseScatterCols - 1) / kDenseScatterCols));
+    wv.np++;
+    const uint32_t rb = h.n_pad / 128, cb = (h.n_pad + 255) / 256;
+    for (uint32_t I = 0; I < rb; ++I)
+      for (uint32_t J = I / 2; J < cb; ++J) {
+        const uint32_t t[3] = {i, I, J};
+        p.dtiles.insert(p.dtiles.end(), t, t + 3);
+        p.dense_flops += 2.0 * 128.0 * 256.0 * (double)h.ld;
+      }
+  }
+  close();
 }
 
 struct Tables {
   std::vector<uint8_t> buf;
-  size_t add(const void* src, size_t bytes) {
-    const size_t o = align_up(buf.size(), 16);
+  size_t add(const void* src, size_t bytes, size_t align = 16) {
+    const size_t o = align_up(buf.size(), align);
     buf.resize(o + bytes);
     if (bytes) memcpy(buf.data() + o, src, bytes);
     return o;
   }
-  size_t reserve(size_t bytes) {
-    const size_t o = align_up(buf.size(), 16);
+  size_t reserve(size_t bytes, size_t align = 16) {
+    const size_t o = align_up(buf.size(), align);
     buf.resize(o + bytes);
     return o;
   }
@@ -631,6 +761,40 @@ void add_common_tables(gakco_ctx* c, Plan& p, Tables& t) {
   }
   p.o_pack = t.reserve(p.ds.size() * sizeof(DsPack));
   p.o_info = t.reserve(p.ds.size() * sizeof(DsInfo));
+  if (!p.dprobs.empty()) {
+    p.o_dprobs = t.reserve(p.dprobs.size() * sizeof(DenseProb));
+    p.o_dtiles = t.add(p.dtiles.data(), p.dtiles.size() * 4);
+    p.o_tmaps = t.reserve(p.dprobs.size() * kDenseTmapBytes, 64);
+  }
+}
+
+// Dense problem records and their TMA descriptors, once the A buffer and
+// the table area have device addresses.
+int fill_dense(gakco_ctx* c, Work& w, Plan& p, Tables& t) {
+  uint8_t* base = (uint8_t*)w.tables.p;
+  std::vector<uint64_t> cacc(p.ds.size(), 0);
+  for (size_t d = 1; d < p.ds.size(); ++d)
+    cacc[d] = cacc[d - 1] + (uint64_t)(c->M + 1) * p.ds[d - 1].n * p.ds[d - 1].n;
+  for (size_t i = 0; i < p.dprobs.size(); ++i) {
+    const DenseHost& h = p.dprobs[i];
+    DenseProb q{};
+    q.A = (uint16_t*)w.Adense.p + h.a_off;
+    q.C = (uint32_t*)w.Cacc.p + cacc[h.ds] + (uint64_t)h.level * h.n * h.n;
+    q.maxc = (uint32_t*)w.dmaxc.p + i;
+    q.tmap = base + p.o_tmaps + i * kDenseTmapBytes;
+    q.ld = h.ld;
+    q.n = h.n;
+    q.n_pad = h.n_pad;
+    q.ds = h.ds;
+    q.mfirst = h.mfirst;
+    q.mcount = h.mcount;
+    q.key_bits = h.key_bits;
+    q.row0 = h.row0;
+    memcpy(t.buf.data() + p.o_dprobs + i * sizeof(DenseProb), &q, sizeof q);
+    const int r = dense_encode_tmap(t.buf.data() + p.o_tmaps + i * kDenseTmapBytes, q.A, h.ld, h.n_pad);
+    if (r != 0) return wfail(w, GAKCO_E_CUDA, "TMA descriptor of dense problem %zu failed (%d)", i, r);
+  }
+  return GAKCO_OK;
 }
 
 // Fill the DsPack / DsInfo records once the table area's device address
@@ -691,10 +855,15 @@ int plan_memory_and_tables(gakco_ctx* c, Work& w, Plan& p, bool plain) {
   for (auto& D : p.ds) csum += (uint64_t)(c->M + 1) * D.n * D.n;
   p.c_elems = plain ? 0 : csum;
   if (!plain) ENSURE(Cacc, csum * 4);
+  if (!p.dprobs.empty()) {
+    ENSURE(Adense, p.dense_abytes);
+    ENSURE(dmaxc, p.dprobs.size() * 4);
+  }
   Tables t;
   add_common_tables(c, p, t);
   if ((rc = ensure(c, w, w.tables, t.buf.size(), "tables")) != GAKCO_OK) return rc;
   p.ftiles = fill_records(c, w, p, t, plain);
+  if (!p.dprobs.empty() && (rc = fill_dense(c, w, p, t)) != GAKCO_OK) return rc;
   return upload_tables(c, w, t);
 }
 
@@ -776,6 +945,21 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
   if (!plain) {
     for (const Chunk& ch : p.chunks) enqueue_chunk(c, w, p, ch, Tail::kGram);
     if (p.c_elems) cudaMemsetAsync(w.Cacc.p, 0, p.c_elems * 4, w.cs);
+    if (!p.dwaves.empty()) {
+      // Dense levels: A = counts per (sequence, mask, key), C_m += A A^T.
+      const DenseProb* probs = (const DenseProb*)(base + p.o_dprobs);
+      const uint32_t* tiles = (const uint32_t*)(base + p.o_dtiles);
+      cudaMemsetAsync(w.dmaxc.p, 0, p.dprobs.size() * 4, w.cs);
+      for (const DenseWave& wv : p.dwaves) {
+        {
+          Bracket b(c, w, "dense_scatter", 1);
+          launch_dense_scatter(probs + wv.p0, wv.np, wv.rows, wv.colblocks, (const DsPack*)(base + p.o_pack),
+                               (const MaskDesc*)(base + p.o_masks), (const uint64_t*)w.fullkey.p, w.cs);
+        }
+        Bracket b(c, w, "dense_gemm", 1);
+        launch_dense_gemm(probs, tiles + 3 * (size_t)wv.t0, wv.nt, c->nsm, status, w.cs);
+      }
+    }
     {
       Bracket b(c, w, "accumulate", 1);
       launch_accum(a, c->accum_threads, p.acc_blocks, p.acc_smem, w.cs);
@@ -819,8 +1003,8 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
 
 uint64_t plan_key(gakco_ctx* c, const Plan& p, bool plain) {
   uint64_t h = 1469598103934665603ull;
-  int64_t o[8] = {plain, c->radix_bits, c->chunk_elems, c->accum_threads, c->smem_cols,
-                  (int64_t)p.ds.size(), c->group_bytes, 0};
+  int64_t o[9] = {plain, c->radix_bits, c->chunk_elems, c->accum_threads, c->smem_cols,
+                  (int64_t)p.ds.size(), c->group_bytes, c->dense, c->dense_bytes};
   h = fnv1a(h, o, sizeof o);
   for (const DsHost& D : p.ds) {
     const void* ptrs[4] = {D.codes, D.K, D.Khat, D.Nm};
@@ -841,6 +1025,7 @@ int check_status(gakco_ctx* c, Work& w) {
   if (st & kErrBadCode) return wfail(w, GAKCO_E_INVALID, "input holds a symbol >= sigma (%d)", c->sigma);
   if (st & kErrKneCM) return wfail(w, GAKCO_E_INTERNAL, "internal check failed: sum h_m N_m != C_M");
   if (st & kErrBadEntry) return wfail(w, GAKCO_E_INTERNAL, "internal check failed: entry out of range");
+  if (st & kErrTimeout) return wfail(w, GAKCO_E_TIMEOUT, "a bounded wait in the dense GEMM ran out");
   if (st) return wfail(w, GAKCO_E_INTERNAL, "device status 0x%x", st);
   return GAKCO_OK;
 }
@@ -897,6 +1082,9 @@ int run_gram(gakco_ctx* c, Plan& p, cudaStream_t user) {
     c->last_replay = 1;
   } else {
     drop_graph(c);
+    plan_dense(c, p, plain);
+    c->plan_dense_probs = (double)p.dprobs.size();
+    c->plan_dense_flops = p.dense_flops;
     plan_chunks(c, p, plain);
     plan_items(c, p);
     if (!plain) {
@@ -931,6 +1119,8 @@ int run_gram(gakco_ctx* c, Plan& p, cudaStream_t user) {
     }
   }
   c->last_launches = w.launches;
+  c->last_dense_probs = c->plan_dense_probs;
+  c->last_dense_flops = c->plan_dense_flops;
   rc = sync_and_check(c, w);
   c->last_pairs = w.pairs;
   c->last_entries = w.entries;
@@ -1580,6 +1770,7 @@ int gakco_create(int sigma, int g, int k, gakco_ctx** out) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
   if (e == cudaSuccess) e = (cudaError_t)prep_init();
+  if (e == cudaSuccess) e = (cudaError_t)dense_init();
   if (e == cudaSuccess && init_work(c->main) != GAKCO_OK) e = cudaErrorMemoryAllocation;
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1661,6 +1852,14 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
       if (v < 0) return fail(c, GAKCO_E_INVALID, "memory budget must be >= 0");
       c->serve_mem_bytes = v;
       break;
+    case GAKCO_OPT_DENSE:
+      if (v < 0 || v > 2) return fail(c, GAKCO_E_INVALID, "dense mode must be 0, 1 or 2");
+      c->dense = (int)v;
+      break;
+    case GAKCO_OPT_DENSE_BYTES:
+      if (v < 1) return fail(c, GAKCO_E_INVALID, "dense bytes must be >= 1");
+      c->dense_bytes = v;
+      break;
     default:
       return fail(c, GAKCO_E_INVALID, "unknown option %d", key);
   }
@@ -1698,6 +1897,12 @@ int gakco_get_stat(const gakco_ctx* c, int key, double* v) {
       return GAKCO_OK;
     case GAKCO_STAT_WINDOWS_VISITED:
       *v = c->last_windows;
+      return GAKCO_OK;
+    case GAKCO_STAT_DENSE_PROBLEMS:
+      *v = c->last_dense_probs;
+      return GAKCO_OK;
+    case GAKCO_STAT_DENSE_FLOPS:
+      *v = c->last_dense_flops;
       return GAKCO_OK;
     case GAKCO_STAT_SERVED_BATCHES: {
       std::lock_guard<std::mutex> lk(cc->mu);

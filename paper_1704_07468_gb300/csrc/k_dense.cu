@@ -1,0 +1,430 @@
+// Dense levels: C_m += F^T F as a dense contraction on the tensor cores
+// (tcgen05.mma, kind::f16, f32 accumulators in tensor memory).
+//
+// For one mask the count matrix F has a row per feature and a column per
+// sequence, and countAndUpdate adds F^T F to C_m (Section 2.2, steps 2-5;
+// Alg. 1).  When a level's key space is small (2^(b(g-m)) keys, e.g.
+// 4^6 = 4096 DNA 6-mers) every key can be a feature: F is dense, and all
+// masks of a run of the level stack into one matrix A with a row per
+// sequence and a column per (mask, key), so that C_m += A A^T.  No sort is
+// needed: the scatter kernel counts A[x, (mask, key)] directly.
+//
+// Exactness.  Counts are integers <= 511 (the host routes a level here only
+// when no sequence has more than 511 windows) and are exact in f16;
+// products and partial sums are exact in the f32 accumulators while they
+// stay below 2^24.  The GEMM therefore closes an accumulation "round" and
+// adds it into the int32 C every floor((2^24 - 1) / (64 maxc^2)) stages of
+// 64 columns, maxc being the largest count the scatter kernel saw.
+//
+// GEMM structure.  One CTA per SM walks a list of (problem, I, J) output
+// tiles of 128 rows x 256 columns (upper triangle only: C is symmetric).
+// Warp 5 loads 64-column slices of A's rows I*128.. and J*256.. with TMA
+// (128-byte swizzle) into a four-stage ring; one thread of warp 4 issues
+// tcgen05.mma (M = 128, N = 256, K = 16) into one of two 256-column TMEM
+// accumulators; warps 0-3 read the finished accumulator back with
+// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. tile rows) and add
+// the upper-triangle part into C.  Hand-offs use mbarriers.  Every wait is
+// bounded: a timeout raises an error bit, stops every role, waits (bounded)
+// for the copies and MMAs already issued, and frees tensor memory.
+#include <cuda.h>  // CUtensorMap and its enums; the encoder is fetched at run time
+#include <cuda_fp16.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace gk {
+
+namespace {
+
+constexpr int kStages = 4;
+constexpr uint32_t kABytes = 128 * 128;  // 128 rows x 64 f16 columns
+constexpr uint32_t kBBytes = 256 * 128;  // 256 rows x 64 f16 columns
+constexpr uint32_t kStageBytes = kABytes + kBBytes;
+constexpr int kMmaWarp = 4, kTmaWarp = 5;
+constexpr int kGemmThreads = 192;
+constexpr uint32_t kTmemCols = 512;  // two 128 x 256 f32 accumulators
+constexpr int kScatterThreads = 256;
+constexpr long long kWaitCycles = 4000000000ll;  // about 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled layout: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);  // start address
+  d |= (uint64_t)(16 >> 4) << 16;          // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
+  d |= (uint64_t)1 << 46;                  // descriptor version
+  d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(b))
+               : "memory");
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool bar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity.  Returns false when the
+// wait ran out (and then raises the abort flag) or another role aborted.
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, volatile uint32_t* abort_flag) {
+  const long long t0 = clock64();
+  for (;;) {
+    if (bar_test(b, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+
+// Bounded wait that ignores the abort flag: used while unwinding, for work
+// already issued.
+__device__ __forceinline__ void bar_drain(uint64_t* b, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!bar_test(b, parity) && clock64() - t0 <= kWaitCycles) {
+  }
+}
+
+__device__ __forceinline__ void tma_load(uint32_t dst, const void* tmap, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(dst),
+      "l"((uint64_t)tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// Stages (64 columns each) per exact accumulation round.
+__device__ __forceinline__ uint32_t stages_per_round(const uint32_t* maxc, uint32_t nk) {
+  const uint32_t mc = *(const volatile uint32_t*)maxc;
+  if (mc == 0) return nk > 0 ? nk : 1;
+  uint64_t s = (uint64_t)((1u << 24) - 1) / (64ull * mc * mc);
+  if (s < 1) s = 1;
+  return (uint32_t)(s < nk ? s : nk);
+}
+
+}  // namespace
+
+// Builds the rows of A: one block per (row of the wave, block of
+// kDenseScatterCols columns).  Counts are gathered in shared memory and the
+// whole column block is written out (zeros included), so A needs no
+// separate clearing; padded rows come out all zero.
+__global__ void __launch_bounds__(kScatterThreads)
+k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, const DsPack* __restrict__ dsp,
+                const MaskDesc* __restrict__ masks, const uint64_t* __restrict__ fullkey) {
+  extern __shared__ uint32_t cnt[];
+  const uint32_t bx = blockIdx.x, tid = threadIdx.x;
+  uint32_t lo = 0, hi = nprobs;  // last problem with row0 <= bx
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (probs[mid].row0 <= bx)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  const DenseProb& P = probs[lo];
+  const uint64_t ld = P.ld;
+  const uint64_t c0 = (uint64_t)blockIdx.y * kDenseScatterCols;
+  if (c0 >= ld) return;
+  const uint32_t x = bx - P.row0;
+  const uint32_t ncol = (uint32_t)(ld - c0 < (uint64_t)kDenseScatterCols ? ld - c0 : kDenseScatterCols);
+  for (uint32_t i = tid; i < ncol / 4; i += kScatterThreads) ((uint4*)cnt)[i] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
+  if (x < P.n) {
+    const DsPack& D = dsp[P.ds];
+    const uint32_t w0 = D.woff[x], nw = D.woff[x + 1] - w0;
+    const uint32_t kb = P.key_bits;
+    const uint32_t mu0 = (uint32_t)(c0 >> kb);
+    uint32_t mu1 = (uint32_t)((c0 + ncol - 1) >> kb) + 1;
+    if (mu1 > P.mcount) mu1 = P.mcount;
+    const uint32_t nmu = mu1 > mu0 ? mu1 - mu0 : 0;
+    const uint64_t* fk = fullkey + D.win0 + w0;
+    for (uint32_t i = tid; i < nw * nmu; i += kScatterThreads) {
+      const uint32_t w = i / nmu, mu = mu0 + i % nmu;
+      const uint64_t key = masked_key(fk[w], masks[P.mfirst + mu]);
+      const uint64_t col = (((uint64_t)mu << kb) | key) - c0;
+      if (col < ncol) atomicAdd(&cnt[col], 1u);
+    }
+  }
+  __syncthreads();
+  uint32_t mymax = 0;
+  uint4* out = (uint4*)(P.A + (uint64_t)x * ld + c0);
+  for (uint32_t j = tid; j < ncol / 8; j += kScatterThreads) {
+    const uint4 a = ((const uint4*)cnt)[2 * j], b = ((const uint4*)cnt)[2 * j + 1];
+    mymax = max(mymax, max(max(max(a.x, a.y), max(a.z, a.w)), max(max(b.x, b.y), max(b.z, b.w))));
+    const __half2 h0 = __floats2half2_rn((float)a.x, (float)a.y);
+    const __half2 h1 = __floats2half2_rn((float)a.z, (float)a.w);
+    const __half2 h2 = __floats2half2_rn((float)b.x, (float)b.y);
+    const __half2 h3 = __floats2half2_rn((float)b.z, (float)b.w);
+    uint4 v;
+    v.x = *(const uint32_t*)&h0;
+    v.y = *(const uint32_t*)&h1;
+    v.z = *(const uint32_t*)&h2;
+    v.w = *(const uint32_t*)&h3;
+    out[j] = v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mymax = max(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
+  if ((tid & 31) == 0 && mymax) atomicMax(P.maxc, mymax);
+}
+
+__global__ void __launch_bounds__(kGemmThreads, 1)
+k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ tiles, uint32_t ntiles,
+             uint32_t* __restrict__ status) {
+  extern __shared__ uint8_t raw[];
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], tfull[2], tempty[2], done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile uint32_t abort_flag;
+  uint8_t* sm = (uint8_t*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      bar_init(&full_bar[s], 1);
+      bar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      bar_init(&tfull[b], 1);
+      bar_init(&tempty[b], 128);
+    }
+    bar_init(&done_bar, 1);
+    abort_flag = 0;
+  }
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t taddr = tmem_base;
+
+  if (warp == kTmaWarp) {
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool stop = false;
+      for (uint32_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+        const DenseProb& P = probs[tiles[3 * t]];
+        const int y_a = (int)(tiles[3 * t + 1] * 128), y_b = (int)(tiles[3 * t + 2] * 256);
+        const void* tm = P.tmap;
+        const uint32_t nk = (uint32_t)(P.ld / 64);
+        for (uint32_t k = 0; k < nk; ++k, ++it) {
+          const uint32_t s = it % kStages;
+          if (!bar_wait(&empty_bar[s], ((it / kStages) & 1) ^ 1, &abort_flag)) {
+            stop = true;
+            break;
+          }
+          const uint32_t dst = smem_u32(sm + s * kStageBytes);
+          bar_expect_tx(&full_bar[s], kStageBytes);
+          tma_load(dst, tm, (int)(k * 64), y_a, &full_bar[s]);
+          tma_load(dst + kABytes, tm, (int)(k * 64), y_b, &full_bar[s]);
+          tma_load(dst + kABytes + kABytes, tm, (int)(k * 64), y_b + 128, &full_bar[s]);
+        }
+      }
+      // Let the copies already issued land before the block can exit.
+      for (uint32_t s = 0; s < (uint32_t)kStages; ++s)
+        if (it > s) {
+          const uint32_t j = s + kStages * ((it - 1 - s) / kStages);
+          bar_drain(&full_bar[s], (j / kStages) & 1);
+        }
+    }
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | ((256u >> 3) << 17) | ((128u >> 4) << 24);  // f32 += f16 x f16
+      uint32_t it = 0, round = 0;
+      bool stop = false;
+      for (uint32_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+        const DenseProb& P = probs[tiles[3 * t]];
+        const uint32_t nk = (uint32_t)(P.ld / 64);
+        const uint32_t spr = stages_per_round(P.maxc, nk);
+        for (uint32_t k = 0; k < nk && !stop; ++round) {
+          const uint32_t b = round & 1;
+          if (!bar_wait(&tempty[b], ((round >> 1) & 1) ^ 1, &abort_flag)) {
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t d = taddr + b * 256;
+          const uint32_t kend = (k + spr < nk) ? k + spr : nk;
+          for (uint32_t kk = k; kk < kend; ++kk, ++it) {
+            const uint32_t s = it % kStages;
+            if (!bar_wait(&full_bar[s], (it / kStages) & 1, &abort_flag)) {
+              stop = true;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t a0 = smem_u32(sm + s * kStageBytes), b0 = a0 + kABytes;
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) {
+              const uint32_t acc = (kk > k || j > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                  "l"(smem_desc(a0 + j * 32)), "l"(smem_desc(b0 + j * 32)), "r"(idesc), "r"(acc));
+            }
+            mma_commit(&empty_bar[s]);
+          }
+          if (stop) break;
+          mma_commit(&tfull[b]);
+          k = kend;
+        }
+      }
+      // Every MMA issued must finish before tensor memory is freed.
+      mma_commit(&done_bar);
+      bar_drain(&done_bar, 0);
+    }
+  } else {
+    // Epilogue warps 0-3: row = I*128 + 32*warp + lane of each tile.
+    uint32_t round = 0;
+    bool stop = false;
+    for (uint32_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+      const DenseProb& P = probs[tiles[3 * t]];
+      const uint32_t n = P.n;
+      const uint32_t nk = (uint32_t)(P.ld / 64);
+      const uint32_t spr = stages_per_round(P.maxc, nk);
+      const uint32_t nr = (nk + spr - 1) / spr;
+      const uint32_t row = tiles[3 * t + 1] * 128 + warp * 32 + lane;
+      const uint32_t col0 = tiles[3 * t + 2] * 256;
+      uint32_t* crow = P.C + (uint64_t)row * n;
+      for (uint32_t r = 0; r < nr; ++r, ++round) {
+        const uint32_t b = round & 1;
+        if (!__all_sync(0xffffffffu, bar_wait(&tfull[b], (round >> 1) & 1, &abort_flag))) {
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll 1
+        for (uint32_t cb = 0; cb < 256; cb += 32) {
+          uint32_t v[32];
+          const uint32_t a = taddr + b * 256 + cb + ((warp * 32) << 16);
+          __syncwarp();
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+              "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+              : "r"(a));
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+          if (row < n) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const uint32_t col = col0 + cb + j;
+              const uint32_t val = (uint32_t)__uint_as_float(v[j]);
+              if (col < n && col >= row && val) atomicAdd(&crow[col], val);
+            }
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        bar_arrive(&tempty[b]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (tid == 0 && abort_flag) atomicOr(status, kErrTimeout);
+  if (warp == kMmaWarp) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols));
+  }
+}
+
+size_t dense_scatter_smem() { return (size_t)kDenseScatterCols * 4; }
+size_t dense_gemm_smem() { return (size_t)kStages * kStageBytes + 1024; }
+
+int dense_init() {
+  cudaError_t e = cudaFuncSetAttribute(k_dense_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)dense_gemm_smem());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_dense_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dense_scatter_smem());
+  return (int)e;
+}
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+}  // namespace
+
+int dense_encode_tmap(void* out, void* A, uint64_t ld, uint64_t rows) {
+  static_assert(sizeof(CUtensorMap) == kDenseTmapBytes, "tensor map size");
+  EncodeTiledFn fn = encoder();
+  if (!fn) return -1;
+  const cuuint64_t dims[2] = {ld, rows};
+  const cuuint64_t strides[1] = {ld * 2};
+  const cuuint32_t box[2] = {64, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn((CUtensorMap*)out, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, A, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : (int)r;
+}
+
+void launch_dense_scatter(const DenseProb* d_probs, uint32_t nprobs, uint32_t rows, uint32_t colblocks,
+                          const DsPack* dsp, const MaskDesc* masks, const uint64_t* fullkey, cudaStream_t st) {
+  if (nprobs == 0 || rows == 0 || colblocks == 0) return;
+  k_dense_scatter<<<dim3(rows, colblocks), kScatterThreads, dense_scatter_smem(), st>>>(d_probs, nprobs, dsp,
+                                                                                        masks, fullkey);
+}
+
+void launch_dense_gemm(const DenseProb* d_probs, const uint32_t* d_tiles, uint32_t ntiles, int nsm,
+                       uint32_t* status, cudaStream_t st) {
+  if (ntiles == 0) return;
+  const uint32_t grid = ntiles < (uint32_t)nsm ? ntiles : (uint32_t)nsm;
+  k_dense_gemm<<<grid, kGemmThreads, dense_gemm_smem(), st>>>(d_probs, d_tiles, ntiles, status);
+}
+
+}  // namespace gk

@@ -1,0 +1,138 @@
+"""Dense levels on the tensor cores: C_m += A A^T with A the per-sequence
+counts of every (mask, (g-m)-mer) of a level (countAndUpdate of Alg. 1 as a
+dense contraction).
+
+The route is exact integer arithmetic (counts <= 511 in f16, f32 partial
+sums flushed to int32 before 2^24), so every integer output must equal the
+oracle's bit for bit, and equal the sparse route's.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1704_07468_gb300 as pkg
+from paper_1704_07468_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+KHAT_RTOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1704_07468_gb300 import build as lib_build
+    lib_build.build()
+    oracle.build()
+
+
+def _run(sigma, g, k, codes, off, **opts):
+    with pkg.gakco_create(sigma, g, k) as ctx:
+        for name, v in opts.items():
+            ctx.set_option(name, v)
+        out = ctx.gram(codes, off, khat=True, nm=True)
+        out["dense_problems"] = ctx.get_stat("dense_problems")
+        out["dense_flops"] = ctx.get_stat("dense_flops")
+    return out
+
+
+def _check(out, ref):
+    np.testing.assert_array_equal(out["K"], ref["K"])
+    np.testing.assert_array_equal(out["Nm"], ref["Nm"])
+    err = np.abs(out["Khat"] - ref["Khat"])
+    assert np.all(err <= KHAT_RTOL * np.abs(ref["Khat"]) + 1e-300)
+
+
+CASES = [  # (seed, n, sigma, lo, hi, g, k)
+    (120, 40, 4, 100, 300, 10, 6),    # DNA large-M shape: level 4 (4096 keys) dense
+    (121, 260, 4, 0, 200, 8, 4),      # three row blocks, ragged n, partial B tile
+    (122, 30, 4, 10, 120, 10, 3),     # M = 7: levels 5..7 have 10, 8, 6 key bits
+    (123, 25, 2, 0, 80, 4, 1),        # binary alphabet: 4..8-column masks padded to 64
+    (124, 19, 3, 5, 60, 6, 2),        # sigma = 3 (2 bits per symbol, code 3 unused)
+    (125, 9, 4, 10, 40, 5, 5),        # M = 0: the spectrum level alone
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_dense_levels_match_the_oracle(case):
+    seed, n, sigma, lo, hi, g, k = case
+    codes, off = synth.random_small(seed, n, sigma, lo, hi)
+    ref = oracle.gram(codes, off, g, k)
+    out = _run(sigma, g, k, codes, off, dense=2)
+    assert out["dense_problems"] > 0
+    _check(out, ref)
+
+
+def test_dense_equals_sparse_on_several_waves():
+    """A small wave budget cuts each level into several mask runs and the
+    runs into several waves; the result must not change."""
+    codes, off = synth.random_small(126, 300, 4, 100, 300)
+    g, k = 9, 5
+    sparse = _run(4, g, k, codes, off, dense=0)
+    assert sparse["dense_problems"] == 0
+    n_pad = 384
+    one_mask = n_pad * 4 ** 5 * 2            # level 4: 5-mers
+    dense = _run(4, g, k, codes, off, dense=2, dense_bytes=3 * one_mask)
+    assert dense["dense_problems"] > 10
+    for key in ("K", "Nm", "Khat"):
+        np.testing.assert_array_equal(dense[key], sparse[key])
+    rows = np.array([0, 127, 128, 255, 299], dtype=np.int32)
+    ref = oracle.gram(codes, off, g, k, rows=rows)
+    np.testing.assert_array_equal(dense["K"][rows], ref["K"])
+
+
+@pytest.mark.parametrize("kind", ["homopolymer", "period2", "mixed"])
+def test_large_counts_flush_exactly(kind):
+    """A homopolymer of 500 symbols gives one count of 496 per mask: every
+    64-column stage then closes its own exact f32 round."""
+    codes, off = synth.repeats(kind, n=4, length=500)
+    ref = oracle.gram(codes, off, 5, 3)
+    out = _run(4, 5, 3, codes, off, dense=2)
+    assert out["dense_problems"] > 0
+    _check(out, ref)
+
+
+def test_long_sequences_stay_sparse():
+    """More than 511 windows in one sequence: counts could leave the exact
+    range, so no level goes dense, and the result is still exact."""
+    codes, off = synth.random_small(127, 6, 4, 500, 700)
+    ref = oracle.gram(codes, off, 6, 3)
+    out = _run(4, 6, 3, codes, off, dense=2)
+    assert out["dense_problems"] == 0
+    _check(out, ref)
+
+
+def test_dense_batch_and_graph_replay():
+    sets = [synth.random_small(130 + i, n, 4, 80, 250) for i, n in enumerate([50, 1, 0, 140])]
+    with pkg.gakco_create(4, 8, 5) as ctx:
+        ctx.set_option("dense", 2)
+        first = ctx.gram_batch(sets, khat=True, nm=True)
+        probs = ctx.get_stat("dense_problems")
+        again = ctx.gram_batch(sets, khat=True, nm=True)
+        assert ctx.get_stat("graph_replay") == 1
+        assert ctx.get_stat("dense_problems") == probs > 0
+    for (c, o), a, b in zip(sets, first, again):
+        for key in ("K", "Nm", "Khat"):
+            np.testing.assert_array_equal(a[key], b[key])
+        if len(o) > 1:
+            _check(a, oracle.gram(c, o, 8, 5))
+
+
+def test_cost_model_mode_is_exact():
+    codes, off = synth.random_small(128, 200, 4, 100, 300)
+    out = _run(4, 10, 6, codes, off, dense=1)
+    sparse = _run(4, 10, 6, codes, off, dense=0)
+    for key in ("K", "Nm", "Khat"):
+        np.testing.assert_array_equal(out[key], sparse[key])
+
+
+def test_dna_large_dataset_sampled_rows():
+    """The N = 4000 dataset of the DNA large-M workload (g = 10, k = 6) with
+    every qualifying level dense; sampled rows against the oracle."""
+    codes, off = synth.dna_large(seeds=[6], sizes=[4000])[0]
+    out = _run(4, 10, 6, codes, off, dense=2)
+    assert out["dense_problems"] > 0
+    rows = np.array([0, 1, 1999, 3998, 3999], dtype=np.int32)
+    ref = oracle.gram(codes, off, 10, 6, rows=rows, threads=len(rows))
+    np.testing.assert_array_equal(out["K"][rows], ref["K"])
+    np.testing.assert_array_equal(out["Nm"][:, rows], ref["Nm"])
+    np.testing.assert_array_equal(out["K"], out["K"].T)
