@@ -199,19 +199,48 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def alg_bytes_sort(ctx_sets, g, bits, radix_bits, masks_per_level):
-    """Algorithmic bytes of all sort passes of one step: per element per
-    pass, one read and one write of (key, payload); the first pass reads
-    the 8-byte full g-mer key instead."""
-    G = sum(int(np.sum(np.maximum(np.diff(o) - g + 1, 0))) for _, o in ctx_sets)
-    total = 0
-    for m, nmask in enumerate(masks_per_level):
-        kb = (g - m) * bits
-        npass = -(-kb // radix_bits)
-        kbytes = 8 if kb > 32 else 4
-        per = (8 + kbytes + 4) + (npass - 1) * 2 * (kbytes + 4)
-        total += nmask * G * per
-    return total
+def kernel_rooflines(timings, work, peaks, sm_count):
+    """Roofline entry per timed stage with a known algorithmic work figure.
+
+    ``work`` holds the engine's own counts for the step: pair updates of
+    the accumulation, algorithmic sort bytes, dense-contraction flops
+    (upper triangle, unpadded) and issued flops, dense A bytes."""
+    out = {}
+    tensor_peak = peaks.get("bf16_tflops", 1900.0)  # f16 and bf16 share one nominal rate
+    for name, (ms, n) in timings.items():
+        sec = ms / 1000.0
+        if sec <= 0:
+            continue
+        e = None
+        if name == "accumulate" and work["pairs"] > 0:
+            # One 32-bit shared-memory add per pair update; peak = banks x
+            # SMs x max SM clock.
+            peak = SMEM_BANKS * sm_count * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            a = work["pairs"] / sec / 1e12
+            e = {"bound": "alu", "achieved": a, "peak": peak, "unit": "Tupdates/s",
+                 "kernel": "k_accum", "peak_source": "32 shared-memory banks x SMs x max SM clock"}
+        elif name == "sort_pass" and work["sort_bytes"] > 0:
+            a = work["sort_bytes"] / sec / 1e9
+            e = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "kernel": "k_sort_upsweep + k_sort_scan + k_sort_downsweep"}
+        elif name == "dense_gemm" and work["dense_flops"] > 0:
+            a = work["dense_flops"] / sec / 1e12
+            e = {"bound": "tensor", "achieved": a, "peak": tensor_peak, "unit": "TFLOP/s",
+                 "kernel": "k_dense_gemm",
+                 "issued_tflops": work["dense_issued"] / sec / 1e12,
+                 "peak_source": "measured bf16 burst (same nominal rate as f16)"}
+        elif name == "dense_scatter" and work["dense_bytes"] > 0:
+            a = work["dense_bytes"] / sec / 1e9
+            e = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "kernel": "k_dense_scatter"}
+        if e is None:
+            continue
+        e["frac"] = e["achieved"] / e["peak"]
+        e["traffic"] = None
+        e["launch_ms"] = ms / n
+        e["launches"] = n
+        out[name] = e
+    return out
 
 
 def run_serve(pkg, n_requests, warmup):
@@ -332,6 +361,9 @@ def run_ours(args):
         tuned = ctx.autotune_device([t.data_ptr() for t in d_codes], offs,
                                     stream=stream.cuda_stream)
         tuned += f" ({time.perf_counter() - t_tune:.1f} s, before warm-up)"
+    if args.dense is not None:
+        ctx.set_option("dense", args.dense)
+        tuned += f"; dense={args.dense} set by --dense"
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -356,6 +388,11 @@ def run_ours(args):
     step_ms = float(np.mean(ms))
     replay = int(ctx.get_stat("graph_replay"))
     pairs = ctx.get_stat("pair_updates")
+    work = {"pairs": pairs, "sort_bytes": ctx.get_stat("sort_bytes"),
+            "dense_flops": ctx.get_stat("dense_flops"),
+            "dense_issued": ctx.get_stat("dense_issued_flops"),
+            "dense_bytes": ctx.get_stat("dense_bytes"),
+            "dense_problems": int(ctx.get_stat("dense_problems"))}
     if ws > 1:
         step_ms = reduce_max(step_ms, dev)
         torch.distributed.barrier()
@@ -414,35 +451,23 @@ def run_ours(args):
                  "bit_identical_K": bool(same)}
         pctx.close()
 
-    # Roofline of the dominant kernel.
+    # Roofline of every stage with a work figure; the dominant one is the
+    # headline entry.
     peaks, peak_kind = measured_peaks()
-    dom = max(timings.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_n) = dom
-    per_launch_ms = dom_ms / dom_n
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    roof = None
-    if dom_name == "accumulate":
-        # Bound by shared-memory read-modify-write throughput: one 32-bit
-        # add per pair update; peak = banks x SMs x max SM clock.
-        peak = SMEM_BANKS * sm_count * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        achieved = pairs / (per_launch_ms / 1000.0) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tupdates/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_accum",
-                "peak_source": "32 shared-memory banks x SMs x max SM clock"}
-    elif dom_name == "sort_pass":
-        bits = max(1, (sigma - 1).bit_length())
-        lv = [__import__("math").comb(g, m) for m in range(g - k + 1)]
-        nbytes = alg_bytes_sort(sets, g, bits, 8, lv) / dom_n
-        achieved = nbytes / (per_launch_ms / 1000.0) / 1e9
-        peak = peaks["hbm_gbs"]
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "sort pass"}
+    roofs = kernel_rooflines(timings, work, peaks, sm_count)
+    total_ms = sum(v[0] for v in timings.values())
+    for name, e in roofs.items():
+        e["peak_kind"] = peak_kind
+        e["share_of_step"] = timings[name][0] / total_ms
+    dom_name = max(timings.items(), key=lambda kv: kv[1][0])[0]
+    if dom_name in roofs:
+        roof = dict(roofs[dom_name])
     else:
         roof = {"bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": None, "traffic": None, "kernel": dom_name}
-    roof["peak_kind"] = peak_kind
-    roof["launch_ms"] = per_launch_ms
-    roof["share_of_step"] = dom_ms / sum(v[0] for v in timings.values())
+                "frac": None, "traffic": None, "kernel": dom_name, "peak_kind": peak_kind,
+                "share_of_step": timings[dom_name][0] / total_ms}
+    roof["stage"] = dom_name
 
     serve = None
     if args.serve_requests > 0 and rank == 0:
@@ -466,7 +491,7 @@ def run_ours(args):
                    "outputs": "K int32 + Khat fp64 per dataset",
                    "l2": "256 MiB write between timed steps",
                    "graph_replay": bool(replay), "parallelism": f"replicas x{ws} (weak)",
-                   "autotune": tuned},
+                   "autotune": tuned, "dense_problems": work["dense_problems"]},
         "mask_passes_per_s": len(sets) * n_masks * ws / (step_ms / 1000.0),
         "pair_updates_per_step": pairs,
         "plain_gpu": plain,
@@ -476,6 +501,7 @@ def run_ours(args):
         "gpu_launches": launches * args.steps,
         "kernel_ms": {kname: {"ms": v[0], "launches": v[1]} for kname, v in timings.items()},
         "roofline": roof,
+        "roofline_stages": roofs,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
@@ -498,6 +524,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=64)
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--dense", type=int, default=None, choices=[0, 1, 2],
+                    help="dense-level mode after autotuning: 0 never, 1 cost model, 2 every qualifying level")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-warmup", type=int, default=50)
     ap.add_argument("--dna-sizes", type=lambda v: [int(t) for t in v.split(",")], default=None,

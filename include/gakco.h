@@ -140,7 +140,12 @@ int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 #define GAKCO_STAT_SERVED_BATCHES 8   /* serving: micro-batches completed so far */
 #define GAKCO_STAT_SERVED_REQUESTS 9  /* serving: requests completed so far */
 #define GAKCO_STAT_DENSE_PROBLEMS 10  /* Gram: (dataset, level, mask run) contractions on the tensor cores */
-#define GAKCO_STAT_DENSE_FLOPS 11     /* Gram: tensor-core flops issued (2 per multiply-add, padding included) */
+#define GAKCO_STAT_DENSE_FLOPS 11     /* Gram: flops of the dense contractions' upper triangles,
+                                         2 per multiply-add, padding excluded */
+#define GAKCO_STAT_DENSE_ISSUED_FLOPS 12 /* Gram: flops the tensor cores issued (whole tiles, padding) */
+#define GAKCO_STAT_DENSE_BYTES 13     /* Gram: bytes of the dense count matrices written */
+#define GAKCO_STAT_SORT_BYTES 14      /* Gram: algorithmic bytes of every sort pass (keys and
+                                         payloads read and written once per pass) */
 int gakco_get_stat(const gakco_ctx *ctx, int key, double *value);
 
 /*

@@ -41,7 +41,8 @@ OPT = {"engine": 1, "radix_bits": 2, "chunk_elems": 3, "graph": 4,
 STAT = {"launches": 1, "mask_passes": 2, "device_bytes": 3,
         "graph_replay": 4, "pair_updates": 5, "entries_visited": 6,
         "windows_visited": 7, "served_batches": 8, "served_requests": 9,
-        "dense_problems": 10, "dense_flops": 11}
+        "dense_problems": 10, "dense_flops": 11, "dense_issued_flops": 12,
+        "dense_bytes": 13, "sort_bytes": 14}
 
 
 class GakcoError(RuntimeError):

@@ -198,8 +198,9 @@ struct gakco_ctx {
   int64_t last_launches = 0, last_mask_passes = 0;
   int last_replay = 0;
   double last_pairs = 0, last_entries = 0, last_windows = 0;
-  double last_dense_probs = 0, last_dense_flops = 0;
-  double plan_dense_probs = 0, plan_dense_flops = 0;  // of the last plan (kept for graph replays)
+  // Work figures of the last plan (kept for graph replays).
+  double plan_dense_probs = 0, plan_dense_flops = 0, plan_dense_issued = 0, plan_dense_bytes = 0,
+         plan_sort_bytes = 0;
   std::vector<Timed> timed;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -388,7 +389,10 @@ struct Plan {
   std::vector<DenseWave> dwaves;
   std::vector<uint32_t> dtiles;
   uint64_t dense_abytes = 0;
-  double dense_flops = 0;
+  double dense_flops = 0;         // upper triangle of A A^T, unpadded: 2 mcount S n(n+1)/2 per problem
+  double dense_issued = 0;        // what the 128 x 256 tiles issue, padding included
+  double dense_bytes = 0;         // A written by the scatter
+  double sort_bytes = 0;          // algorithmic bytes of every sort pass
   // device table offsets
   size_t o_masks, o_level, o_pack, o_info, o_segs, o_tiles, o_items, o_dprobs = 0, o_dtiles = 0, o_tmaps = 0;
   std::vector<size_t> o_coff, o_woff;
@@ -460,6 +464,7 @@ int plan_datasets(gakco_ctx* c, Work& w, Plan& p, int32_t nd, const uint8_t* con
 
 // Chunks of (dataset, mask) segments, all of one level per chunk.
 void plan_chunks(gakco_ctx* c, Plan& p, bool plain) {
+  p.sort_bytes = 0;
   const uint64_t limit = plain ? 0 : (uint64_t)std::max<int64_t>(c->chunk_elems, kTile);
   for (int m = 0; m <= c->M; ++m) {
     const int kb = (c->g - m) * c->bits;
@@ -472,6 +477,10 @@ void plan_chunks(gakco_ctx* c, Plan& p, bool plain) {
     Chunk cur{};
     auto flush = [&]() {
       if (cur.nseg == 0) return;
+      // Per element: the first pass reads the full key and the window id
+      // and writes (key, payload); later passes read and write both.
+      const double kbytes = wide ? 8.0 : 4.0;
+      p.sort_bytes += (double)cur.elems * ((8.0 + 4.0 + kbytes + 4.0) + 2.0 * (kbytes + 4.0) * (np - 1));
       p.chunks.push_back(cur);
       p.max_chunk_elems = std::max(p.max_chunk_elems, cur.elems);
       p.max_chunk_nseg = std::max<uint64_t>(p.max_chunk_nseg, cur.nseg);
@@ -615,7 +624,7 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
   p.dwaves.clear();
   p.dtiles.clear();
   p.dense_abytes = 0;
-  p.dense_flops = 0;
+  p.dense_flops = p.dense_issued = p.dense_bytes = 0;
   if (plain || c->dense == 0) return;
   const std::vector<uint32_t> lf = level_firsts(c);
   const uint64_t budget = (uint64_t)std::max<int64_t>(c->dense_bytes, 1);
@@ -683,8 +692,10 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
       for (uint32_t J = I / 2; J < cb; ++J) {
         const uint32_t t[3] = {i, I, J};
         p.dtiles.insert(p.dtiles.end(), t, t + 3);
-        p.dense_flops += 2.0 * 128.0 * 256.0 * (double)h.ld;
+        p.dense_issued += 2.0 * 128.0 * 256.0 * (double)h.ld;
       }
+    p.dense_flops += 2.0 * (double)h.mcount * std::ldexp(1.0, (int)h.key_bits) * 0.5 * h.n * (h.n + 1.0);
+    p.dense_bytes += 2.0 * (double)el;
   }
   close();
 }
@@ -1083,9 +1094,12 @@ int run_gram(gakco_ctx* c, Plan& p, cudaStream_t user) {
   } else {
     drop_graph(c);
     plan_dense(c, p, plain);
+    plan_chunks(c, p, plain);
     c->plan_dense_probs = (double)p.dprobs.size();
     c->plan_dense_flops = p.dense_flops;
-    plan_chunks(c, p, plain);
+    c->plan_dense_issued = p.dense_issued;
+    c->plan_dense_bytes = p.dense_bytes;
+    c->plan_sort_bytes = p.sort_bytes;
     plan_items(c, p);
     if (!plain) {
       const int nb = accum_blocks_per_sm(c->accum_threads, p.acc_smem);
@@ -1119,8 +1133,6 @@ int run_gram(gakco_ctx* c, Plan& p, cudaStream_t user) {
     }
   }
   c->last_launches = w.launches;
-  c->last_dense_probs = c->plan_dense_probs;
-  c->last_dense_flops = c->plan_dense_flops;
   rc = sync_and_check(c, w);
   c->last_pairs = w.pairs;
   c->last_entries = w.entries;
@@ -1572,7 +1584,8 @@ void stop_serving(gakco_ctx* c) {
 // Picks the sort digit width, the sort chunk size, the accumulation block
 // size and the mask-group size for a workload by timing the stages they
 // drive (each candidate run once with per-kernel events), one parameter at
-// a time.  Choices are cached per (sigma, g, k, SM count, window and
+// a time; then the dense-level mode (never / cost model / every qualifying
+// level) by the time of all stages together.  Choices are cached per (sigma, g, k, SM count, window and
 // sequence-count buckets) for the life of the process.
 
 struct TuneChoice {
@@ -1580,15 +1593,18 @@ struct TuneChoice {
   int64_t chunk_elems;
   int accum_threads;
   int64_t group_bytes;
+  int dense;
 };
 
 std::mutex g_tune_mu;
 std::unordered_map<uint64_t, TuneChoice> g_tune_cache;
 
+// Time of the named stages of the last profiled call (all stages when
+// `a` is null).
 double stage_ms(gakco_ctx* c, const char* a, const char* b = nullptr) {
   double t = 0;
   for (auto& kv : c->timings)
-    if (kv.first == a || (b && kv.first == b)) t += kv.second.first;
+    if (!a || kv.first == a || (b && kv.first == b)) t += kv.second.first;
   return t;
 }
 
@@ -1622,6 +1638,7 @@ int autotune(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64_
       c->chunk_elems = it->second.chunk_elems;
       c->accum_threads = it->second.accum_threads;
       c->group_bytes = it->second.group_bytes;
+      c->dense = it->second.dense;
       drop_graph(c);
       report = "cached";
       return GAKCO_OK;
@@ -1638,6 +1655,7 @@ int autotune(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64_
   const int saved_profile = c->profile, saved_engine = c->engine;
   c->profile = 1;
   c->engine = 0;
+  c->dense = 0;
   auto trial = [&](const char* s1, const char* s2, double& ms) -> int {
     Plan p;
     int r = plan_datasets(c, w, p, nd, codes, off, n, Kp.data(), nullptr, nullptr, true);
@@ -1681,16 +1699,26 @@ int autotune(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64_
   }
   c->accum_threads = best_th;
   c->group_bytes = best_gb;
+  // Dense-level mode, by the time of every stage.
+  int best_dense = 0;
+  best = 1e30;
+  for (int dm : {0, 1, 2}) {
+    if (rc != GAKCO_OK) break;
+    c->dense = dm;
+    if ((rc = trial(nullptr, nullptr, t)) != GAKCO_OK) break;
+    if (t < best) best = t, best_dense = dm;
+  }
+  c->dense = best_dense;
   c->profile = saved_profile;
   c->engine = saved_engine;
   drop_graph(c);
   if (rc != GAKCO_OK) return rc;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = {best_rb, best_ch, best_th, best_gb};
+    g_tune_cache[key] = {best_rb, best_ch, best_th, best_gb, best_dense};
   }
-  snprintf(buf, sizeof buf, "radix_bits=%d chunk_elems=%lld accum_threads=%d group_bytes=%lld", best_rb,
-           (long long)best_ch, best_th, (long long)best_gb);
+  snprintf(buf, sizeof buf, "radix_bits=%d chunk_elems=%lld accum_threads=%d group_bytes=%lld dense=%d", best_rb,
+           (long long)best_ch, best_th, (long long)best_gb, best_dense);
   report = buf;
   return GAKCO_OK;
 }
@@ -1899,10 +1927,19 @@ int gakco_get_stat(const gakco_ctx* c, int key, double* v) {
       *v = c->last_windows;
       return GAKCO_OK;
     case GAKCO_STAT_DENSE_PROBLEMS:
-      *v = c->last_dense_probs;
+      *v = c->plan_dense_probs;
       return GAKCO_OK;
     case GAKCO_STAT_DENSE_FLOPS:
-      *v = c->last_dense_flops;
+      *v = c->plan_dense_flops;
+      return GAKCO_OK;
+    case GAKCO_STAT_DENSE_ISSUED_FLOPS:
+      *v = c->plan_dense_issued;
+      return GAKCO_OK;
+    case GAKCO_STAT_DENSE_BYTES:
+      *v = c->plan_dense_bytes;
+      return GAKCO_OK;
+    case GAKCO_STAT_SORT_BYTES:
+      *v = c->plan_sort_bytes;
       return GAKCO_OK;
     case GAKCO_STAT_SERVED_BATCHES: {
       std::lock_guard<std::mutex> lk(cc->mu);
