@@ -109,16 +109,20 @@ const char *gakco_last_error(const gakco_ctx *ctx);
 #define GAKCO_OPT_SERVE_MAX_WINDOWS 12 /* serving: test windows per micro-batch (default 2^19) */
 #define GAKCO_OPT_SERVE_MEM_BYTES 13 /* serving: device-memory budget of busy slots (0 = none) */
 /* Dense levels (batched Gram engine only).  For a level m whose masked
- * keys have at most 16 bits, and a dataset in which no sequence has more
- * than 511 windows, countAndUpdate (Section 2.2, Alg. 1) can run as a
- * dense contraction C_m += A A^T on the tensor cores, A holding the count
- * of every (mask, (g-m)-mer) per sequence.  Results are identical (exact
- * integer arithmetic).  0 = never (default), 1 = where a cost model
- * expects it to be faster, 2 = every qualifying level. */
+ * keys have at most 16 bits, countAndUpdate (Section 2.2, Alg. 1) can run
+ * as a dense contraction C_m += A A^T on the tensor cores, A holding the
+ * count of every (mask, (g-m)-mer) per sequence (in e4m3 up to 16; larger
+ * counts are corrected exactly on the side).  Results are identical.
+ * 0 = never (default), 1 = where a cost model expects it to be faster,
+ * 2 = every qualifying level. */
 #define GAKCO_OPT_DENSE 14
-#define GAKCO_OPT_DENSE_BYTES 15    /* device bytes of the A matrices of one dense wave
-                                       (default 2 GiB); a level whose one-mask A exceeds
-                                       it stays sparse */
+#define GAKCO_OPT_DENSE_BYTES 15    /* device bytes of the count matrices of one dense
+                                       wave (default 16 GiB, at most a quarter of the
+                                       device); a level whose one-mask matrix exceeds it
+                                       stays sparse */
+#define GAKCO_OPT_DENSE_OVERFLOW 16 /* entries of the list of counts above 16 per dense
+                                       wave (default 32768); a call that needs more runs
+                                       again with every level sparse */
 int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 
 /*

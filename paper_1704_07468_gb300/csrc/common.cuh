@@ -80,6 +80,7 @@ enum : uint32_t {
   kErrBadEntry = 2u,       // entry index out of range
   kErrBadCode = 4u,        // a symbol >= sigma in the input
   kErrTimeout = 8u,        // a bounded wait in a pipelined kernel ran out
+  kErrDenseOverflow = 16u, // the dense overflow list ran out of room
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -103,13 +104,14 @@ struct Work {
   cudaStream_t cs = nullptr;
   DevBuf fullkey, wid, ewin, eseq, efe, keyA, keyB, valA, valB, hist, tcnt, segtot, estart,
       etseq, efid, fstart, tables, codes, outK, outKhat, outNm, rinv, status, Cplain, Cacc, ea, eb,
-      Cd, Cx, Adense, dmaxc;
+      Cd, Cx, Adense, dmaxc, dovf;
   void* h_tables = nullptr;
   size_t h_tables_cap = 0;
   void* h_status = nullptr;
   void* h_io = nullptr;  // pinned staging of a serving slot
   size_t h_io_cap = 0;
   int64_t launches = 0;
+  bool dense_overflow = false;  // the last run's dense overflow list ran out of room
   std::string err;
   double pairs = 0, entries = 0, windows = 0;
 
@@ -117,7 +119,7 @@ struct Work {
     return {&fullkey, &wid, &ewin,   &eseq,  &efe,  &keyA,  &keyB,  &valA,    &valB,
             &hist,    &tcnt,    &segtot, &estart, &etseq, &efid, &fstart, &tables, &codes,
             &outK,    &outKhat, &outNm,  &rinv,  &status, &Cplain, &Cacc, &ea,    &eb,
-            &Cd,      &Cx,      &Adense, &dmaxc};
+            &Cd,      &Cx,      &Adense, &dmaxc,  &dovf};
   }
   size_t bytes() {
     size_t s = 0;
@@ -183,7 +185,8 @@ struct gakco_ctx {
   int64_t serve_max_windows = (int64_t)1 << 19;
   int64_t serve_mem_bytes = 0;  // 0: no budget
   int dense = 0;                            // 0 off, 1 cost model, 2 every eligible level
-  int64_t dense_bytes = (int64_t)2 << 30;   // A matrices per dense wave
+  int64_t dense_bytes = (int64_t)16 << 30;  // A matrices per dense wave (capped at create)
+  int64_t dense_overflow = 32768;           // overflow-list entries per dense wave
 
   std::string err;
   int device = 0;
@@ -354,15 +357,20 @@ struct Bracket {
 // One dense problem (see DenseProb) before its device addresses are known.
 struct DenseHost {
   uint32_t ds, level, mfirst, mcount, n, n_pad, key_bits, row0;
-  uint64_t ld, a_off;  // columns; element offset of A in the A buffer
+  uint64_t ld, a_off;  // columns; byte offset of A in the A buffer
 };
 
 struct DenseWave {
   uint32_t p0, np;       // problems
   uint32_t t0, nt;       // tiles
-  uint32_t rows, colblocks;
-  uint64_t elems;        // A elements of the wave
+  uint32_t rows;         // A rows of the wave (the scatter grid)
+  uint64_t elems;        // A bytes of the wave
 };
+
+// Columns of one dense problem (a run of masks of one level): long enough
+// to amortise a tile's epilogue, short enough that a level yields many
+// tiles for the persistent GEMM to balance.
+constexpr uint64_t kDenseRunCols = 131072;
 
 struct Plan {
   std::vector<DsHost> ds;
@@ -602,21 +610,21 @@ void plan_items(gakco_ctx* c, Plan& p) {
 // sparse route (sort, run-length, pair updates) and on the dense route
 // (scatter into A, tensor-core GEMM), from effective rates of the kernels.
 bool dense_is_cheaper(gakco_ctx* c, const DsHost& D, uint32_t n_pad, int kb) {
-  const double hbm = 6.0e12, updates = 1.0e12, tensor = 1.0e15;
+  const double hbm = 6.0e12, updates = 1.0e12, tensor = 2.0e15;
   const double G = (double)D.G, S = std::ldexp(1.0, kb);
   const double passes = std::ceil((double)kb / (double)c->radix_bits);
   const double sparse = G * (passes * 16.0 + 48.0) / hbm + 0.5 * (G * G / S + G) / updates;
   const double rb = n_pad / 128.0, cb = std::ceil(n_pad / 256.0);
   const double tiles = rb * cb - std::floor(rb / 2.0) * std::ceil(rb / 2.0);
-  const double dense = tiles * 128.0 * 256.0 * 2.0 * std::max(S, 64.0) / tensor + 4.0 * n_pad * S / hbm;
+  const double dense = tiles * 128.0 * 256.0 * 2.0 * std::max(S, 128.0) / tensor + 3.0 * n_pad * S / hbm;
   return dense < sparse;
 }
 
 // Marks the (dataset, level) pairs that run on the tensor cores and cuts
-// them into problems (runs of masks whose A fits the wave budget), waves
-// and upper-triangle output tiles.  A level qualifies when every count is
-// at most kDenseMaxCount (no sequence has more windows), its masked keys
-// have at most 16 bits, and one mask's A fits the budget.
+// them into problems (runs of masks of at most kDenseRunCols columns whose
+// A fits the wave budget), waves and upper-triangle output tiles, the
+// tiles of a wave longest first.  A level qualifies when its masked keys
+// have at most 16 bits and one mask's A fits the budget.
 void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
   const int L = c->M + 1;
   p.dense.assign(p.ds.size() * (size_t)L, 0);
@@ -631,20 +639,19 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
   for (size_t d = 0; d < p.ds.size(); ++d) {
     const DsHost& D = p.ds[d];
     if (D.n == 0 || D.G == 0) continue;
-    uint32_t wmax = 0;
-    for (int32_t x = 0; x < D.n; ++x) wmax = std::max(wmax, D.woff[x + 1] - D.woff[x]);
-    if (wmax > kDenseMaxCount) continue;
     const uint32_t n_pad = (uint32_t)align_up((size_t)D.n, 128);
     for (int m = 0; m <= c->M; ++m) {
       const int kb = c->bits * (c->g - m);
       if (kb > 16) continue;
       const uint64_t S = (uint64_t)1 << kb;
-      const uint64_t per_mask = (uint64_t)n_pad * S * 2;
+      const uint64_t per_mask = (uint64_t)n_pad * S;
       if (per_mask > budget) continue;
       if (c->dense == 1 && !dense_is_cheaper(c, D, n_pad, kb)) continue;
       p.dense[d * L + m] = 1;
       const uint32_t mf = lf[m], mc = lf[m + 1] - lf[m];
-      const uint32_t gmax = (uint32_t)std::min<uint64_t>(mc, std::max<uint64_t>(1, budget / per_mask));
+      const uint64_t by_mem = std::max<uint64_t>(1, budget / per_mask);
+      const uint64_t by_cols = std::max<uint64_t>(1, kDenseRunCols / S);
+      const uint32_t gmax = (uint32_t)std::min<uint64_t>(mc, std::min(by_mem, by_cols));
       const uint32_t ng = (mc + gmax - 1) / gmax;
       for (uint32_t gi = 0; gi < ng; ++gi) {
         const uint32_t a = mf + (uint32_t)((uint64_t)mc * gi / ng);
@@ -657,7 +664,7 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
         h.n = (uint32_t)D.n;
         h.n_pad = n_pad;
         h.key_bits = (uint32_t)kb;
-        h.ld = align_up((size_t)h.mcount * S, 64);
+        h.ld = align_up((size_t)h.mcount * S, 128);
         p.dprobs.push_back(h);
       }
     }
@@ -666,14 +673,24 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
   DenseWave wv{};
   auto close = [&]() {
     if (wv.np == 0) return;
-    wv.nt = (uint32_t)(p.dtiles.size() / 3) - wv.t0;
-    p.dense_abytes = std::max<uint64_t>(p.dense_abytes, wv.elems * 2);
+    // Longest tiles first, so the persistent CTAs finish together.
+    const size_t t0 = (size_t)wv.t0 * 3, t1 = p.dtiles.size();
+    std::vector<std::array<uint32_t, 3>> tl((t1 - t0) / 3);
+    for (size_t i = 0; i < tl.size(); ++i)
+      tl[i] = {p.dtiles[t0 + 3 * i], p.dtiles[t0 + 3 * i + 1], p.dtiles[t0 + 3 * i + 2]};
+    std::stable_sort(tl.begin(), tl.end(), [&](const std::array<uint32_t, 3>& a, const std::array<uint32_t, 3>& b) {
+      return p.dprobs[a[0]].ld > p.dprobs[b[0]].ld;
+    });
+    for (size_t i = 0; i < tl.size(); ++i)
+      for (int q = 0; q < 3; ++q) p.dtiles[t0 + 3 * i + q] = tl[i][q];
+    wv.nt = (uint32_t)(tl.size());
+    p.dense_abytes = std::max<uint64_t>(p.dense_abytes, wv.elems);
     p.dwaves.push_back(wv);
   };
   for (uint32_t i = 0; i < (uint32_t)p.dprobs.size(); ++i) {
     DenseHost& h = p.dprobs[i];
     const uint64_t el = (uint64_t)h.n_pad * h.ld;
-    if (wv.np > 0 && (wv.elems + el) * 2 > budget) {
+    if (wv.np > 0 && wv.elems + el > budget) {
       close();
       wv = DenseWave{};
     }
@@ -685,7 +702,6 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
     h.row0 = wv.rows;
     wv.elems += el;
     wv.rows += h.n_pad;
-    wv.colblocks = std::max<uint32_t>(wv.colblocks, (uint32_t)((h.ld + kDenseScatterCols - 1) / kDenseScatterCols));
     wv.np++;
     const uint32_t rb = h.n_pad / 128, cb = (h.n_pad + 255) / 256;
     for (uint32_t I = 0; I < rb; ++I)
@@ -695,7 +711,7 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
         p.dense_issued += 2.0 * 128.0 * 256.0 * (double)h.ld;
       }
     p.dense_flops += 2.0 * (double)h.mcount * std::ldexp(1.0, (int)h.key_bits) * 0.5 * h.n * (h.n + 1.0);
-    p.dense_bytes += 2.0 * (double)el;
+    p.dense_bytes += (double)el;
   }
   close();
 }
@@ -789,7 +805,7 @@ int fill_dense(gakco_ctx* c, Work& w, Plan& p, Tables& t) {
   for (size_t i = 0; i < p.dprobs.size(); ++i) {
     const DenseHost& h = p.dprobs[i];
     DenseProb q{};
-    q.A = (uint16_t*)w.Adense.p + h.a_off;
+    q.A = (uint8_t*)w.Adense.p + h.a_off;
     q.C = (uint32_t*)w.Cacc.p + cacc[h.ds] + (uint64_t)h.level * h.n * h.n;
     q.maxc = (uint32_t*)w.dmaxc.p + i;
     q.tmap = base + p.o_tmaps + i * kDenseTmapBytes;
@@ -868,7 +884,8 @@ int plan_memory_and_tables(gakco_ctx* c, Work& w, Plan& p, bool plain) {
   if (!plain) ENSURE(Cacc, csum * 4);
   if (!p.dprobs.empty()) {
     ENSURE(Adense, p.dense_abytes);
-    ENSURE(dmaxc, p.dprobs.size() * 4);
+    ENSURE(dmaxc, (p.dprobs.size() + 1) * 4);  // + the overflow-list counter
+    ENSURE(dovf, (size_t)c->dense_overflow * sizeof(DenseOvf));
   }
   Tables t;
   add_common_tables(c, p, t);
@@ -960,15 +977,22 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
       // Dense levels: A = counts per (sequence, mask, key), C_m += A A^T.
       const DenseProb* probs = (const DenseProb*)(base + p.o_dprobs);
       const uint32_t* tiles = (const uint32_t*)(base + p.o_dtiles);
+      uint32_t* ovf_n = (uint32_t*)w.dmaxc.p + p.dprobs.size();
+      const uint32_t cap = (uint32_t)c->dense_overflow;
       cudaMemsetAsync(w.dmaxc.p, 0, p.dprobs.size() * 4, w.cs);
       for (const DenseWave& wv : p.dwaves) {
+        cudaMemsetAsync(ovf_n, 0, 4, w.cs);
         {
           Bracket b(c, w, "dense_scatter", 1);
-          launch_dense_scatter(probs + wv.p0, wv.np, wv.rows, wv.colblocks, (const DsPack*)(base + p.o_pack),
-                               (const MaskDesc*)(base + p.o_masks), (const uint64_t*)w.fullkey.p, w.cs);
+          launch_dense_scatter(probs + wv.p0, wv.np, wv.p0, wv.rows, (const DsPack*)(base + p.o_pack), (const MaskDesc*)(base + p.o_masks),
+                               (const uint64_t*)w.fullkey.p, ovf_n, (DenseOvf*)w.dovf.p, cap, w.cs);
         }
-        Bracket b(c, w, "dense_gemm", 1);
-        launch_dense_gemm(probs, tiles + 3 * (size_t)wv.t0, wv.nt, c->nsm, status, w.cs);
+        {
+          Bracket b(c, w, "dense_gemm", 1);
+          launch_dense_gemm(probs, tiles + 3 * (size_t)wv.t0, wv.nt, c->nsm, status, w.cs);
+        }
+        Bracket b(c, w, "dense_fix", 1);
+        launch_dense_fix(probs, ovf_n, (const DenseOvf*)w.dovf.p, cap, status, w.cs);
       }
     }
     {
@@ -1014,8 +1038,8 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
 
 uint64_t plan_key(gakco_ctx* c, const Plan& p, bool plain) {
   uint64_t h = 1469598103934665603ull;
-  int64_t o[9] = {plain, c->radix_bits, c->chunk_elems, c->accum_threads, c->smem_cols,
-                  (int64_t)p.ds.size(), c->group_bytes, c->dense, c->dense_bytes};
+  int64_t o[10] = {plain, c->radix_bits, c->chunk_elems, c->accum_threads, c->smem_cols,
+                   (int64_t)p.ds.size(), c->group_bytes, c->dense, c->dense_bytes, c->dense_overflow};
   h = fnv1a(h, o, sizeof o);
   for (const DsHost& D : p.ds) {
     const void* ptrs[4] = {D.codes, D.K, D.Khat, D.Nm};
@@ -1037,11 +1061,16 @@ int check_status(gakco_ctx* c, Work& w) {
   if (st & kErrKneCM) return wfail(w, GAKCO_E_INTERNAL, "internal check failed: sum h_m N_m != C_M");
   if (st & kErrBadEntry) return wfail(w, GAKCO_E_INTERNAL, "internal check failed: entry out of range");
   if (st & kErrTimeout) return wfail(w, GAKCO_E_TIMEOUT, "a bounded wait in the dense GEMM ran out");
+  if (st & kErrDenseOverflow) {
+    w.dense_overflow = true;
+    return wfail(w, GAKCO_E_INTERNAL, "dense overflow list full");
+  }
   if (st) return wfail(w, GAKCO_E_INTERNAL, "device status 0x%x", st);
   return GAKCO_OK;
 }
 
 int sync_and_check(gakco_ctx* c, Work& w) {
+  w.dense_overflow = false;
   cudaError_t e = cudaMemcpyAsync(w.h_status, w.status.p, 128, cudaMemcpyDeviceToHost, w.cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(w.cs);
   if (e != cudaSuccess) return wcuda(w, e, "engine run");
@@ -1063,8 +1092,34 @@ int sync_and_check(gakco_ctx* c, Work& w) {
   return check_status(c, w);
 }
 
+int run_gram_once(gakco_ctx* c, Plan& p, cudaStream_t user);
+
 // The batched / plain Gram engine on device buffers, on the context's Work.
+// When a dense level met more counts above 16 than its overflow list holds,
+// the call is run again with every level on the sparse route, so results
+// stay exact.
 int run_gram(gakco_ctx* c, Plan& p, cudaStream_t user) {
+  c->main.dense_overflow = false;
+  Plan q;  // the validated datasets alone, for a second run
+  q.ds = p.ds;
+  q.gtot = p.gtot;
+  q.nseq = p.nseq;
+  q.nmax = p.nmax;
+  q.want_nm = p.want_nm;
+  q.want_khat = p.want_khat;
+  int rc = run_gram_once(c, p, user);
+  if (rc != GAKCO_OK && c->main.dense_overflow && c->dense != 0) {
+    const int saved = c->dense;
+    c->dense = 0;
+    drop_graph(c);
+    rc = run_gram_once(c, q, user);
+    c->dense = saved;
+    drop_graph(c);
+  }
+  return rc;
+}
+
+int run_gram_once(gakco_ctx* c, Plan& p, cudaStream_t user) {
   Work& w = c->main;
   const bool plain = c->engine == 1;
   w.launches = 0;
@@ -1799,6 +1854,12 @@ int gakco_create(int sigma, int g, int k, gakco_ctx** out) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
   if (e == cudaSuccess) e = (cudaError_t)prep_init();
   if (e == cudaSuccess) e = (cudaError_t)dense_init();
+  if (e == cudaSuccess) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && tot > 0)
+      c->dense_bytes = std::min<int64_t>(c->dense_bytes, (int64_t)(tot / 4));
+    cudaGetLastError();
+  }
   if (e == cudaSuccess && init_work(c->main) != GAKCO_OK) e = cudaErrorMemoryAllocation;
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1887,6 +1948,10 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
     case GAKCO_OPT_DENSE_BYTES:
       if (v < 1) return fail(c, GAKCO_E_INVALID, "dense bytes must be >= 1");
       c->dense_bytes = v;
+      break;
+    case GAKCO_OPT_DENSE_OVERFLOW:
+      if (v < 1 || v > ((int64_t)1 << 26)) return fail(c, GAKCO_E_INVALID, "overflow entries must be 1..2^26");
+      c->dense_overflow = v;
       break;
     default:
       return fail(c, GAKCO_E_INVALID, "unknown option %d", key);

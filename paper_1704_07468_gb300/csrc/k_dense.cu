@@ -1,5 +1,6 @@
 // Dense levels: C_m += F^T F as a dense contraction on the tensor cores
-// (tcgen05.mma, kind::f16, f32 accumulators in tensor memory).
+// (tcgen05.mma, kind::f8f6f4 with e4m3 operands, f32 accumulators in
+// tensor memory).
 //
 // For one mask the count matrix F has a row per feature and a column per
 // sequence, and countAndUpdate adds F^T F to C_m (Section 2.2, steps 2-5;
@@ -9,25 +10,30 @@
 // sequence and a column per (mask, key), so that C_m += A A^T.  No sort is
 // needed: the scatter kernel counts A[x, (mask, key)] directly.
 //
-// Exactness.  Counts are integers <= 511 (the host routes a level here only
-// when no sequence has more than 511 windows) and are exact in f16;
-// products and partial sums are exact in the f32 accumulators while they
-// stay below 2^24.  The GEMM therefore closes an accumulation "round" and
-// adds it into the int32 C every floor((2^24 - 1) / (64 maxc^2)) stages of
-// 64 columns, maxc being the largest count the scatter kernel saw.
+// Exactness.  A holds D0 = min(count, 16), which e4m3 represents exactly;
+// products (<= 256) and partial sums are exact in the f32 accumulators
+// while they stay below 2^24, so the GEMM closes an accumulation "round"
+// and adds it into the int32 C every floor((2^24 - 1) / (128 maxD0^2))
+// stages of 128 columns, maxD0 being the largest D0 the scatter kernel
+// wrote.  A count c > 16 is also appended to an overflow list, and the fix
+// kernel adds the exact difference A A^T - D0 D0^T, which is nonzero only
+// in rows and columns of overflowing sequences:
+//   (x, y), y without overflow at the column:  (c_x - 16) D0(y)
+//   (x, y), both overflowing at the column:    c_x c_y - 256
+// (the second as (c_x-16) 16 + (c_y-16) 16 + (c_x-16)(c_y-16), one term
+// from each entry's row scan and the product from the pair scan).
 //
 // GEMM structure.  One CTA per SM walks a list of (problem, I, J) output
 // tiles of 128 rows x 256 columns (upper triangle only: C is symmetric).
-// Warp 5 loads 64-column slices of A's rows I*128.. and J*256.. with TMA
+// Warp 5 loads 128-column slices of A's rows I*128.. and J*256.. with TMA
 // (128-byte swizzle) into a four-stage ring; one thread of warp 4 issues
-// tcgen05.mma (M = 128, N = 256, K = 16) into one of two 256-column TMEM
+// tcgen05.mma (M = 128, N = 256, K = 32) into one of two 256-column TMEM
 // accumulators; warps 0-3 read the finished accumulator back with
 // tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. tile rows) and add
 // the upper-triangle part into C.  Hand-offs use mbarriers.  Every wait is
 // bounded: a timeout raises an error bit, stops every role, waits (bounded)
 // for the copies and MMAs already issued, and frees tensor memory.
 #include <cuda.h>  // CUtensorMap and its enums; the encoder is fetched at run time
-#include <cuda_fp16.h>
 
 #include <cstdint>
 #include <mutex>
@@ -40,13 +46,14 @@ namespace gk {
 namespace {
 
 constexpr int kStages = 4;
-constexpr uint32_t kABytes = 128 * 128;  // 128 rows x 64 f16 columns
-constexpr uint32_t kBBytes = 256 * 128;  // 256 rows x 64 f16 columns
+constexpr uint32_t kABytes = 128 * 128;  // 128 rows x 128 e4m3 columns
+constexpr uint32_t kBBytes = 256 * 128;  // 256 rows x 128 e4m3 columns
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
 constexpr int kMmaWarp = 4, kTmaWarp = 5;
 constexpr int kGemmThreads = 192;
 constexpr uint32_t kTmemCols = 512;  // two 128 x 256 f32 accumulators
-constexpr int kScatterThreads = 256;
+constexpr int kScatterThreads = 512;
+constexpr int kScatterMasks = 16;  // masks of one scatter block held in shared memory
 constexpr long long kWaitCycles = 4000000000ll;  // about 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -124,25 +131,48 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// Stages (64 columns each) per exact accumulation round.
+// Stages (128 columns each) per exact accumulation round.
 __device__ __forceinline__ uint32_t stages_per_round(const uint32_t* maxc, uint32_t nk) {
   const uint32_t mc = *(const volatile uint32_t*)maxc;
   if (mc == 0) return nk > 0 ? nk : 1;
-  uint64_t s = (uint64_t)((1u << 24) - 1) / (64ull * mc * mc);
+  uint64_t s = (uint64_t)((1u << 24) - 1) / (128ull * mc * mc);
   if (s < 1) s = 1;
   return (uint32_t)(s < nk ? s : nk);
 }
 
+// Two 16-bit counts (each <= 16) -> two e4m3 bytes, low count in the low
+// byte.  The counts become exact f16 values through the 1024-offset form
+// (the f16 bits of 1024 + v are 0x6400 | v), then one hardware conversion
+// packs both.
+__device__ __forceinline__ uint32_t e4m3x2_of_counts(uint32_t clamped) {
+  const uint32_t biased = clamped | 0x64006400u;
+  uint32_t h;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(h) : "r"(biased), "r"(0x64006400u));
+  uint16_t e;
+  asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;" : "=h"(e) : "r"(h));
+  return e;
+}
+
+// The integer an e4m3 byte of a count (0..16) encodes: exponent bias 7,
+// three mantissa bits, v = 2^(e-7) (1 + m/8).
+__device__ __forceinline__ uint32_t e4m3_small_value(uint32_t b) {
+  if (b == 0) return 0;
+  return ((8 + (b & 7)) << ((b >> 3) - 7)) >> 3;
+}
+
 }  // namespace
 
-// Builds the rows of A: one block per (row of the wave, block of
-// kDenseScatterCols columns).  Counts are gathered in shared memory and the
-// whole column block is written out (zeros included), so A needs no
-// separate clearing; padded rows come out all zero.
+// Builds the rows of A: one block per row of the wave, walking the row's
+// column chunks of kDenseScatterCols.  Counts are gathered in shared memory
+// and each chunk is written out whole (zeros included), so A needs no
+// separate clearing; padded rows come out all zero.  The conversion loop
+// clears the counts it has read, ready for the next chunk.
 __global__ void __launch_bounds__(kScatterThreads)
-k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, const DsPack* __restrict__ dsp,
-                const MaskDesc* __restrict__ masks, const uint64_t* __restrict__ fullkey) {
-  extern __shared__ uint32_t cnt[];
+k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p0, const DsPack* __restrict__ dsp,
+                const MaskDesc* __restrict__ masks, const uint64_t* __restrict__ fullkey, uint32_t* __restrict__ ovf_n,
+                DenseOvf* __restrict__ ovf, uint32_t ovf_cap) {
+  extern __shared__ uint32_t cnt[];  // two 16-bit counts per word (counts <= 65535 windows)
+  __shared__ MaskDesc smask[kScatterMasks];
   const uint32_t bx = blockIdx.x, tid = threadIdx.x;
   uint32_t lo = 0, hi = nprobs;  // last problem with row0 <= bx
   while (hi - lo > 1) {
@@ -154,48 +184,117 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, const DsPa
   }
   const DenseProb& P = probs[lo];
   const uint64_t ld = P.ld;
-  const uint64_t c0 = (uint64_t)blockIdx.y * kDenseScatterCols;
-  if (c0 >= ld) return;
   const uint32_t x = bx - P.row0;
-  const uint32_t ncol = (uint32_t)(ld - c0 < (uint64_t)kDenseScatterCols ? ld - c0 : kDenseScatterCols);
-  for (uint32_t i = tid; i < ncol / 4; i += kScatterThreads) ((uint4*)cnt)[i] = make_uint4(0, 0, 0, 0);
-  __syncthreads();
+  const uint32_t kb = P.key_bits;
+  uint32_t w0 = 0, nw = 0;
+  const uint64_t* fk = fullkey;
   if (x < P.n) {
     const DsPack& D = dsp[P.ds];
-    const uint32_t w0 = D.woff[x], nw = D.woff[x + 1] - w0;
-    const uint32_t kb = P.key_bits;
+    w0 = D.woff[x];
+    nw = D.woff[x + 1] - w0;
+    fk = fullkey + D.win0 + w0;
+  }
+  {
+    const uint32_t words = (uint32_t)(ld < (uint64_t)kDenseScatterCols ? ld : kDenseScatterCols) / 2;
+    for (uint32_t i = tid; i < words / 4; i += kScatterThreads) ((uint4*)cnt)[i] = make_uint4(0, 0, 0, 0);
+  }
+  uint32_t mx2 = 0;  // two 16-bit running maxima
+  for (uint64_t c0 = 0; c0 < ld; c0 += kDenseScatterCols) {
+    const uint32_t ncol = (uint32_t)(ld - c0 < (uint64_t)kDenseScatterCols ? ld - c0 : kDenseScatterCols);
     const uint32_t mu0 = (uint32_t)(c0 >> kb);
     uint32_t mu1 = (uint32_t)((c0 + ncol - 1) >> kb) + 1;
     if (mu1 > P.mcount) mu1 = P.mcount;
-    const uint32_t nmu = mu1 > mu0 ? mu1 - mu0 : 0;
-    const uint64_t* fk = fullkey + D.win0 + w0;
-    for (uint32_t i = tid; i < nw * nmu; i += kScatterThreads) {
-      const uint32_t w = i / nmu, mu = mu0 + i % nmu;
-      const uint64_t key = masked_key(fk[w], masks[P.mfirst + mu]);
-      const uint64_t col = (((uint64_t)mu << kb) | key) - c0;
-      if (col < ncol) atomicAdd(&cnt[col], 1u);
+    const uint32_t nmu = (nw > 0 && mu1 > mu0) ? mu1 - mu0 : 0;
+    const bool staged = nmu <= (uint32_t)kScatterMasks;
+    if (staged) {
+      // The chunk's masks, for warp-broadcast reads below.
+      const uint32_t words = nmu * (uint32_t)(sizeof(MaskDesc) / 4);
+      const uint32_t* src = (const uint32_t*)(masks + P.mfirst + mu0);
+      for (uint32_t i = tid; i < words; i += kScatterThreads) ((uint32_t*)smask)[i] = src[i];
     }
+    __syncthreads();
+    // Mask-major: the lanes of a warp mostly share one mask and read
+    // consecutive windows.
+    for (uint32_t i = tid; i < nw * nmu; i += kScatterThreads) {
+      const uint32_t mi = i / nw, w = i - mi * nw;
+      const MaskDesc& md = staged ? smask[mi] : masks[P.mfirst + mu0 + mi];
+      const uint64_t key = masked_key(fk[w], md);
+      const uint64_t col = (((uint64_t)(mu0 + mi) << kb) | key) - c0;
+      if (col < ncol) atomicAdd(&cnt[col >> 1], 1u << (16 * (uint32_t)(col & 1)));
+    }
+    __syncthreads();
+    uint4* out = (uint4*)(P.A + (uint64_t)x * ld + c0);
+    for (uint32_t j = tid; j < ncol / 16; j += kScatterThreads) {
+      uint4* cw = (uint4*)cnt + 2 * j;
+      const uint4 a = cw[0], b = cw[1];
+      cw[0] = make_uint4(0, 0, 0, 0);
+      cw[1] = make_uint4(0, 0, 0, 0);
+      const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+      uint32_t over = 0, e[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t cl = __vminu2(w[q], 0x00100010u);
+        over |= __vcmpgtu2(w[q], 0x00100010u);
+        mx2 = __vmaxu2(mx2, cl);
+        e[q] = e4m3x2_of_counts(cl);
+      }
+      out[j] = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16), e[6] | (e[7] << 16));
+      if (over) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const uint32_t c = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+          if (c > 16) {
+            const uint32_t slot = atomicAdd(ovf_n, 1u);
+            if (slot < ovf_cap) ovf[slot] = DenseOvf{p0 + lo, x, (uint32_t)(c0 + 16 * j + q), c};
+          }
+        }
+      }
+    }
+    // The next chunk's counting waits at its first barrier for this
+    // conversion (and its clearing) to finish.
   }
-  __syncthreads();
-  uint32_t mymax = 0;
-  uint4* out = (uint4*)(P.A + (uint64_t)x * ld + c0);
-  for (uint32_t j = tid; j < ncol / 8; j += kScatterThreads) {
-    const uint4 a = ((const uint4*)cnt)[2 * j], b = ((const uint4*)cnt)[2 * j + 1];
-    mymax = max(mymax, max(max(max(a.x, a.y), max(a.z, a.w)), max(max(b.x, b.y), max(b.z, b.w))));
-    const __half2 h0 = __floats2half2_rn((float)a.x, (float)a.y);
-    const __half2 h1 = __floats2half2_rn((float)a.z, (float)a.w);
-    const __half2 h2 = __floats2half2_rn((float)b.x, (float)b.y);
-    const __half2 h3 = __floats2half2_rn((float)b.z, (float)b.w);
-    uint4 v;
-    v.x = *(const uint32_t*)&h0;
-    v.y = *(const uint32_t*)&h1;
-    v.z = *(const uint32_t*)&h2;
-    v.w = *(const uint32_t*)&h3;
-    out[j] = v;
-  }
+  uint32_t mymax = max(mx2 & 0xFFFFu, mx2 >> 16);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mymax = max(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
   if ((tid & 31) == 0 && mymax) atomicMax(P.maxc, mymax);
+}
+
+// Exact correction for counts above 16 (see the top of this file): one warp
+// per overflow entry scans the entry's column of A over every row, then the
+// later entries of the list for the same (problem, column).
+__global__ void __launch_bounds__(256)
+k_dense_fix(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ ovf_n, const DenseOvf* __restrict__ ovf,
+            uint32_t ovf_cap, uint32_t* __restrict__ status) {
+  const uint32_t E = *ovf_n;
+  if (E > ovf_cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kErrDenseOverflow);
+    return;
+  }
+  const uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i >= E) return;
+  const DenseOvf e = ovf[i];
+  const DenseProb& P = probs[e.prob];
+  const uint32_t n = P.n, x = e.x, d = e.count - 16;
+  const uint8_t* colp = P.A + e.col;
+  uint32_t* C = P.C;
+  for (uint32_t y = lane; y < n; y += 32) {
+    if (y == x) {
+      atomicAdd(&C[(uint64_t)x * n + x], 32u * d + d * d);  // (16 + d)^2 - 16^2
+      continue;
+    }
+    const uint32_t v = e4m3_small_value(colp[(uint64_t)y * P.ld]);
+    if (v) {
+      const uint32_t r = min(x, y), q = max(x, y);
+      atomicAdd(&C[(uint64_t)r * n + q], d * v);
+    }
+  }
+  for (uint32_t j = i + 1 + lane; j < E; j += 32) {
+    const DenseOvf f = ovf[j];
+    if (f.prob == e.prob && f.col == e.col) {
+      const uint32_t r = min(x, f.x), q = max(x, f.x);
+      atomicAdd(&C[(uint64_t)r * n + q], d * (f.count - 16));
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kGemmThreads, 1)
@@ -238,7 +337,7 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
         const DenseProb& P = probs[tiles[3 * t]];
         const int y_a = (int)(tiles[3 * t + 1] * 128), y_b = (int)(tiles[3 * t + 2] * 256);
         const void* tm = P.tmap;
-        const uint32_t nk = (uint32_t)(P.ld / 64);
+        const uint32_t nk = (uint32_t)(P.ld / 128);
         for (uint32_t k = 0; k < nk; ++k, ++it) {
           const uint32_t s = it % kStages;
           if (!bar_wait(&empty_bar[s], ((it / kStages) & 1) ^ 1, &abort_flag)) {
@@ -247,9 +346,9 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
           }
           const uint32_t dst = smem_u32(sm + s * kStageBytes);
           bar_expect_tx(&full_bar[s], kStageBytes);
-          tma_load(dst, tm, (int)(k * 64), y_a, &full_bar[s]);
-          tma_load(dst + kABytes, tm, (int)(k * 64), y_b, &full_bar[s]);
-          tma_load(dst + kABytes + kABytes, tm, (int)(k * 64), y_b + 128, &full_bar[s]);
+          tma_load(dst, tm, (int)(k * 128), y_a, &full_bar[s]);
+          tma_load(dst + kABytes, tm, (int)(k * 128), y_b, &full_bar[s]);
+          tma_load(dst + kABytes + kABytes, tm, (int)(k * 128), y_b + 128, &full_bar[s]);
         }
       }
       // Let the copies already issued land before the block can exit.
@@ -261,12 +360,13 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
     }
   } else if (warp == kMmaWarp) {
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | ((256u >> 3) << 17) | ((128u >> 4) << 24);  // f32 += f16 x f16
+      // f32 accumulator, e4m3 A and B (type code 0), K-major, N = 256, M = 128.
+      const uint32_t idesc = (1u << 4) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
       uint32_t it = 0, round = 0;
       bool stop = false;
       for (uint32_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
         const DenseProb& P = probs[tiles[3 * t]];
-        const uint32_t nk = (uint32_t)(P.ld / 64);
+        const uint32_t nk = (uint32_t)(P.ld / 128);
         const uint32_t spr = stages_per_round(P.maxc, nk);
         for (uint32_t k = 0; k < nk && !stop; ++round) {
           const uint32_t b = round & 1;
@@ -290,7 +390,7 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
               const uint32_t acc = (kk > k || j > 0) ? 1u : 0u;
               asm volatile(
                   "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                  "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
                   "l"(smem_desc(a0 + j * 32)), "l"(smem_desc(b0 + j * 32)), "r"(idesc), "r"(acc));
             }
             mma_commit(&empty_bar[s]);
@@ -311,7 +411,7 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
     for (uint32_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
       const DenseProb& P = probs[tiles[3 * t]];
       const uint32_t n = P.n;
-      const uint32_t nk = (uint32_t)(P.ld / 64);
+      const uint32_t nk = (uint32_t)(P.ld / 128);
       const uint32_t spr = stages_per_round(P.maxc, nk);
       const uint32_t nr = (nk + spr - 1) / spr;
       const uint32_t row = tiles[3 * t + 1] * 128 + warp * 32 + lane;
@@ -364,7 +464,7 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
   }
 }
 
-size_t dense_scatter_smem() { return (size_t)kDenseScatterCols * 4; }
+size_t dense_scatter_smem() { return (size_t)kDenseScatterCols * 2; }
 size_t dense_gemm_smem() { return (size_t)kStages * kStageBytes + 1024; }
 
 int dense_init() {
@@ -404,20 +504,27 @@ int dense_encode_tmap(void* out, void* A, uint64_t ld, uint64_t rows) {
   EncodeTiledFn fn = encoder();
   if (!fn) return -1;
   const cuuint64_t dims[2] = {ld, rows};
-  const cuuint64_t strides[1] = {ld * 2};
-  const cuuint32_t box[2] = {64, 128};
+  const cuuint64_t strides[1] = {ld};
+  const cuuint32_t box[2] = {128, 128};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = fn((CUtensorMap*)out, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, A, dims, strides, box, estr,
+  const CUresult r = fn((CUtensorMap*)out, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, A, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : (int)r;
 }
 
-void launch_dense_scatter(const DenseProb* d_probs, uint32_t nprobs, uint32_t rows, uint32_t colblocks,
-                          const DsPack* dsp, const MaskDesc* masks, const uint64_t* fullkey, cudaStream_t st) {
-  if (nprobs == 0 || rows == 0 || colblocks == 0) return;
-  k_dense_scatter<<<dim3(rows, colblocks), kScatterThreads, dense_scatter_smem(), st>>>(d_probs, nprobs, dsp,
-                                                                                        masks, fullkey);
+void launch_dense_scatter(const DenseProb* d_probs, uint32_t nprobs, uint32_t p0, uint32_t rows,
+                          const DsPack* dsp, const MaskDesc* masks, const uint64_t* fullkey,
+                          uint32_t* ovf_n, DenseOvf* ovf, uint32_t ovf_cap, cudaStream_t st) {
+  if (nprobs == 0 || rows == 0) return;
+  k_dense_scatter<<<rows, kScatterThreads, dense_scatter_smem(), st>>>(
+      d_probs, nprobs, p0, dsp, masks, fullkey, ovf_n, ovf, ovf_cap);
+}
+
+void launch_dense_fix(const DenseProb* d_probs, const uint32_t* ovf_n, const DenseOvf* ovf, uint32_t ovf_cap,
+                      uint32_t* status, cudaStream_t st) {
+  const uint32_t blocks = (ovf_cap + 7) / 8;
+  k_dense_fix<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(d_probs, ovf_n, ovf, ovf_cap, status);
 }
 
 void launch_dense_gemm(const DenseProb* d_probs, const uint32_t* d_tiles, uint32_t ntiles, int nsm,

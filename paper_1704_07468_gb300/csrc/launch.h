@@ -161,13 +161,15 @@ void launch_cross_combine(const CrossParams& p, int32_t* K, double* Khat, cudaSt
 // One dense problem: the count matrix A of one dataset over a run of masks
 // of one level; row x = sequence x (rows padded to a multiple of 128, the
 // padding all zero), column mu * 2^key_bits + key = (mask mfirst + mu,
-// masked key).  C_m += A A^T runs on the tensor cores.
+// masked key), entry e4m3(min(count, 16)).  C_m += A A^T runs on the
+// tensor cores; counts above 16 go to the overflow list and are corrected
+// exactly by the fix kernel.
 struct DenseProb {
-  uint16_t* A;          // f16 bits, n_pad x ld, row-major
+  uint8_t* A;           // e4m3 bytes, n_pad x ld, row-major
   uint32_t* C;          // n x n cumulative profile C_m of the dataset
-  uint32_t* maxc;       // largest count of A (written by the scatter kernel)
+  uint32_t* maxc;       // largest entry of A as an integer (written by the scatter kernel)
   const void* tmap;     // TMA descriptor of A (kDenseTmapBytes, 64-byte aligned)
-  uint64_t ld;          // columns of A, a multiple of 64
+  uint64_t ld;          // columns of A, a multiple of 128
   uint32_t n, n_pad;    // sequences; rows of A
   uint32_t ds;          // dataset (DsPack index)
   uint32_t mfirst, mcount;
@@ -175,19 +177,32 @@ struct DenseProb {
   uint32_t row0;        // first row of the problem in its wave's scatter grid
   uint32_t pad;
 };
-constexpr int kDenseScatterCols = 16384;  // columns per scatter block
+
+// A count above 16: problem (plan-wide index), row, column, count.
+struct DenseOvf {
+  uint32_t prob, x, col, count;
+};
+
+constexpr int kDenseScatterCols = 32768;  // columns per scatter block
 constexpr int kDenseTmapBytes = 128;
-constexpr uint32_t kDenseMaxCount = 511;  // largest count the f32 rounds keep exact
 
 int dense_init();  // one-time kernel attributes; returns a cudaError_t
-// Host: the TMA descriptor of an f16 matrix of `rows` x `ld` (box 64 x 128,
+// Host: the TMA descriptor of a byte matrix of `rows` x `ld` (box 128 x 128,
 // 128-byte swizzle).  Returns 0 on success.
 int dense_encode_tmap(void* out, void* A, uint64_t ld, uint64_t rows);
-void launch_dense_scatter(const DenseProb* d_probs, uint32_t nprobs, uint32_t rows, uint32_t colblocks,
-                          const DsPack* dsp, const MaskDesc* masks, const uint64_t* fullkey, cudaStream_t st);
+// d_probs: the wave's problems (row0 relative to the wave), p0 the plan
+// index of the first; overflow entries go to ovf[*ovf_n++] while below
+// ovf_cap.
+void launch_dense_scatter(const DenseProb* d_probs, uint32_t nprobs, uint32_t p0, uint32_t rows,
+                          const DsPack* dsp, const MaskDesc* masks, const uint64_t* fullkey,
+                          uint32_t* ovf_n, DenseOvf* ovf, uint32_t ovf_cap, cudaStream_t st);
 // Tiles: (problem, I, J) triples, I over 128-row and J over 256-column blocks.
 void launch_dense_gemm(const DenseProb* d_probs, const uint32_t* d_tiles, uint32_t ntiles, int nsm,
                        uint32_t* status, cudaStream_t st);
+// d_probs: every problem of the plan.  Raises kErrDenseOverflow when the
+// list overflowed (the results are then incomplete).
+void launch_dense_fix(const DenseProb* d_probs, const uint32_t* ovf_n, const DenseOvf* ovf, uint32_t ovf_cap,
+                      uint32_t* status, cudaStream_t st);
 
 // Plain per-mask path (Alg. 1 as written: countAndUpdate straight into the
 // global C_m with atomics, then inclusion-exclusion).

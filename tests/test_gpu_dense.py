@@ -2,9 +2,10 @@
 counts of every (mask, (g-m)-mer) of a level (countAndUpdate of Alg. 1 as a
 dense contraction).
 
-The route is exact integer arithmetic (counts <= 511 in f16, f32 partial
-sums flushed to int32 before 2^24), so every integer output must equal the
-oracle's bit for bit, and equal the sparse route's.
+The route is exact integer arithmetic (counts up to 16 in e4m3, f32 partial
+sums flushed to int32 before 2^24, larger counts corrected from an overflow
+list), so every integer output must equal the oracle's bit for bit, and
+equal the sparse route's.
 """
 
 import numpy as np
@@ -46,7 +47,7 @@ CASES = [  # (seed, n, sigma, lo, hi, g, k)
     (120, 40, 4, 100, 300, 10, 6),    # DNA large-M shape: level 4 (4096 keys) dense
     (121, 260, 4, 0, 200, 8, 4),      # three row blocks, ragged n, partial B tile
     (122, 30, 4, 10, 120, 10, 3),     # M = 7: levels 5..7 have 10, 8, 6 key bits
-    (123, 25, 2, 0, 80, 4, 1),        # binary alphabet: 4..8-column masks padded to 64
+    (123, 25, 2, 0, 80, 4, 1),        # binary alphabet: 2..16-column masks, rows padded to 128 columns
     (124, 19, 3, 5, 60, 6, 2),        # sigma = 3 (2 bits per symbol, code 3 unused)
     (125, 9, 4, 10, 40, 5, 5),        # M = 0: the spectrum level alone
 ]
@@ -70,7 +71,7 @@ def test_dense_equals_sparse_on_several_waves():
     sparse = _run(4, g, k, codes, off, dense=0)
     assert sparse["dense_problems"] == 0
     n_pad = 384
-    one_mask = n_pad * 4 ** 5 * 2            # level 4: 5-mers
+    one_mask = n_pad * 4 ** 5                # level 4: 5-mers, one byte each
     dense = _run(4, g, k, codes, off, dense=2, dense_bytes=3 * one_mask)
     assert dense["dense_problems"] > 10
     for key in ("K", "Nm", "Khat"):
@@ -81,9 +82,9 @@ def test_dense_equals_sparse_on_several_waves():
 
 
 @pytest.mark.parametrize("kind", ["homopolymer", "period2", "mixed"])
-def test_large_counts_flush_exactly(kind):
-    """A homopolymer of 500 symbols gives one count of 496 per mask: every
-    64-column stage then closes its own exact f32 round."""
+def test_large_counts_are_corrected_exactly(kind):
+    """Counts of 496 for one feature per mask: A holds 16 and the overflow
+    list carries the rest."""
     codes, off = synth.repeats(kind, n=4, length=500)
     ref = oracle.gram(codes, off, 5, 3)
     out = _run(4, 5, 3, codes, off, dense=2)
@@ -91,13 +92,38 @@ def test_large_counts_flush_exactly(kind):
     _check(out, ref)
 
 
-def test_long_sequences_stay_sparse():
-    """More than 511 windows in one sequence: counts could leave the exact
-    range, so no level goes dense, and the result is still exact."""
+def test_overflows_sharing_a_column():
+    """Homopolymers of one symbol: every sequence overflows at the same
+    column of every mask, so the pair terms of the correction meet; lengths
+    around g + 15 put counts at 15, 16, 17 and 18 (the e4m3 edge)."""
+    g, k = 6, 3
+    lens = [g + 14, g + 15, g + 16, g + 17, 40, 100, 7, 0, 300]
+    seqs = [np.zeros(n, np.uint8) for n in lens]
+    seqs += [np.full(60, 2, np.uint8), np.array([0, 1] * 40, np.uint8)]
+    codes, off = synth.pack(seqs)
+    ref = oracle.gram(codes, off, g, k)
+    out = _run(4, g, k, codes, off, dense=2)
+    assert out["dense_problems"] > 0
+    _check(out, ref)
+
+
+def test_full_overflow_list_reruns_sparse():
+    """An overflow list too small for the input: the call reruns with every
+    level sparse and stays exact."""
+    codes, off = synth.repeats("mixed", n=6, length=400)
+    ref = oracle.gram(codes, off, 5, 2)
+    out = _run(4, 5, 2, codes, off, dense=2, dense_overflow=2)
+    assert out["dense_problems"] == 0     # the rerun planned every level sparse
+    _check(out, ref)
+
+
+def test_long_sequences_go_dense():
+    """More than 511 windows per sequence: counts are not bounded by the
+    e4m3 range, which the overflow list covers."""
     codes, off = synth.random_small(127, 6, 4, 500, 700)
     ref = oracle.gram(codes, off, 6, 3)
     out = _run(4, 6, 3, codes, off, dense=2)
-    assert out["dense_problems"] == 0
+    assert out["dense_problems"] > 0
     _check(out, ref)
 
 
