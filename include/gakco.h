@@ -123,6 +123,9 @@ const char *gakco_last_error(const gakco_ctx *ctx);
 #define GAKCO_OPT_DENSE_OVERFLOW 16 /* entries of the list of counts above 16 per dense
                                        wave (default 32768); a call that needs more runs
                                        again with every level sparse */
+#define GAKCO_OPT_DENSE_RUN_COLS 17 /* columns (masks x keys) of one dense contraction
+                                       (default 131072); shorter runs keep concurrent
+                                       tiles closer together in L2 */
 int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 
 /*

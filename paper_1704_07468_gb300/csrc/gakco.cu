@@ -187,6 +187,10 @@ struct gakco_ctx {
   int dense = 0;                            // 0 off, 1 cost model, 2 every eligible level
   int64_t dense_bytes = (int64_t)16 << 30;  // A matrices per dense wave (capped at create)
   int64_t dense_overflow = 32768;           // overflow-list entries per dense wave
+  // Columns of one dense problem (a run of masks of one level): long enough
+  // to amortise a tile's epilogue, short enough that a level yields many
+  // tiles and that concurrent tiles stay within one L2-sized window of A.
+  int64_t dense_run_cols = 131072;
 
   std::string err;
   int device = 0;
@@ -367,10 +371,7 @@ struct DenseWave {
   uint64_t elems;        // A bytes of the wave
 };
 
-// Columns of one dense problem (a run of masks of one level): long enough
-// to amortise a tile's epilogue, short enough that a level yields many
-// tiles for the persistent GEMM to balance.
-constexpr uint64_t kDenseRunCols = 131072;
+
 
 struct Plan {
   std::vector<DsHost> ds;
@@ -650,7 +651,7 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
       p.dense[d * L + m] = 1;
       const uint32_t mf = lf[m], mc = lf[m + 1] - lf[m];
       const uint64_t by_mem = std::max<uint64_t>(1, budget / per_mask);
-      const uint64_t by_cols = std::max<uint64_t>(1, kDenseRunCols / S);
+      const uint64_t by_cols = std::max<uint64_t>(1, (uint64_t)c->dense_run_cols / S);
       const uint32_t gmax = (uint32_t)std::min<uint64_t>(mc, std::min(by_mem, by_cols));
       const uint32_t ng = (mc + gmax - 1) / gmax;
       for (uint32_t gi = 0; gi < ng; ++gi) {
@@ -670,20 +671,46 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
     }
   }
   // Waves: consecutive problems whose A matrices fit the budget together.
+  // A wave's macro tiles cover each run of its problems that shares one
+  // (dataset, level); longest first, so the persistent CTAs finish together.
+  // Each macro tile issues one 128 x 256 product per row half below n.
+  auto sub_tiles = [](uint32_t I2, uint32_t, uint32_t n) {
+    return (I2 * 256 < n ? 2 : 0) + (I2 * 256 + 128 < n ? 2 : 0);  // in 128 x 128 units
+  };
   DenseWave wv{};
   auto close = [&]() {
     if (wv.np == 0) return;
-    // Longest tiles first, so the persistent CTAs finish together.
-    const size_t t0 = (size_t)wv.t0 * 3, t1 = p.dtiles.size();
-    std::vector<std::array<uint32_t, 3>> tl((t1 - t0) / 3);
-    for (size_t i = 0; i < tl.size(); ++i)
-      tl[i] = {p.dtiles[t0 + 3 * i], p.dtiles[t0 + 3 * i + 1], p.dtiles[t0 + 3 * i + 2]};
-    std::stable_sort(tl.begin(), tl.end(), [&](const std::array<uint32_t, 3>& a, const std::array<uint32_t, 3>& b) {
-      return p.dprobs[a[0]].ld > p.dprobs[b[0]].ld;
-    });
-    for (size_t i = 0; i < tl.size(); ++i)
-      for (int q = 0; q < 3; ++q) p.dtiles[t0 + 3 * i + q] = tl[i][q];
-    wv.nt = (uint32_t)(tl.size());
+    // Macro tiles per (dataset, level) run of problems, each sweeping all
+    // of the run's columns (one epilogue per tile: tensor memory holds no
+    // second accumulator pair to overlap more), longest first.
+    struct Part {
+      std::array<uint32_t, kDenseTileWords> w;
+      double cost;
+    };
+    std::vector<Part> best;
+    for (uint32_t g0 = wv.p0; g0 < wv.p0 + wv.np;) {
+      uint32_t g1 = g0 + 1;
+      while (g1 < wv.p0 + wv.np && p.dprobs[g1].ds == p.dprobs[g0].ds && p.dprobs[g1].level == p.dprobs[g0].level) ++g1;
+      const DenseHost& h = p.dprobs[g0];
+      double stages = 0;
+      for (uint32_t j = g0; j < g1; ++j) stages += (double)(p.dprobs[j].ld / 128);
+      const uint32_t R = (h.n_pad + 255) / 256;
+      for (uint32_t I2 = 0; I2 < R; ++I2)
+        for (uint32_t J2 = I2; J2 < R; ++J2) {
+          const int k = sub_tiles(I2, J2, h.n);
+          if (k > 0) best.push_back({{g0, g1 - g0, I2, J2}, stages * k});
+        }
+      g0 = g1;
+    }
+    std::stable_sort(best.begin(), best.end(), [](const Part& x, const Part& y) { return x.cost > y.cost; });
+    wv.t0 = (uint32_t)(p.dtiles.size() / kDenseTileWords);
+    for (const Part& pt : best) {
+      p.dtiles.insert(p.dtiles.end(), pt.w.begin(), pt.w.end());
+      double cols = 0;
+      for (uint32_t j = pt.w[0]; j < pt.w[0] + pt.w[1]; ++j) cols += (double)p.dprobs[j].ld;
+      p.dense_issued += 2.0 * 128.0 * 128.0 * cols * sub_tiles(pt.w[2], pt.w[3], p.dprobs[pt.w[0]].n);
+    }
+    wv.nt = (uint32_t)best.size();
     p.dense_abytes = std::max<uint64_t>(p.dense_abytes, wv.elems);
     p.dwaves.push_back(wv);
   };
@@ -694,22 +721,12 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
       close();
       wv = DenseWave{};
     }
-    if (wv.np == 0) {
-      wv.p0 = i;
-      wv.t0 = (uint32_t)(p.dtiles.size() / 3);
-    }
+    if (wv.np == 0) wv.p0 = i;
     h.a_off = wv.elems;
     h.row0 = wv.rows;
     wv.elems += el;
     wv.rows += h.n_pad;
     wv.np++;
-    const uint32_t rb = h.n_pad / 128, cb = (h.n_pad + 255) / 256;
-    for (uint32_t I = 0; I < rb; ++I)
-      for (uint32_t J = I / 2; J < cb; ++J) {
-        const uint32_t t[3] = {i, I, J};
-        p.dtiles.insert(p.dtiles.end(), t, t + 3);
-        p.dense_issued += 2.0 * 128.0 * 256.0 * (double)h.ld;
-      }
     p.dense_flops += 2.0 * (double)h.mcount * std::ldexp(1.0, (int)h.key_bits) * 0.5 * h.n * (h.n + 1.0);
     p.dense_bytes += (double)el;
   }
@@ -807,7 +824,7 @@ int fill_dense(gakco_ctx* c, Work& w, Plan& p, Tables& t) {
     DenseProb q{};
     q.A = (uint8_t*)w.Adense.p + h.a_off;
     q.C = (uint32_t*)w.Cacc.p + cacc[h.ds] + (uint64_t)h.level * h.n * h.n;
-    q.maxc = (uint32_t*)w.dmaxc.p + i;
+    q.maxc = (uint32_t*)w.dmaxc.p + (size_t)h.ds * (c->M + 1) + h.level;
     q.tmap = base + p.o_tmaps + i * kDenseTmapBytes;
     q.ld = h.ld;
     q.n = h.n;
@@ -884,7 +901,7 @@ int plan_memory_and_tables(gakco_ctx* c, Work& w, Plan& p, bool plain) {
   if (!plain) ENSURE(Cacc, csum * 4);
   if (!p.dprobs.empty()) {
     ENSURE(Adense, p.dense_abytes);
-    ENSURE(dmaxc, (p.dprobs.size() + 1) * 4);  // + the overflow-list counter
+    ENSURE(dmaxc, (p.ds.size() * (c->M + 1) + 1) * 4);  // per (dataset, level), + the overflow counter
     ENSURE(dovf, (size_t)c->dense_overflow * sizeof(DenseOvf));
   }
   Tables t;
@@ -977,9 +994,10 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
       // Dense levels: A = counts per (sequence, mask, key), C_m += A A^T.
       const DenseProb* probs = (const DenseProb*)(base + p.o_dprobs);
       const uint32_t* tiles = (const uint32_t*)(base + p.o_dtiles);
-      uint32_t* ovf_n = (uint32_t*)w.dmaxc.p + p.dprobs.size();
+      const size_t nmax_words = p.ds.size() * (size_t)(c->M + 1);
+      uint32_t* ovf_n = (uint32_t*)w.dmaxc.p + nmax_words;
       const uint32_t cap = (uint32_t)c->dense_overflow;
-      cudaMemsetAsync(w.dmaxc.p, 0, p.dprobs.size() * 4, w.cs);
+      cudaMemsetAsync(w.dmaxc.p, 0, nmax_words * 4, w.cs);
       for (const DenseWave& wv : p.dwaves) {
         cudaMemsetAsync(ovf_n, 0, 4, w.cs);
         {
@@ -989,7 +1007,7 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
         }
         {
           Bracket b(c, w, "dense_gemm", 1);
-          launch_dense_gemm(probs, tiles + 3 * (size_t)wv.t0, wv.nt, c->nsm, status, w.cs);
+          launch_dense_gemm(probs, tiles + kDenseTileWords * (size_t)wv.t0, wv.nt, c->nsm, status, w.cs);
         }
         Bracket b(c, w, "dense_fix", 1);
         launch_dense_fix(probs, ovf_n, (const DenseOvf*)w.dovf.p, cap, status, w.cs);
@@ -1038,8 +1056,9 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
 
 uint64_t plan_key(gakco_ctx* c, const Plan& p, bool plain) {
   uint64_t h = 1469598103934665603ull;
-  int64_t o[10] = {plain, c->radix_bits, c->chunk_elems, c->accum_threads, c->smem_cols,
-                   (int64_t)p.ds.size(), c->group_bytes, c->dense, c->dense_bytes, c->dense_overflow};
+  int64_t o[11] = {plain,           c->radix_bits, c->chunk_elems, c->accum_threads,  c->smem_cols,
+                   (int64_t)p.ds.size(), c->group_bytes, c->dense,    c->dense_bytes, c->dense_overflow,
+                   c->dense_run_cols};
   h = fnv1a(h, o, sizeof o);
   for (const DsHost& D : p.ds) {
     const void* ptrs[4] = {D.codes, D.K, D.Khat, D.Nm};
@@ -1948,6 +1967,10 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
     case GAKCO_OPT_DENSE_BYTES:
       if (v < 1) return fail(c, GAKCO_E_INVALID, "dense bytes must be >= 1");
       c->dense_bytes = v;
+      break;
+    case GAKCO_OPT_DENSE_RUN_COLS:
+      if (v < 128) return fail(c, GAKCO_E_INVALID, "dense run columns must be >= 128");
+      c->dense_run_cols = v;
       break;
     case GAKCO_OPT_DENSE_OVERFLOW:
       if (v < 1 || v > ((int64_t)1 << 26)) return fail(c, GAKCO_E_INVALID, "overflow entries must be 1..2^26");

@@ -23,16 +23,17 @@
 // (the second as (c_x-16) 16 + (c_y-16) 16 + (c_x-16)(c_y-16), one term
 // from each entry's row scan and the product from the pair scan).
 //
-// GEMM structure.  One CTA per SM walks a list of (problem, I, J) output
-// tiles of 128 rows x 256 columns (upper triangle only: C is symmetric).
-// Warp 5 loads 128-column slices of A's rows I*128.. and J*256.. with TMA
-// (128-byte swizzle) into a four-stage ring; one thread of warp 4 issues
-// tcgen05.mma (M = 128, N = 256, K = 32) into one of two 256-column TMEM
-// accumulators; warps 0-3 read the finished accumulator back with
-// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. tile rows) and add
-// the upper-triangle part into C.  Hand-offs use mbarriers.  Every wait is
-// bounded: a timeout raises an error bit, stops every role, waits (bounded)
-// for the copies and MMAs already issued, and frees tensor memory.
+// GEMM structure.  One CTA per SM walks a list of macro tiles of 256 x 256
+// outputs (upper triangle only: C is symmetric), each covering every mask
+// run of its (dataset, level), so C receives one epilogue per macro tile.
+// Warp 5 loads 128-column slices of A's rows I2*256.. (two 128-row blocks)
+// and J2*256.. (256 rows) with TMA (128-byte swizzle) into a three-stage
+// ring; one thread of warp 4 issues tcgen05.mma (M = 128, N = 256, K = 32)
+// into two 256-column TMEM accumulators, one per 128-row half; warps 0-3
+// read them back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31) and
+// add the upper-triangle part into C.  Hand-offs use mbarriers.  Every
+// wait is bounded: a timeout raises an error bit, stops every role, waits
+// (bounded) for the copies and MMAs already issued, and frees tensor memory.
 #include <cuda.h>  // CUtensorMap and its enums; the encoder is fetched at run time
 
 #include <cstdint>
@@ -45,10 +46,9 @@ namespace gk {
 
 namespace {
 
-constexpr int kStages = 4;
-constexpr uint32_t kABytes = 128 * 128;  // 128 rows x 128 e4m3 columns
-constexpr uint32_t kBBytes = 256 * 128;  // 256 rows x 128 e4m3 columns
-constexpr uint32_t kStageBytes = kABytes + kBBytes;
+constexpr int kStages = 3;
+constexpr uint32_t kSubBytes = 128 * 128;         // 128 rows x 128 e4m3 columns
+constexpr uint32_t kStageBytes = 4 * kSubBytes;   // A rows I2*256 + {0, 128}, B rows J2*256 + {0, 128}
 constexpr int kMmaWarp = 4, kTmaWarp = 5;
 constexpr int kGemmThreads = 192;
 constexpr uint32_t kTmemCols = 512;  // two 128 x 256 f32 accumulators
@@ -167,7 +167,7 @@ __device__ __forceinline__ uint32_t e4m3_small_value(uint32_t b) {
 // and each chunk is written out whole (zeros included), so A needs no
 // separate clearing; padded rows come out all zero.  The conversion loop
 // clears the counts it has read, ready for the next chunk.
-__global__ void __launch_bounds__(kScatterThreads)
+__global__ void __launch_bounds__(kScatterThreads, 3)
 k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p0, const DsPack* __restrict__ dsp,
                 const MaskDesc* __restrict__ masks, const uint64_t* __restrict__ fullkey, uint32_t* __restrict__ ovf_n,
                 DenseOvf* __restrict__ ovf, uint32_t ovf_cap) {
@@ -215,12 +215,17 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
     __syncthreads();
     // Mask-major: the lanes of a warp mostly share one mask and read
     // consecutive windows.
+    uint32_t mi = nw ? tid / nw : 0, w = nw ? tid - mi * nw : 0;
     for (uint32_t i = tid; i < nw * nmu; i += kScatterThreads) {
-      const uint32_t mi = i / nw, w = i - mi * nw;
       const MaskDesc& md = staged ? smask[mi] : masks[P.mfirst + mu0 + mi];
       const uint64_t key = masked_key(fk[w], md);
       const uint64_t col = (((uint64_t)(mu0 + mi) << kb) | key) - c0;
       if (col < ncol) atomicAdd(&cnt[col >> 1], 1u << (16 * (uint32_t)(col & 1)));
+      w += kScatterThreads;
+      while (w >= nw) {
+        w -= nw;
+        ++mi;
+      }
     }
     __syncthreads();
     uint4* out = (uint4*)(P.A + (uint64_t)x * ld + c0);
@@ -230,16 +235,17 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
       cw[0] = make_uint4(0, 0, 0, 0);
       cw[1] = make_uint4(0, 0, 0, 0);
       const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-      uint32_t over = 0, e[8];
+      uint32_t m = 0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const uint32_t cl = __vminu2(w[q], 0x00100010u);
-        over |= __vcmpgtu2(w[q], 0x00100010u);
-        mx2 = __vmaxu2(mx2, cl);
-        e[q] = e4m3x2_of_counts(cl);
-      }
-      out[j] = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16), e[6] | (e[7] << 16));
-      if (over) {
+      for (int q = 0; q < 8; ++q) m = __vmaxu2(m, w[q]);
+      mx2 = __vmaxu2(mx2, m);
+      uint32_t e[8];
+      if ((m & 0xFFFFu) <= 16u && (m >> 16) <= 16u) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) e[q] = e4m3x2_of_counts(w[q]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) e[q] = e4m3x2_of_counts(__vminu2(w[q], 0x00100010u));
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const uint32_t c = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
@@ -249,11 +255,12 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
           }
         }
       }
+      out[j] = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16), e[6] | (e[7] << 16));
     }
     // The next chunk's counting waits at its first barrier for this
     // conversion (and its clearing) to finish.
   }
-  uint32_t mymax = max(mx2 & 0xFFFFu, mx2 >> 16);
+  uint32_t mymax = min(max(mx2 & 0xFFFFu, mx2 >> 16), 16u);  // largest entry of A
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mymax = max(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
   if ((tid & 31) == 0 && mymax) atomicMax(P.maxc, mymax);
@@ -297,11 +304,17 @@ k_dense_fix(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ ov
   }
 }
 
+// Row halves a of macro tile (I2, J2) that hold rows below n: bit a set
+// when rows I2*256+128a.. start below n.
+__device__ __forceinline__ uint32_t row_halves(uint32_t I2, uint32_t n) {
+  return (I2 * 256 < n ? 1u : 0u) | (I2 * 256 + 128 < n ? 2u : 0u);
+}
+
 __global__ void __launch_bounds__(kGemmThreads, 1)
 k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ tiles, uint32_t ntiles,
              uint32_t* __restrict__ status) {
   extern __shared__ uint8_t raw[];
-  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], tfull[2], tempty[2], done_bar;
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], tfull, tempty, done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ volatile uint32_t abort_flag;
   uint8_t* sm = (uint8_t*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
@@ -311,10 +324,8 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
       bar_init(&full_bar[s], 1);
       bar_init(&empty_bar[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      bar_init(&tfull[b], 1);
-      bar_init(&tempty[b], 128);
-    }
+    bar_init(&tfull, 1);
+    bar_init(&tempty, 128);
     bar_init(&done_bar, 1);
     abort_flag = 0;
   }
@@ -334,21 +345,29 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
       uint32_t it = 0;
       bool stop = false;
       for (uint32_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-        const DenseProb& P = probs[tiles[3 * t]];
-        const int y_a = (int)(tiles[3 * t + 1] * 128), y_b = (int)(tiles[3 * t + 2] * 256);
-        const void* tm = P.tmap;
-        const uint32_t nk = (uint32_t)(P.ld / 128);
-        for (uint32_t k = 0; k < nk; ++k, ++it) {
-          const uint32_t s = it % kStages;
-          if (!bar_wait(&empty_bar[s], ((it / kStages) & 1) ^ 1, &abort_flag)) {
-            stop = true;
-            break;
+        const uint32_t* tl = tiles + kDenseTileWords * t;
+        const uint32_t pa = tl[0], pn = tl[1], I2 = tl[2], J2 = tl[3];
+        const uint32_t st = row_halves(I2, probs[pa].n);
+        const bool needA[2] = {(st & 1u) != 0, (st & 2u) != 0};
+        const uint32_t bytes = kSubBytes * (2 + needA[0] + needA[1]);  // B: both 128-row blocks
+        for (uint32_t p = pa; p < pa + pn && !stop; ++p) {
+          const void* tm = probs[p].tmap;
+          const uint32_t nk = (uint32_t)(probs[p].ld / 128);
+          for (uint32_t k = 0; k < nk; ++k, ++it) {
+            const uint32_t s = it % kStages;
+            if (!bar_wait(&empty_bar[s], ((it / kStages) & 1) ^ 1, &abort_flag)) {
+              stop = true;
+              break;
+            }
+            const uint32_t dst = smem_u32(sm + s * kStageBytes);
+            bar_expect_tx(&full_bar[s], bytes);
+#pragma unroll
+            for (uint32_t a = 0; a < 2; ++a)
+              if (needA[a]) tma_load(dst + a * kSubBytes, tm, (int)(k * 128), (int)(I2 * 256 + a * 128), &full_bar[s]);
+#pragma unroll
+            for (uint32_t b = 0; b < 2; ++b)
+              tma_load(dst + (2 + b) * kSubBytes, tm, (int)(k * 128), (int)(J2 * 256 + b * 128), &full_bar[s]);
           }
-          const uint32_t dst = smem_u32(sm + s * kStageBytes);
-          bar_expect_tx(&full_bar[s], kStageBytes);
-          tma_load(dst, tm, (int)(k * 128), y_a, &full_bar[s]);
-          tma_load(dst + kABytes, tm, (int)(k * 128), y_b, &full_bar[s]);
-          tma_load(dst + kABytes + kABytes, tm, (int)(k * 128), y_b + 128, &full_bar[s]);
         }
       }
       // Let the copies already issued land before the block can exit.
@@ -365,39 +384,55 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
       uint32_t it = 0, round = 0;
       bool stop = false;
       for (uint32_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-        const DenseProb& P = probs[tiles[3 * t]];
-        const uint32_t nk = (uint32_t)(P.ld / 128);
-        const uint32_t spr = stages_per_round(P.maxc, nk);
-        for (uint32_t k = 0; k < nk && !stop; ++round) {
-          const uint32_t b = round & 1;
-          if (!bar_wait(&tempty[b], ((round >> 1) & 1) ^ 1, &abort_flag)) {
-            stop = true;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t d = taddr + b * 256;
-          const uint32_t kend = (k + spr < nk) ? k + spr : nk;
-          for (uint32_t kk = k; kk < kend; ++kk, ++it) {
+        const uint32_t* tl = tiles + kDenseTileWords * t;
+        const uint32_t pa = tl[0], pn = tl[1], I2 = tl[2], J2 = tl[3];
+        const uint32_t st = row_halves(I2, probs[pa].n);
+        uint32_t total = 0;
+        for (uint32_t p = pa; p < pa + pn; ++p) total += (uint32_t)(probs[p].ld / 128);
+        const uint32_t spr = stages_per_round(probs[pa].maxc, total);
+        uint32_t kr = 0;  // stages into the current round
+        for (uint32_t p = pa; p < pa + pn && !stop; ++p) {
+          const uint32_t nk = (uint32_t)(probs[p].ld / 128);
+          for (uint32_t k = 0; k < nk; ++k, ++it) {
+            if (kr == 0) {
+              if (!bar_wait(&tempty, (round & 1) ^ 1, &abort_flag)) {
+                stop = true;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;");
+            }
             const uint32_t s = it % kStages;
             if (!bar_wait(&full_bar[s], (it / kStages) & 1, &abort_flag)) {
               stop = true;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t a0 = smem_u32(sm + s * kStageBytes), b0 = a0 + kABytes;
+            const uint32_t base = smem_u32(sm + s * kStageBytes);
 #pragma unroll
-            for (uint32_t j = 0; j < 4; ++j) {
-              const uint32_t acc = (kk > k || j > 0) ? 1u : 0u;
-              asm volatile(
-                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                  "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                  "l"(smem_desc(a0 + j * 32)), "l"(smem_desc(b0 + j * 32)), "r"(idesc), "r"(acc));
+            for (uint32_t ah = 0; ah < 2; ++ah) {
+              if (!(st & (1u << ah))) continue;
+              const uint32_t a0 = base + ah * kSubBytes, b0 = base + 2 * kSubBytes;
+              const uint32_t d = taddr + 256 * ah;
+#pragma unroll
+              for (uint32_t j = 0; j < 4; ++j) {
+                const uint32_t acc = (kr > 0 || j > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                    "l"(smem_desc(a0 + j * 32)), "l"(smem_desc(b0 + j * 32)), "r"(idesc), "r"(acc));
+              }
             }
             mma_commit(&empty_bar[s]);
+            if (++kr == spr) {
+              mma_commit(&tfull);
+              ++round;
+              kr = 0;
+            }
           }
-          if (stop) break;
-          mma_commit(&tfull[b]);
-          k = kend;
+        }
+        if (!stop && kr > 0) {
+          mma_commit(&tfull);
+          ++round;
         }
       }
       // Every MMA issued must finish before tensor memory is freed.
@@ -405,52 +440,58 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
       bar_drain(&done_bar, 0);
     }
   } else {
-    // Epilogue warps 0-3: row = I*128 + 32*warp + lane of each tile.
+    // Epilogue warps 0-3: TMEM lanes 32*warp.. = rows of each sub-tile.
     uint32_t round = 0;
     bool stop = false;
     for (uint32_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-      const DenseProb& P = probs[tiles[3 * t]];
-      const uint32_t n = P.n;
-      const uint32_t nk = (uint32_t)(P.ld / 128);
-      const uint32_t spr = stages_per_round(P.maxc, nk);
-      const uint32_t nr = (nk + spr - 1) / spr;
-      const uint32_t row = tiles[3 * t + 1] * 128 + warp * 32 + lane;
-      const uint32_t col0 = tiles[3 * t + 2] * 256;
-      uint32_t* crow = P.C + (uint64_t)row * n;
+      const uint32_t* tl = tiles + kDenseTileWords * t;
+      const uint32_t pa = tl[0], pn = tl[1], I2 = tl[2], J2 = tl[3];
+      const uint32_t n = probs[pa].n;
+      const uint32_t st = row_halves(I2, n);
+      uint32_t total = 0;
+      for (uint32_t p = pa; p < pa + pn; ++p) total += (uint32_t)(probs[p].ld / 128);
+      const uint32_t spr = stages_per_round(probs[pa].maxc, total);
+      const uint32_t nr = (total + spr - 1) / spr;
+      uint32_t* C = probs[pa].C;
       for (uint32_t r = 0; r < nr; ++r, ++round) {
-        const uint32_t b = round & 1;
-        if (!__all_sync(0xffffffffu, bar_wait(&tfull[b], (round >> 1) & 1, &abort_flag))) {
+        if (!__all_sync(0xffffffffu, bar_wait(&tfull, round & 1, &abort_flag))) {
           stop = true;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
+        for (uint32_t ah = 0; ah < 2; ++ah) {
+          if (!(st & (1u << ah))) continue;
+          const uint32_t row = I2 * 256 + ah * 128 + warp * 32 + lane;
+          const uint32_t col0 = J2 * 256;
+          uint32_t* crow = C + (uint64_t)row * n;
 #pragma unroll 1
-        for (uint32_t cb = 0; cb < 256; cb += 32) {
-          uint32_t v[32];
-          const uint32_t a = taddr + b * 256 + cb + ((warp * 32) << 16);
-          __syncwarp();
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-              "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-              : "r"(a));
-          asm volatile("tcgen05.wait::ld.sync.aligned;");
-          if (row < n) {
+          for (uint32_t cb = 0; cb < 256; cb += 32) {
+            uint32_t v[32];
+            const uint32_t a = taddr + 256 * ah + cb + ((warp * 32) << 16);
+            __syncwarp();
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(a));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (row < n) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const uint32_t col = col0 + cb + j;
-              const uint32_t val = (uint32_t)__uint_as_float(v[j]);
-              if (col < n && col >= row && val) atomicAdd(&crow[col], val);
+              for (int j = 0; j < 32; ++j) {
+                const uint32_t col = col0 + cb + j;
+                const uint32_t val = (uint32_t)__uint_as_float(v[j]);
+                if (col < n && col >= row && val) atomicAdd(&crow[col], val);
+              }
             }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
-        bar_arrive(&tempty[b]);
+        bar_arrive(&tempty);
       }
     }
   }

@@ -167,7 +167,8 @@ void launch_cross_combine(const CrossParams& p, int32_t* K, double* Khat, cudaSt
 struct DenseProb {
   uint8_t* A;           // e4m3 bytes, n_pad x ld, row-major
   uint32_t* C;          // n x n cumulative profile C_m of the dataset
-  uint32_t* maxc;       // largest entry of A as an integer (written by the scatter kernel)
+  uint32_t* maxc;       // largest entry of A as an integer, shared by the problems of one
+                        // (dataset, level) (written by the scatter kernel)
   const void* tmap;     // TMA descriptor of A (kDenseTmapBytes, 64-byte aligned)
   uint64_t ld;          // columns of A, a multiple of 128
   uint32_t n, n_pad;    // sequences; rows of A
@@ -196,7 +197,10 @@ int dense_encode_tmap(void* out, void* A, uint64_t ld, uint64_t rows);
 void launch_dense_scatter(const DenseProb* d_probs, uint32_t nprobs, uint32_t p0, uint32_t rows,
                           const DsPack* dsp, const MaskDesc* masks, const uint64_t* fullkey,
                           uint32_t* ovf_n, DenseOvf* ovf, uint32_t ovf_cap, cudaStream_t st);
-// Tiles: (problem, I, J) triples, I over 128-row and J over 256-column blocks.
+// Macro tiles of kDenseTileWords words: first problem, problem count (the
+// consecutive problems of one dataset and level, whose columns the tile
+// sweeps), I2, J2 (256-row and 256-column blocks, I2 <= J2).
+constexpr int kDenseTileWords = 4;
 void launch_dense_gemm(const DenseProb* d_probs, const uint32_t* d_tiles, uint32_t ntiles, int nsm,
                        uint32_t* status, cudaStream_t st);
 // d_probs: every problem of the plan.  Raises kErrDenseOverflow when the
