@@ -197,8 +197,10 @@ __host__ __device__ constexpr size_t downsweep_smem(int rbits, int key_bytes) {
 // point that orders consecutive items.  The tile is then laid out in digit
 // order in shared memory and written out with consecutive threads on
 // consecutive addresses of each digit's run.
+// Resident blocks per SM: four for 32-bit keys, three for 64-bit keys
+// (more would spill their register-held tiles).
 template <typename KeyT, bool kFirst>
-__global__ void __launch_bounds__(kSortThreads, 2)
+__global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4)
 k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg,
             const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin,
             KeyT* __restrict__ kout, uint32_t* __restrict__ vout,
