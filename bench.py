@@ -454,6 +454,42 @@ def run_ours(args):
                  "bit_identical_K": bool(same)}
         pctx.close()
 
+    # Kernel-only mode (K = C_M: the level-M masks alone), same options,
+    # reported beside the full path; the headline value is the full path.
+    konly = None
+    if args.kernel_only_steps > 0:
+        kctx = pkg.gakco_create(sigma, g, k)
+        if not args.no_autotune:
+            kctx.autotune_device([t.data_ptr() for t in d_codes], offs, stream=stream.cuda_stream)
+        if args.dense is not None:
+            kctx.set_option("dense", args.dense)
+        kctx.set_option("kernel_only", 1)
+        kk = [torch.empty((n, n), dtype=torch.int32, device=dev) for n in ns]
+        kkh = [torch.empty((n, n), dtype=torch.float64, device=dev) for n in ns]
+
+        def kstep():
+            kctx.gram_batch_device([t.data_ptr() for t in d_codes], offs,
+                                   [t.data_ptr() for t in kk], [t.data_ptr() for t in kkh],
+                                   None, stream=stream.cuda_stream)
+        for _ in range(3):
+            kstep()
+        kms = []
+        for _ in range(args.kernel_only_steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            kstep()
+            b.record(stream)
+            torch.cuda.synchronize()
+            kms.append(a.elapsed_time(b))
+        kmean = float(np.mean(kms))
+        konly = {"value": entries * ws / (kmean / 1000.0), "unit": UNIT, "ms_per_step": kmean,
+                 "mask_passes_per_step": int(kctx.get_stat("mask_passes")),
+                 "bit_identical_K": bool(all(torch.equal(x, y) for x, y in zip(kk, d_K))),
+                 "what": "K = C_M (Eq. 6 coefficients = Eq. 8 level-M coefficients): level-M masks only"}
+        kctx.close()
+
     # Roofline of every stage with a work figure; the dominant one is the
     # headline entry.
     peaks, peak_kind = measured_peaks()
@@ -498,6 +534,7 @@ def run_ours(args):
         "mask_passes_per_s": len(sets) * n_masks * ws / (step_ms / 1000.0),
         "pair_updates_per_step": pairs,
         "plain_gpu": plain,
+        "kernel_only": konly,
         "serve": serve,
         "e2e": {"value": entries * ws / (e2e_step / 1000.0), "unit": UNIT,
                 "ms_per_step": e2e_step, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -527,6 +564,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=64)
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--kernel-only-steps", type=int, default=3,
+                    help="also time the K = C_M mode (level-M masks only); 0 to skip")
     ap.add_argument("--dense", type=int, default=None, choices=[0, 1, 2],
                     help="dense-level mode after autotuning: 0 never, 1 cost model, 2 every qualifying level")
     ap.add_argument("--serve-requests", type=int, default=300)

@@ -126,6 +126,14 @@ const char *gakco_last_error(const gakco_ctx *ctx);
 #define GAKCO_OPT_DENSE_RUN_COLS 17 /* columns (masks x keys) of one dense contraction
                                        (default 131072); shorter runs keep concurrent
                                        tiles closer together in L2 */
+/* Kernel-only mode (batched Gram engine).  The coefficients of Eq. 6 are
+ * those of N_m in Eq. 8 at level M: h_m = C(g-m, k) = C(g-m, M-m), so
+ * K = sum_m h_m N_m equals the cumulative profile C_M.  With this option
+ * set to 1, a call that requests no N_m output computes the C(g, M) masks
+ * of level M alone (K and Khat are identical); a call that asks for N_m
+ * computes every level as usual.  This identity is derived here; the paper
+ * computes all levels.  Default 0. */
+#define GAKCO_OPT_KERNEL_ONLY 18
 int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 
 /*

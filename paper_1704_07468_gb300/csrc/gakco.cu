@@ -191,6 +191,7 @@ struct gakco_ctx {
   // to amortise a tile's epilogue, short enough that a level yields many
   // tiles and that concurrent tiles stay within one L2-sized window of A.
   int64_t dense_run_cols = 131072;
+  int kernel_only = 0;  // 1: compute level M alone when N_m is not requested (K = C_M)
 
   std::string err;
   int device = 0;
@@ -391,6 +392,10 @@ struct Plan {
   uint64_t c_elems = 0;
   std::vector<uint32_t> seg_ds;  // dataset of each segment
   bool want_nm = false, want_khat = false;
+  // First level computed: M when only the kernel is wanted (K = C_M, so
+  // C_0..C_{M-1} may stay zero: Eq. 9 then gives N_M = C_M and Eq. 7
+  // K = h_M C_M = C_M), else 0.
+  int first_level = 0;
   // Dense (tensor-core) levels: flags per (dataset, level), problems,
   // waves of problems whose A matrices share the A buffer, GEMM tiles.
   std::vector<uint8_t> dense;
@@ -475,7 +480,7 @@ int plan_datasets(gakco_ctx* c, Work& w, Plan& p, int32_t nd, const uint8_t* con
 void plan_chunks(gakco_ctx* c, Plan& p, bool plain) {
   p.sort_bytes = 0;
   const uint64_t limit = plain ? 0 : (uint64_t)std::max<int64_t>(c->chunk_elems, kTile);
-  for (int m = 0; m <= c->M; ++m) {
+  for (int m = p.first_level; m <= c->M; ++m) {
     const int kb = (c->g - m) * c->bits;
     const int np = (kb + c->radix_bits - 1) / c->radix_bits;
     const int rb = (kb + np - 1) / np;
@@ -580,7 +585,7 @@ void add_items(gakco_ctx* c, std::vector<uint32_t>& items, uint32_t d, const std
   const uint32_t gmax =
       (uint32_t)std::max(1.0, std::floor((double)c->group_bytes / std::max(per_mask_bytes, 1.0)));
   for (int m = 0; m <= c->M; ++m) {
-    if (skip && skip->is_dense(d, m, c->M)) continue;  // done on the tensor cores
+    if (skip && (m < skip->first_level || skip->is_dense(d, m, c->M))) continue;  // not needed / tensor cores
     const uint32_t mf = lf[m], mc = lf[m + 1] - lf[m];
     const uint32_t ng = (mc + gmax - 1) / gmax;
     for (uint32_t gi = 0; gi < ng; ++gi) {
@@ -641,7 +646,7 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
     const DsHost& D = p.ds[d];
     if (D.n == 0 || D.G == 0) continue;
     const uint32_t n_pad = (uint32_t)align_up((size_t)D.n, 128);
-    for (int m = 0; m <= c->M; ++m) {
+    for (int m = p.first_level; m <= c->M; ++m) {
       const int kb = c->bits * (c->g - m);
       if (kb > 16) continue;
       const uint64_t S = (uint64_t)1 << kb;
@@ -1056,9 +1061,9 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
 
 uint64_t plan_key(gakco_ctx* c, const Plan& p, bool plain) {
   uint64_t h = 1469598103934665603ull;
-  int64_t o[11] = {plain,           c->radix_bits, c->chunk_elems, c->accum_threads,  c->smem_cols,
+  int64_t o[12] = {plain,           c->radix_bits, c->chunk_elems, c->accum_threads,  c->smem_cols,
                    (int64_t)p.ds.size(), c->group_bytes, c->dense,    c->dense_bytes, c->dense_overflow,
-                   c->dense_run_cols};
+                   c->dense_run_cols, p.first_level};
   h = fnv1a(h, o, sizeof o);
   for (const DsHost& D : p.ds) {
     const void* ptrs[4] = {D.codes, D.K, D.Khat, D.Nm};
@@ -1146,8 +1151,10 @@ int run_gram_once(gakco_ctx* c, Plan& p, cudaStream_t user) {
   c->ev_used = 0;
   c->last_replay = 0;
   c->last_mask_passes = 0;
+  p.first_level = (c->kernel_only && !p.want_nm && !plain) ? c->M : 0;
+  const int64_t masks_run = (int64_t)c->masks.size() - (int64_t)level_firsts(c)[p.first_level];
   for (const DsHost& D : p.ds)
-    if (D.G > 0) c->last_mask_passes += (int64_t)c->masks.size();
+    if (D.G > 0) c->last_mask_passes += masks_run;
   if (p.ds.empty()) {
     c->last_launches = 0;
     return GAKCO_OK;
@@ -1967,6 +1974,10 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
     case GAKCO_OPT_DENSE_BYTES:
       if (v < 1) return fail(c, GAKCO_E_INVALID, "dense bytes must be >= 1");
       c->dense_bytes = v;
+      break;
+    case GAKCO_OPT_KERNEL_ONLY:
+      if (v != 0 && v != 1) return fail(c, GAKCO_E_INVALID, "kernel-only must be 0 or 1");
+      c->kernel_only = (int)v;
       break;
     case GAKCO_OPT_DENSE_RUN_COLS:
       if (v < 128) return fail(c, GAKCO_E_INVALID, "dense run columns must be >= 128");
