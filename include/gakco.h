@@ -283,6 +283,30 @@ int gakco_poll(gakco_ctx *ctx, uint64_t ticket, int timeout_ms,
                double *latency_ms);
 
 /*
+ * SVM decision values on the fitted training set (Eq. 1):
+ *   f(x) = sum_i coef[i] * k(x_i, x) + bias,
+ * with coef[i] = alpha_i * y_i and the bias supplied by the caller (training
+ * the SVM is outside this library) and k = Khat (kind 0) or K (kind 1).
+ * The sum runs over the training sequences in a fixed order, so a value does
+ * not depend on the batch a request ran in.
+ *
+ * gakco_set_svm copies n coefficients (n must equal the fitted training
+ * set's size) next to the resident training index; a later gakco_fit drops
+ * them.  It fails with GAKCO_E_INVALID while served requests are in flight.
+ * gakco_decision computes the decision values of nt test sequences (host
+ * buffers; `decision` holds nt doubles).  gakco_submit_svm is gakco_submit
+ * with the request's decision values as one more output (nt doubles, may
+ * be NULL); it fails with GAKCO_E_INVALID when no coefficients are set.
+ */
+int gakco_set_svm(gakco_ctx *ctx, const double *coef, int32_t n, double bias,
+                  int kind);
+int gakco_decision(gakco_ctx *ctx, const uint8_t *codes,
+                   const int64_t *offsets, int32_t nt, double *decision);
+int gakco_submit_svm(gakco_ctx *ctx, const uint8_t *codes,
+                     const int64_t *offsets, int32_t nt, int32_t *K,
+                     double *Khat, double *decision, uint64_t *ticket);
+
+/*
  * Gram kernel of one dataset that allocates nothing.  The paper has no
  * counterpart; this entry point exists for callers that cannot let a
  * library allocate device memory: applications whose GPU memory belongs to

@@ -94,6 +94,10 @@ def load_library(build_if_missing: bool = False):
         "gakco_submit": ([p, p, p, i32, p, p, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
         "gakco_poll": ([p, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
                        ctypes.c_int),
+        "gakco_set_svm": ([p, p, i32, ctypes.c_double, ctypes.c_int], ctypes.c_int),
+        "gakco_decision": ([p, p, p, i32, p], ctypes.c_int),
+        "gakco_submit_svm": ([p, p, p, i32, p, p, p, ctypes.POINTER(ctypes.c_uint64)],
+                             ctypes.c_int),
         "gakco_gram_device_noalloc": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, p, p, i32,
                                        p, p, p, p, ctypes.c_char_p, ctypes.c_int],
                                       ctypes.c_int),
@@ -294,17 +298,37 @@ def _add_cross_methods(cls):
         self.fit(*train)
         return self.cross_fitted(*test, khat=khat)
 
-    def submit(self, codes, offsets, khat=True, K=True):
+    def set_svm(self, coef, bias=0.0, kind=0):
+        """Coefficients alpha_i * y_i of the fitted training set and the bias
+        for decision values (Eq. 1); kind 0 uses Khat, 1 uses K."""
+        coef = np.ascontiguousarray(coef, dtype=np.float64)
+        self._check(self._lib.gakco_set_svm(self._h, _ptr(coef) if coef.size else None, len(coef),
+                                            float(bias), int(kind)))
+        return self
+
+    def decision(self, codes, offsets):
+        """SVM decision values of test sequences against the fitted set."""
+        codes, offsets = _dataset(codes, offsets)
+        nt = len(offsets) - 1
+        f = np.empty(nt, np.float64)
+        keep = codes if codes.size else np.zeros(1, np.uint8)
+        self._check(self._lib.gakco_decision(self._h, keep.ctypes.data, offsets.ctypes.data, nt,
+                                             _ptr(f) if nt else None))
+        return f
+
+    def submit(self, codes, offsets, khat=True, K=True, decision=False):
         """Queue a cross-kernel request; returns its ticket.  The output
         arrays are kept alive by the context until poll() reports done."""
         codes, offsets = _dataset(codes, offsets)
         nt = len(offsets) - 1
         out = {"K": np.empty((nt, self._ntrain), np.int32) if K else None,
-               "Khat": np.empty((nt, self._ntrain), np.float64) if khat else None}
+               "Khat": np.empty((nt, self._ntrain), np.float64) if khat else None,
+               "decision": np.empty(nt, np.float64) if decision else None}
         keep = codes if codes.size else np.zeros(1, np.uint8)
         t = ctypes.c_uint64()
-        rc = self._lib.gakco_submit(self._h, keep.ctypes.data, offsets.ctypes.data, nt,
-                                    _ptr(out["K"]), _ptr(out["Khat"]), ctypes.byref(t))
+        rc = self._lib.gakco_submit_svm(self._h, keep.ctypes.data, offsets.ctypes.data, nt,
+                                        _ptr(out["K"]), _ptr(out["Khat"]), _ptr(out["decision"]),
+                                        ctypes.byref(t))
         self._check(rc)
         self._inflight[t.value] = out
         return t.value
@@ -321,7 +345,7 @@ def _add_cross_methods(cls):
         out["latency_ms"] = lat.value
         return out
 
-    for f in (fit, fit_device, cross_fitted, cross_fitted_device, cross, submit, poll):
+    for f in (fit, fit_device, cross_fitted, cross_fitted_device, cross, set_svm, decision, submit, poll):
         setattr(cls, f.__name__, f)
     return cls
 

@@ -104,7 +104,7 @@ struct Work {
   cudaStream_t cs = nullptr;
   DevBuf fullkey, wid, ewin, eseq, efe, keyA, keyB, valA, valB, hist, tcnt, segtot, estart,
       etseq, efid, fstart, tables, codes, outK, outKhat, outNm, rinv, status, Cplain, Cacc, ea, eb,
-      Cd, Cx, Adense, dmaxc, dovf;
+      Cd, Cx, Adense, dmaxc, dovf, outF;
   void* h_tables = nullptr;
   size_t h_tables_cap = 0;
   void* h_status = nullptr;
@@ -119,7 +119,7 @@ struct Work {
     return {&fullkey, &wid, &ewin,   &eseq,  &efe,  &keyA,  &keyB,  &valA,    &valB,
             &hist,    &tcnt,    &segtot, &estart, &etseq, &efid, &fstart, &tables, &codes,
             &outK,    &outKhat, &outNm,  &rinv,  &status, &Cplain, &Cacc, &ea,    &eb,
-            &Cd,      &Cx,      &Adense, &dmaxc,  &dovf};
+            &Cd,      &Cx,      &Adense, &dmaxc,  &dovf,  &outF};
   }
   size_t bytes() {
     size_t s = 0;
@@ -135,6 +135,11 @@ struct Train {
   uint64_t G = 0;
   std::vector<uint32_t> woff;
   DevBuf ukey, ufirst, eseq, nfeat, diagC, rinv;
+  // SVM coefficients alpha_i y_i for decision values (Eq. 1), if set.
+  DevBuf svm;
+  double svm_bias = 0;
+  int svm_kind = 0;
+  bool svm_ok = false;
 };
 
 struct Request {
@@ -145,6 +150,7 @@ struct Request {
   uint64_t windows = 0;
   int32_t* K = nullptr;     // caller host buffers
   double* Khat = nullptr;
+  double* F = nullptr;      // SVM decision values, or null
   int rc = 1;               // 1 pending, 0 done, < 0 error
   std::string err;
   double t_submit = 0, t_done = 0;
@@ -157,7 +163,7 @@ struct Slot {
   int32_t nt = 0;
   bool busy = false;
   std::atomic<bool> gpu_done{false};
-  size_t k_off = 0, kh_off = 0;  // output offsets in the pinned staging
+  size_t k_off = 0, kh_off = 0, f_off = 0;  // output offsets in the pinned staging
 };
 
 }  // namespace
@@ -1309,6 +1315,7 @@ int fit(gakco_ctx* c, const uint8_t* d_codes, const int64_t* off, int32_t n) {
   Work& w = c->main;
   Train& T = c->train;
   T.ok = false;
+  T.svm_ok = false;  // coefficients belong to the previous training set
   Plan p;
   int rc = plan_datasets(c, w, p, 1, &d_codes, &off, &n, nullptr, nullptr, nullptr, false);
   if (rc != GAKCO_OK) return rc;
@@ -1357,11 +1364,13 @@ int fit(gakco_ctx* c, const uint8_t* d_codes, const int64_t* off, int32_t n) {
 }
 
 // Enqueue the cross kernel of one test batch on w (device codes, host
-// offsets; K / Khat device outputs of nt x n_train).  Does not wait.
+// offsets; K / Khat device outputs of nt x n_train, dF nt SVM decision
+// values, each may be null).  Does not wait.
 int enqueue_cross(gakco_ctx* c, Work& w, const uint8_t* d_codes, const int64_t* off, int32_t nt,
-                  int32_t* dK, double* dKhat) {
+                  int32_t* dK, double* dKhat, double* dF = nullptr) {
   Train& T = c->train;
   if (!T.ok) return wfail(w, GAKCO_E_INVALID, "no training set: call gakco_fit first");
+  if (dF && !T.svm_ok) return wfail(w, GAKCO_E_INVALID, "no SVM coefficients: call gakco_set_svm first");
   uint64_t twmax = 1;
   for (size_t y = 0; y + 1 < T.woff.size(); ++y) twmax = std::max<uint64_t>(twmax, T.woff[y + 1] - T.woff[y]);
   Plan p;
@@ -1421,14 +1430,19 @@ int enqueue_cross(gakco_ctx* c, Work& w, const uint8_t* d_codes, const int64_t* 
   launch_vec_diag(x.xo.Cd, (uint32_t)nt, x, x.xo.rinv, w.cs);
   launch_cross_combine(x, dK, dKhat, w.cs);
   w.launches += 5;
+  if (dF) {
+    launch_svm_decision(x, (const double*)T.svm.p, T.svm_bias, T.svm_kind, dF, w.cs);
+    w.launches += 1;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return wcuda(w, e, "kernel launch");
   return GAKCO_OK;
 }
 
-// Synchronous cross kernel on host buffers, on the context's Work.
+// Synchronous cross kernel on host buffers, on the context's Work (F: SVM
+// decision values, nt, or null).
 int cross_host(gakco_ctx* c, const uint8_t* codes, const int64_t* off, int32_t nt, int32_t* K,
-               double* Khat) {
+               double* Khat, double* F = nullptr) {
   Work& w = c->main;
   int rc;
   if (nt < 0 || nt > 65535) return wfail(w, GAKCO_E_INVALID, "nt = %d outside [0, 65535]", nt);
@@ -1440,16 +1454,18 @@ int cross_host(gakco_ctx* c, const uint8_t* codes, const int64_t* off, int32_t n
   ENSURE(codes, cbytes + 16);
   ENSURE(outK, nel * 4 + 16);
   ENSURE(outKhat, nel * 8 + 16);
+  if (F) ENSURE(outF, (size_t)nt * 8);
   cudaError_t e = cudaSuccess;
   if (cbytes) e = cudaMemcpyAsync(w.codes.p, codes, cbytes, cudaMemcpyHostToDevice, w.cs);
   if (e != cudaSuccess) return wcuda(w, e, "copy codes to device");
-  if ((rc = enqueue_cross(c, w, (const uint8_t*)w.codes.p, off, nt, (int32_t*)w.outK.p,
-                          (double*)w.outKhat.p)) != GAKCO_OK)
+  if ((rc = enqueue_cross(c, w, (const uint8_t*)w.codes.p, off, nt, K ? (int32_t*)w.outK.p : nullptr,
+                          Khat ? (double*)w.outKhat.p : nullptr, F ? (double*)w.outF.p : nullptr)) != GAKCO_OK)
     return rc;
   if ((rc = sync_and_check(c, w)) != GAKCO_OK) return rc;
   if (K && nel) e = cudaMemcpyAsync(K, w.outK.p, nel * 4, cudaMemcpyDeviceToHost, w.cs);
   if (e == cudaSuccess && Khat && nel)
     e = cudaMemcpyAsync(Khat, w.outKhat.p, nel * 8, cudaMemcpyDeviceToHost, w.cs);
+  if (e == cudaSuccess && F) e = cudaMemcpyAsync(F, w.outF.p, (size_t)nt * 8, cudaMemcpyDeviceToHost, w.cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(w.cs);
   if (e != cudaSuccess) return wcuda(w, e, "copy results to host");
   return GAKCO_OK;
@@ -1498,9 +1514,12 @@ int launch_batch(gakco_ctx* c, Slot& s) {
   s.nt = nt;
   const uint32_t ntr = (uint32_t)c->train.n;
   const size_t nel = (size_t)nt * ntr;
+  bool want_f = false;
+  for (Request* r : s.batch) want_f |= r->F != nullptr;
   s.k_off = align_up(cbytes, 256);
   s.kh_off = align_up(s.k_off + nel * 4, 256);
-  if ((rc = ensure_pinned(w, w.h_io, w.h_io_cap, s.kh_off + nel * 8 + 256, "serve staging")) != GAKCO_OK)
+  s.f_off = align_up(s.kh_off + nel * 8, 256);
+  if ((rc = ensure_pinned(w, w.h_io, w.h_io_cap, s.f_off + (size_t)nt * 8 + 256, "serve staging")) != GAKCO_OK)
     return rc;
   uint8_t* hio = (uint8_t*)w.h_io;
   size_t pos = 0;
@@ -1512,14 +1531,17 @@ int launch_batch(gakco_ctx* c, Slot& s) {
   ENSURE(codes, cbytes + 16);
   ENSURE(outK, nel * 4 + 16);
   ENSURE(outKhat, nel * 8 + 16);
+  if (want_f) ENSURE(outF, (size_t)nt * 8);
   cudaError_t e = cudaSuccess;
   if (cbytes) e = cudaMemcpyAsync(w.codes.p, hio, cbytes, cudaMemcpyHostToDevice, w.cs);
   if (e != cudaSuccess) return wcuda(w, e, "copy codes to device");
   if ((rc = enqueue_cross(c, w, (const uint8_t*)w.codes.p, off.data(), nt, (int32_t*)w.outK.p,
-                          (double*)w.outKhat.p)) != GAKCO_OK)
+                          (double*)w.outKhat.p, want_f ? (double*)w.outF.p : nullptr)) != GAKCO_OK)
     return rc;
   e = cudaMemcpyAsync(hio + s.k_off, w.outK.p, nel * 4, cudaMemcpyDeviceToHost, w.cs);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hio + s.kh_off, w.outKhat.p, nel * 8, cudaMemcpyDeviceToHost, w.cs);
+  if (e == cudaSuccess && want_f)
+    e = cudaMemcpyAsync(hio + s.f_off, w.outF.p, (size_t)nt * 8, cudaMemcpyDeviceToHost, w.cs);
   if (e == cudaSuccess) e = cudaMemcpyAsync(w.h_status, w.status.p, 128, cudaMemcpyDeviceToHost, w.cs);
   if (e == cudaSuccess) e = cudaLaunchHostFunc(w.cs, on_slot_done, &s);
   if (e != cudaSuccess) return wcuda(w, e, "enqueue results");
@@ -1541,6 +1563,7 @@ int complete_batch(gakco_ctx* c, Slot& s) {
     const size_t rows = (size_t)r->nt;
     if (r->K) memcpy(r->K, hio + s.k_off + (size_t)s.row0[i] * ntr * 4, rows * ntr * 4);
     if (r->Khat) memcpy(r->Khat, hio + s.kh_off + (size_t)s.row0[i] * ntr * 8, rows * ntr * 8);
+    if (r->F) memcpy(r->F, hio + s.f_off + (size_t)s.row0[i] * 8, rows * 8);
   }
   return GAKCO_OK;
 }
@@ -1903,7 +1926,7 @@ void gakco_destroy(gakco_ctx* c) {
   drop_graph(c);
   release_work(c->main);
   Train& T = c->train;
-  DevBuf* tb[] = {&T.ukey, &T.ufirst, &T.eseq, &T.nfeat, &T.diagC, &T.rinv};
+  DevBuf* tb[] = {&T.ukey, &T.ufirst, &T.eseq, &T.nfeat, &T.diagC, &T.rinv, &T.svm};
   for (DevBuf* b : tb) release(*b);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -2152,6 +2175,41 @@ int gakco_cross_fitted(gakco_ctx* c, const uint8_t* codes, const int64_t* offset
   return ret(c, c->main, cross_host(c, codes, offsets, nt, K, Khat));
 }
 
+int gakco_set_svm(gakco_ctx* c, const double* coef, int32_t n, double bias, int kind) {
+  if (!c) return GAKCO_E_INVALID;
+  c->err.clear();
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    bool busy = !c->pending.empty();
+    for (auto& sp : c->slots) busy |= sp->busy;
+    if (busy) return fail(c, GAKCO_E_INVALID, "requests are in flight; wait for them before setting coefficients");
+  }
+  Train& T = c->train;
+  if (!T.ok) return fail(c, GAKCO_E_INVALID, "no training set: call gakco_fit first");
+  if (n != T.n) return fail(c, GAKCO_E_INVALID, "%d coefficients for %d training sequences", n, T.n);
+  if (kind != 0 && kind != 1) return fail(c, GAKCO_E_INVALID, "kernel kind must be 0 (Khat) or 1 (K)");
+  if (n > 0 && !coef) return fail(c, GAKCO_E_INVALID, "null coefficients");
+  Work& w = c->main;
+  int rc = ensure(c, w, T.svm, (size_t)std::max(n, 1) * 8, "svm coefficients");
+  if (rc != GAKCO_OK) return ret(c, w, rc);
+  cudaError_t e = cudaSuccess;
+  if (n > 0) e = cudaMemcpyAsync(T.svm.p, coef, (size_t)n * 8, cudaMemcpyHostToDevice, w.cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(w.cs);
+  if (e != cudaSuccess) return ret(c, w, wcuda(w, e, "copy coefficients"));
+  T.svm_bias = bias;
+  T.svm_kind = kind;
+  T.svm_ok = true;
+  return GAKCO_OK;
+}
+
+int gakco_decision(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t nt,
+                   double* decision) {
+  if (!c) return GAKCO_E_INVALID;
+  c->err.clear();
+  if (nt > 0 && !decision) return fail(c, GAKCO_E_INVALID, "null decision buffer");
+  return ret(c, c->main, cross_host(c, codes, offsets, nt, nullptr, nullptr, decision));
+}
+
 int gakco_cross_fitted_device(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets,
                               int32_t nt, int32_t* K, double* Khat, void* stream) {
   if (!c) return GAKCO_E_INVALID;
@@ -2182,9 +2240,18 @@ int gakco_cross(gakco_ctx* c, const uint8_t* test_codes, const int64_t* test_off
 
 int gakco_submit(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t nt,
                  int32_t* K, double* Khat, uint64_t* ticket) {
+  return gakco_submit_svm(c, codes, offsets, nt, K, Khat, nullptr, ticket);
+}
+
+int gakco_submit_svm(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t nt,
+                     int32_t* K, double* Khat, double* decision, uint64_t* ticket) {
   if (!c || !ticket) return GAKCO_E_INVALID;
   if (nt < 1 || nt > 65535 || !offsets) return GAKCO_E_INVALID;
   if (!c->train.ok) return GAKCO_E_INVALID;
+  if (decision) {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!c->train.svm_ok) return fail(c, GAKCO_E_INVALID, "no SVM coefficients: call gakco_set_svm first");
+  }
   std::unique_ptr<Request> r(new Request());
   r->nt = nt;
   r->off.assign(offsets, offsets + nt + 1);
@@ -2195,6 +2262,7 @@ int gakco_submit(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int
   r->windows = req_windows(c, r.get());
   r->K = K;
   r->Khat = Khat;
+  r->F = decision;
   r->t_submit = now_ms();
   std::lock_guard<std::mutex> lk(c->mu);
   if (!c->serving) {

@@ -286,7 +286,43 @@ k_cross_combine(const CrossParams p, int32_t* __restrict__ K, double* __restrict
   }
 }
 
+// SVM decision values (Eq. 1): f(t) = sum_y coef[y] k(t, y) + bias with
+// coef[y] = alpha_y * label_y supplied by the caller and k = Khat (kind 0,
+// computed exactly as k_cross_combine writes it) or K (kind 1).  One block
+// per test row and a fixed-order reduction, so a row's value does not
+// depend on the batch it ran in.
+__global__ void __launch_bounds__(256)
+k_svm_decision(const CrossParams p, const double* __restrict__ coef, double bias, int kind,
+               double* __restrict__ f) {
+  __shared__ double red[256];
+  const uint32_t t = blockIdx.x;
+  const uint64_t plane = (uint64_t)p.xo.nt * p.tr.n;
+  double acc = 0.0;
+  for (uint32_t y = threadIdx.x; y < p.tr.n; y += 256) {
+    const uint64_t o = (uint64_t)t * p.tr.n + y;
+    uint32_t C[kMaxLevels], N[kMaxLevels];
+#pragma unroll
+    for (int m = 0; m < kMaxLevels; ++m) C[m] = (uint32_t)m <= p.M ? p.xo.Cx[m * plane + o] : 0u;
+    const uint32_t k = ie_kernel(C, p.M, p.ie, p.h, N);
+    const double v = kind ? (double)k : ((double)k * p.xo.rinv[t]) * p.tr.rinv[y];
+    acc += coef[y] * v;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (uint32_t s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) f[t] = red[0] + bias;
+}
+
 }  // namespace
+
+void launch_svm_decision(const CrossParams& p, const double* coef, double bias, int kind, double* f,
+                         cudaStream_t st) {
+  if (p.xo.nt == 0) return;
+  k_svm_decision<<<p.xo.nt, 256, 0, st>>>(p, coef, bias, kind, f);
+}
 
 void launch_train_index(bool wide, const SegDesc* segs, const uint32_t* tile_seg, uint32_t ntiles,
                         const uint32_t* segtot, const void* keys, const uint32_t* estart,

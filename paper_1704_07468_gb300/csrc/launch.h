@@ -156,6 +156,10 @@ void launch_cross_accum(const CrossParams& p, int blocks, size_t smem, cudaStrea
 void launch_vec_diag(const uint32_t* Cd, uint32_t n, const CrossParams& p, double* rinv,
                      cudaStream_t st);
 void launch_cross_combine(const CrossParams& p, int32_t* K, double* Khat, cudaStream_t st);
+// SVM decision values f[t] = sum_y coef[y] k(t, y) + bias (Eq. 1); k = Khat
+// (kind 0) or K (kind 1); f holds nt values.
+void launch_svm_decision(const CrossParams& p, const double* coef, double bias, int kind, double* f,
+                         cudaStream_t st);
 
 // k_dense.cu ------------------------------------------------------------
 // One dense problem: the count matrix A of one dataset over a run of masks
