@@ -298,6 +298,22 @@ int gakco_poll(gakco_ctx *ctx, uint64_t ticket, int timeout_ms,
  * with the request's decision values as one more output (nt doubles, may
  * be NULL); it fails with GAKCO_E_INVALID when no coefficients are set.
  */
+/*
+ * Adding sequences to the fitted set (the adaptive training that Section 3.2
+ * discusses with Fig. 5(c): the kernel grows as new sequences arrive).  K_old is the caller's n x n Gram matrix of the
+ * fitted set (from gakco_gram on the same sequences, or a previous
+ * gakco_extend); the call computes the new rows against the fitted set
+ * (its cross kernel) and the Gram matrix of the nb new sequences, and
+ * writes the (n + nb) x (n + nb) Gram matrix of the union, old sequences
+ * first, into K_out and its normalisation into Khat_out (may be NULL),
+ * equal to gakco_gram on the union.  The fitted set then becomes the union
+ * (SVM coefficients are dropped).  Host buffers; fails with
+ * GAKCO_E_INVALID while served requests are in flight.
+ */
+int gakco_extend(gakco_ctx *ctx, const uint8_t *codes, const int64_t *offsets,
+                 int32_t nb, const int32_t *K_old, int32_t *K_out,
+                 double *Khat_out);
+
 int gakco_set_svm(gakco_ctx *ctx, const double *coef, int32_t n, double bias,
                   int kind);
 int gakco_decision(gakco_ctx *ctx, const uint8_t *codes,

@@ -95,6 +95,7 @@ def load_library(build_if_missing: bool = False):
         "gakco_poll": ([p, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
                        ctypes.c_int),
         "gakco_set_svm": ([p, p, i32, ctypes.c_double, ctypes.c_int], ctypes.c_int),
+        "gakco_extend": ([p, p, p, i32, p, p, p], ctypes.c_int),
         "gakco_decision": ([p, p, p, i32, p], ctypes.c_int),
         "gakco_submit_svm": ([p, p, p, i32, p, p, p, ctypes.POINTER(ctypes.c_uint64)],
                              ctypes.c_int),
@@ -298,6 +299,21 @@ def _add_cross_methods(cls):
         self.fit(*train)
         return self.cross_fitted(*test, khat=khat)
 
+    def extend(self, codes, offsets, K_old, khat=True):
+        """Add sequences to the fitted set; returns the Gram matrix of the
+        union (old sequences first) given K_old, the fitted set's."""
+        codes, offsets = _dataset(codes, offsets)
+        nb = len(offsets) - 1
+        K_old = np.ascontiguousarray(K_old, dtype=np.int32)
+        N = self._ntrain + nb
+        out = {"K": np.empty((N, N), np.int32), "Khat": np.empty((N, N), np.float64) if khat else None}
+        keep = codes if codes.size else np.zeros(1, np.uint8)
+        self._check(self._lib.gakco_extend(self._h, keep.ctypes.data, offsets.ctypes.data, nb,
+                                           _ptr(K_old) if K_old.size else None, _ptr(out["K"]),
+                                           _ptr(out["Khat"])))
+        self._ntrain = N
+        return out
+
     def set_svm(self, coef, bias=0.0, kind=0):
         """Coefficients alpha_i * y_i of the fitted training set and the bias
         for decision values (Eq. 1); kind 0 uses Khat, 1 uses K."""
@@ -345,7 +361,8 @@ def _add_cross_methods(cls):
         out["latency_ms"] = lat.value
         return out
 
-    for f in (fit, fit_device, cross_fitted, cross_fitted_device, cross, set_svm, decision, submit, poll):
+    for f in (fit, fit_device, cross_fitted, cross_fitted_device, cross, extend, set_svm, decision, submit,
+              poll):
         setattr(cls, f.__name__, f)
     return cls
 

@@ -135,6 +135,8 @@ struct Train {
   uint64_t G = 0;
   std::vector<uint32_t> woff;
   DevBuf ukey, ufirst, eseq, nfeat, diagC, rinv;
+  DevBuf tcodes;               // the training codes (for adding sequences)
+  std::vector<int64_t> toff;   // their offsets
   // SVM coefficients alpha_i y_i for decision values (Eq. 1), if set.
   DevBuf svm;
   double svm_bias = 0;
@@ -1358,9 +1360,85 @@ int fit(gakco_ctx* c, const uint8_t* d_codes, const int64_t* off, int32_t n) {
   launch_vec_diag(tr.diagC, (uint32_t)n, x, tr.rinv, w.cs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return wcuda(w, e, "kernel launch");
+  // Keep the training codes: adding sequences later refits on the union.
+  const uint64_t cbytes = n > 0 ? (uint64_t)off[n] : 0;
+  if ((rc = ensure(c, w, T.tcodes, cbytes + 16, "training codes")) != GAKCO_OK) return rc;
+  if (cbytes && (e = cudaMemcpyAsync(T.tcodes.p, d_codes, cbytes, cudaMemcpyDeviceToDevice, w.cs)) != cudaSuccess)
+    return wcuda(w, e, "keep training codes");
+  T.toff.assign(off, off + n + 1);
+  if (n == 0) T.toff.assign(1, 0);
   if ((rc = sync_and_check(c, w)) != GAKCO_OK) return rc;
   T.ok = true;
   return GAKCO_OK;
+}
+
+int cross_host(gakco_ctx* c, const uint8_t* codes, const int64_t* off, int32_t nt, int32_t* K,
+               double* Khat, double* F = nullptr);
+
+// Adds nb sequences (host buffers) to the fitted set: the new rows against
+// the old set are its cross kernel, the new block a Gram kernel of the new
+// sequences; together with the caller's Gram matrix of the old set they
+// form the Gram matrix of the union (old sequences first), normalised as
+// the Gram engine does it.  The fitted set becomes the union.
+int extend(gakco_ctx* c, const uint8_t* codes, const int64_t* off, int32_t nb, const int32_t* Kold,
+           int32_t* Kout, double* Khat) {
+  Work& w = c->main;
+  Train& T = c->train;
+  int rc;
+  if (!T.ok) return wfail(w, GAKCO_E_INVALID, "no training set: call gakco_fit first");
+  const int32_t n = T.n;
+  if (nb < 0 || (nb > 0 && !off)) return wfail(w, GAKCO_E_INVALID, "bad new sequences");
+  if ((int64_t)n + nb > 65535) return wfail(w, GAKCO_E_INVALID, "n + nb = %d above 65535", n + nb);
+  if ((n > 0 && !Kold) || (n + nb > 0 && !Kout)) return wfail(w, GAKCO_E_INVALID, "null kernel buffer");
+  const size_t N = (size_t)n + nb;
+  std::vector<int32_t> kbt((size_t)nb * n), kbb((size_t)nb * nb);
+  if (nb > 0 && n > 0 && (rc = cross_host(c, codes, off, nb, kbt.data(), nullptr)) != GAKCO_OK) return rc;
+  if (nb > 0) {
+    int32_t* kp = kbb.data();
+    if ((rc = gram_host(c, 1, &codes, &off, &nb, &kp, nullptr, nullptr)) != GAKCO_OK) return rc;
+  }
+  for (size_t i = 0; i < N; ++i)
+    for (size_t j = 0; j < N; ++j) {
+      int32_t v;
+      if (i < (size_t)n && j < (size_t)n)
+        v = Kold[i * n + j];
+      else if (i < (size_t)n)
+        v = kbt[(j - n) * n + i];
+      else if (j < (size_t)n)
+        v = kbt[(i - n) * n + j];
+      else
+        v = kbb[(i - n) * nb + (j - n)];
+      Kout[i * N + j] = v;
+    }
+  if (Khat) {
+    // As the Gram engine: r = 1 / sqrt(K(x, x)) (0 for an empty diagonal),
+    // Khat = (K * r_x) * r_y for x < y, mirrored, exactly 1 on the diagonal.
+    std::vector<double> r(N);
+    for (size_t i = 0; i < N; ++i) {
+      const int32_t d = Kout[i * N + i];
+      r[i] = d ? 1.0 / std::sqrt((double)d) : 0.0;
+    }
+    for (size_t i = 0; i < N; ++i) {
+      Khat[i * N + i] = r[i] > 0.0 ? 1.0 : 0.0;
+      for (size_t j = i + 1; j < N; ++j) {
+        const double v = ((double)Kout[i * N + j] * r[i]) * r[j];
+        Khat[i * N + j] = v;
+        Khat[j * N + i] = v;
+      }
+    }
+  }
+  // Refit on the union: old codes (kept on the device) then the new ones.
+  std::vector<int64_t> uoff(T.toff);
+  const int64_t base = uoff.back();
+  for (int32_t x = 0; x < nb; ++x) uoff.push_back(base + off[x + 1]);
+  const uint64_t newbytes = nb > 0 ? (uint64_t)off[nb] : 0;
+  if ((rc = ensure(c, w, w.codes, (size_t)base + newbytes + 16, "codes")) != GAKCO_OK) return rc;
+  cudaError_t e = cudaSuccess;
+  if (base) e = cudaMemcpyAsync(w.codes.p, T.tcodes.p, (size_t)base, cudaMemcpyDeviceToDevice, w.cs);
+  if (e == cudaSuccess && newbytes)
+    e = cudaMemcpyAsync((uint8_t*)w.codes.p + base, codes, newbytes, cudaMemcpyHostToDevice, w.cs);
+  if (e != cudaSuccess) return wcuda(w, e, "stage the union's codes");
+  return fit(c, (const uint8_t*)w.codes.p, uoff.data(), (int32_t)N);
 }
 
 // Enqueue the cross kernel of one test batch on w (device codes, host
@@ -1442,7 +1520,7 @@ int enqueue_cross(gakco_ctx* c, Work& w, const uint8_t* d_codes, const int64_t* 
 // Synchronous cross kernel on host buffers, on the context's Work (F: SVM
 // decision values, nt, or null).
 int cross_host(gakco_ctx* c, const uint8_t* codes, const int64_t* off, int32_t nt, int32_t* K,
-               double* Khat, double* F = nullptr) {
+               double* Khat, double* F) {
   Work& w = c->main;
   int rc;
   if (nt < 0 || nt > 65535) return wfail(w, GAKCO_E_INVALID, "nt = %d outside [0, 65535]", nt);
@@ -1926,7 +2004,7 @@ void gakco_destroy(gakco_ctx* c) {
   drop_graph(c);
   release_work(c->main);
   Train& T = c->train;
-  DevBuf* tb[] = {&T.ukey, &T.ufirst, &T.eseq, &T.nfeat, &T.diagC, &T.rinv, &T.svm};
+  DevBuf* tb[] = {&T.ukey, &T.ufirst, &T.eseq, &T.nfeat, &T.diagC, &T.rinv, &T.svm, &T.tcodes};
   for (DevBuf* b : tb) release(*b);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -2200,6 +2278,19 @@ int gakco_set_svm(gakco_ctx* c, const double* coef, int32_t n, double bias, int 
   T.svm_kind = kind;
   T.svm_ok = true;
   return GAKCO_OK;
+}
+
+int gakco_extend(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t nb,
+                 const int32_t* K_old, int32_t* K_out, double* Khat_out) {
+  if (!c) return GAKCO_E_INVALID;
+  c->err.clear();
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    bool busy = !c->pending.empty();
+    for (auto& sp : c->slots) busy |= sp->busy;
+    if (busy) return fail(c, GAKCO_E_INVALID, "requests are in flight; wait for them before extending");
+  }
+  return ret(c, c->main, extend(c, codes, offsets, nb, K_old, K_out, Khat_out));
 }
 
 int gakco_decision(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t nt,
