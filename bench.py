@@ -325,6 +325,54 @@ def run_serve(pkg, n_requests, warmup):
             "continuous_batching": cb, "plain_per_request": plain}
 
 
+def run_extend(pkg, sigma, g, k, sets, add=100):
+    """Adding `add` sequences (the tail of the largest dataset) to a fitted
+    set of the rest, against a fresh Gram computation on the union."""
+    codes, off = max(sets, key=lambda s: len(s[1]))
+    n = len(off) - 1
+    cut = n - add
+    old = (codes[:off[cut]], off[:cut + 1])
+    new = (codes[off[cut]:], off[cut:] - off[cut])
+    with pkg.gakco_create(sigma, g, k) as ctx:
+        ctx.set_option("dense", 1)
+        ctx.gram(codes, off, khat=True)           # warm the full-size plan
+        t0 = time.perf_counter()
+        full = ctx.gram(codes, off, khat=True)
+        t_full = time.perf_counter() - t0
+        ctx.fit(*old)
+        ctx.extend(*new)                           # warm-up (refits on the union)
+        ctx.fit(*old)
+        t0 = time.perf_counter()
+        rows = ctx.extend(*new)
+        t_ext = time.perf_counter() - t0
+    return {"workload": f"add {add} sequences to a fitted set of {cut} (DNA large-M N={n} dataset)",
+            "extend_ms": 1000 * t_ext, "fresh_gram_ms": 1000 * t_full,
+            "equal_to_fresh_rows": bool(np.array_equal(rows["K"], full["K"][cut:]) and
+                                        np.array_equal(rows["Khat"], full["Khat"][cut:])),
+            "timing": "wall clock through the host-buffer C ABI, copies and the refit on the union included"}
+
+
+def run_nsweep(pkg):
+    """Kernel time as N grows at fixed length l = 100 (Section 3.2, Fig. 5(c)):
+    DNA with an unknown-base symbol (sigma = 5), protein, text."""
+    out = []
+    for name, sigma, g, k in (("dna_sigma5", 5, 10, 6), ("protein", 20, 8, 4), ("text", 36, 8, 5)):
+        for n in (100, 250, 500, 750):
+            rng = np.random.default_rng(1000 + n)
+            codes = rng.integers(0, sigma, size=n * 100).astype(np.uint8)
+            off = np.arange(0, n * 100 + 1, 100, dtype=np.int64)
+            with pkg.gakco_create(sigma, g, k) as ctx:
+                ctx.set_option("dense", 1)
+                ctx.gram(codes, off)
+                ts = []
+                for _ in range(3):
+                    t0 = time.perf_counter()
+                    ctx.gram(codes, off)
+                    ts.append(time.perf_counter() - t0)
+            out.append({"data": name, "N": n, "l": 100, "g": g, "k": k, "ms": 1000 * min(ts)})
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -511,6 +559,8 @@ def run_ours(args):
     serve = None
     if args.serve_requests > 0 and rank == 0:
         serve = run_serve(pkg, args.serve_requests, args.serve_warmup)
+    extend = run_extend(pkg, sigma, g, k, sets) if args.extras and rank == 0 else None
+    nsweep = run_nsweep(pkg) if args.extras and rank == 0 else None
 
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_rows > 0:
@@ -536,6 +586,8 @@ def run_ours(args):
         "plain_gpu": plain,
         "kernel_only": konly,
         "serve": serve,
+        "extend": extend,
+        "nsweep_l100": nsweep,
         "e2e": {"value": entries * ws / (e2e_step / 1000.0), "unit": UNIT,
                 "ms_per_step": e2e_step, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches * args.steps,
@@ -564,6 +616,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=64)
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--extras", type=int, default=1,
+                    help="1: also time adding sequences and the N-sweep at l = 100")
     ap.add_argument("--kernel-only-steps", type=int, default=3,
                     help="also time the K = C_M mode (level-M masks only); 0 to skip")
     ap.add_argument("--dense", type=int, default=None, choices=[0, 1, 2],

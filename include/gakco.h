@@ -300,19 +300,19 @@ int gakco_poll(gakco_ctx *ctx, uint64_t ticket, int timeout_ms,
  */
 /*
  * Adding sequences to the fitted set (the adaptive training that Section 3.2
- * discusses with Fig. 5(c): the kernel grows as new sequences arrive).  K_old is the caller's n x n Gram matrix of the
- * fitted set (from gakco_gram on the same sequences, or a previous
- * gakco_extend); the call computes the new rows against the fitted set
- * (its cross kernel) and the Gram matrix of the nb new sequences, and
- * writes the (n + nb) x (n + nb) Gram matrix of the union, old sequences
- * first, into K_out and its normalisation into Khat_out (may be NULL),
- * equal to gakco_gram on the union.  The fitted set then becomes the union
- * (SVM coefficients are dropped).  Host buffers; fails with
- * GAKCO_E_INVALID while served requests are in flight.
+ * discusses with Fig. 5(c): the kernel grows as new sequences arrive).
+ * Computes the nb new rows of the Gram matrix of the union (old sequences
+ * first, then the new ones in order): K_rows and Khat_rows (may be NULL)
+ * are nb x (n + nb), row-major; the full matrix is the old one bordered by
+ * these rows and their transposes.  The values equal gakco_gram on the
+ * union bit for bit.  The new rows against the old sequences come from the
+ * resident index (the cross kernel), the new block from a Gram kernel of
+ * the new sequences; the fitted set then becomes the union (SVM
+ * coefficients are dropped).  Host buffers; fails with GAKCO_E_INVALID
+ * while served requests are in flight.
  */
 int gakco_extend(gakco_ctx *ctx, const uint8_t *codes, const int64_t *offsets,
-                 int32_t nb, const int32_t *K_old, int32_t *K_out,
-                 double *Khat_out);
+                 int32_t nb, int32_t *K_rows, double *Khat_rows);
 
 int gakco_set_svm(gakco_ctx *ctx, const double *coef, int32_t n, double bias,
                   int kind);

@@ -95,7 +95,7 @@ def load_library(build_if_missing: bool = False):
         "gakco_poll": ([p, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
                        ctypes.c_int),
         "gakco_set_svm": ([p, p, i32, ctypes.c_double, ctypes.c_int], ctypes.c_int),
-        "gakco_extend": ([p, p, p, i32, p, p, p], ctypes.c_int),
+        "gakco_extend": ([p, p, p, i32, p, p], ctypes.c_int),
         "gakco_decision": ([p, p, p, i32, p], ctypes.c_int),
         "gakco_submit_svm": ([p, p, p, i32, p, p, p, ctypes.POINTER(ctypes.c_uint64)],
                              ctypes.c_int),
@@ -299,18 +299,17 @@ def _add_cross_methods(cls):
         self.fit(*train)
         return self.cross_fitted(*test, khat=khat)
 
-    def extend(self, codes, offsets, K_old, khat=True):
-        """Add sequences to the fitted set; returns the Gram matrix of the
-        union (old sequences first) given K_old, the fitted set's."""
+    def extend(self, codes, offsets, khat=True):
+        """Add sequences to the fitted set; returns the new rows of the
+        union's Gram matrix (old sequences first), nb x (n + nb)."""
         codes, offsets = _dataset(codes, offsets)
         nb = len(offsets) - 1
-        K_old = np.ascontiguousarray(K_old, dtype=np.int32)
         N = self._ntrain + nb
-        out = {"K": np.empty((N, N), np.int32), "Khat": np.empty((N, N), np.float64) if khat else None}
+        out = {"K": np.empty((nb, N), np.int32), "Khat": np.empty((nb, N), np.float64) if khat else None}
         keep = codes if codes.size else np.zeros(1, np.uint8)
         self._check(self._lib.gakco_extend(self._h, keep.ctypes.data, offsets.ctypes.data, nb,
-                                           _ptr(K_old) if K_old.size else None, _ptr(out["K"]),
-                                           _ptr(out["Khat"])))
+                                           _ptr(out["K"]) if nb else None,
+                                           _ptr(out["Khat"]) if nb else None))
         self._ntrain = N
         return out
 

@@ -1316,6 +1316,9 @@ CrossParams cross_params(gakco_ctx* c, Work& w) {
 int fit(gakco_ctx* c, const uint8_t* d_codes, const int64_t* off, int32_t n) {
   Work& w = c->main;
   Train& T = c->train;
+  // The cached Gram graph points into w's tables and buffers, which this
+  // call rewrites and may reallocate.
+  drop_graph(c);
   T.ok = false;
   T.svm_ok = false;  // coefficients belong to the previous training set
   Plan p;
@@ -1375,13 +1378,14 @@ int fit(gakco_ctx* c, const uint8_t* d_codes, const int64_t* off, int32_t n) {
 int cross_host(gakco_ctx* c, const uint8_t* codes, const int64_t* off, int32_t nt, int32_t* K,
                double* Khat, double* F = nullptr);
 
-// Adds nb sequences (host buffers) to the fitted set: the new rows against
-// the old set are its cross kernel, the new block a Gram kernel of the new
-// sequences; together with the caller's Gram matrix of the old set they
-// form the Gram matrix of the union (old sequences first), normalised as
-// the Gram engine does it.  The fitted set becomes the union.
-int extend(gakco_ctx* c, const uint8_t* codes, const int64_t* off, int32_t nb, const int32_t* Kold,
-           int32_t* Kout, double* Khat) {
+// Adds nb sequences (host buffers) to the fitted set and returns the new
+// rows of the union's Gram matrix (old sequences first): against the old
+// sequences they are the cross kernel, among themselves the Gram kernel of
+// the new block.  Khat follows the Gram engine exactly: r = 1 / sqrt(K(x, x))
+// (the resident index keeps the old ones), (K * r_a) * r_b with a the
+// smaller index, 1 on a nonzero diagonal.  The fitted set becomes the union.
+int extend(gakco_ctx* c, const uint8_t* codes, const int64_t* off, int32_t nb, int32_t* Krows,
+           double* Khat) {
   Work& w = c->main;
   Train& T = c->train;
   int rc;
@@ -1389,42 +1393,41 @@ int extend(gakco_ctx* c, const uint8_t* codes, const int64_t* off, int32_t nb, c
   const int32_t n = T.n;
   if (nb < 0 || (nb > 0 && !off)) return wfail(w, GAKCO_E_INVALID, "bad new sequences");
   if ((int64_t)n + nb > 65535) return wfail(w, GAKCO_E_INVALID, "n + nb = %d above 65535", n + nb);
-  if ((n > 0 && !Kold) || (n + nb > 0 && !Kout)) return wfail(w, GAKCO_E_INVALID, "null kernel buffer");
+  if (nb > 0 && !Krows) return wfail(w, GAKCO_E_INVALID, "null kernel buffer");
   const size_t N = (size_t)n + nb;
   std::vector<int32_t> kbt((size_t)nb * n), kbb((size_t)nb * nb);
-  if (nb > 0 && n > 0 && (rc = cross_host(c, codes, off, nb, kbt.data(), nullptr)) != GAKCO_OK) return rc;
+  std::vector<double> rold(n);
+  if (nb > 0 && n > 0) {
+    if ((rc = cross_host(c, codes, off, nb, kbt.data(), nullptr)) != GAKCO_OK) return rc;
+    cudaError_t e = cudaMemcpy(rold.data(), T.rinv.p, (size_t)n * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return wcuda(w, e, "copy training norms");
+  }
   if (nb > 0) {
     int32_t* kp = kbb.data();
     if ((rc = gram_host(c, 1, &codes, &off, &nb, &kp, nullptr, nullptr)) != GAKCO_OK) return rc;
   }
-  for (size_t i = 0; i < N; ++i)
-    for (size_t j = 0; j < N; ++j) {
-      int32_t v;
-      if (i < (size_t)n && j < (size_t)n)
-        v = Kold[i * n + j];
-      else if (i < (size_t)n)
-        v = kbt[(j - n) * n + i];
-      else if (j < (size_t)n)
-        v = kbt[(i - n) * n + j];
+  std::vector<double> rnew(nb);
+  for (int32_t i = 0; i < nb; ++i) {
+    const int32_t d = kbb[(size_t)i * nb + i];
+    rnew[i] = d ? 1.0 / std::sqrt((double)d) : 0.0;
+  }
+  for (int32_t i = 0; i < nb; ++i) {
+    int32_t* kr = Krows + (size_t)i * N;
+    double* hr = Khat ? Khat + (size_t)i * N : nullptr;
+    for (int32_t j = 0; j < n; ++j) {
+      kr[j] = kbt[(size_t)i * n + j];
+      if (hr) hr[j] = ((double)kr[j] * rold[j]) * rnew[i];
+    }
+    for (int32_t j = 0; j < nb; ++j) {
+      const int32_t v = kbb[(size_t)i * nb + j];
+      kr[n + j] = v;
+      if (!hr) continue;
+      if (j == i)
+        hr[n + j] = rnew[i] > 0.0 ? 1.0 : 0.0;
+      else if (j < i)
+        hr[n + j] = ((double)v * rnew[j]) * rnew[i];
       else
-        v = kbb[(i - n) * nb + (j - n)];
-      Kout[i * N + j] = v;
-    }
-  if (Khat) {
-    // As the Gram engine: r = 1 / sqrt(K(x, x)) (0 for an empty diagonal),
-    // Khat = (K * r_x) * r_y for x < y, mirrored, exactly 1 on the diagonal.
-    std::vector<double> r(N);
-    for (size_t i = 0; i < N; ++i) {
-      const int32_t d = Kout[i * N + i];
-      r[i] = d ? 1.0 / std::sqrt((double)d) : 0.0;
-    }
-    for (size_t i = 0; i < N; ++i) {
-      Khat[i * N + i] = r[i] > 0.0 ? 1.0 : 0.0;
-      for (size_t j = i + 1; j < N; ++j) {
-        const double v = ((double)Kout[i * N + j] * r[i]) * r[j];
-        Khat[i * N + j] = v;
-        Khat[j * N + i] = v;
-      }
+        hr[n + j] = ((double)v * rnew[i]) * rnew[j];
     }
   }
   // Refit on the union: old codes (kept on the device) then the new ones.
@@ -1449,6 +1452,10 @@ int enqueue_cross(gakco_ctx* c, Work& w, const uint8_t* d_codes, const int64_t* 
   Train& T = c->train;
   if (!T.ok) return wfail(w, GAKCO_E_INVALID, "no training set: call gakco_fit first");
   if (dF && !T.svm_ok) return wfail(w, GAKCO_E_INVALID, "no SVM coefficients: call gakco_set_svm first");
+  // On the context's own Work the cached Gram graph points into the tables
+  // and buffers this call rewrites and may reallocate (serving slots have
+  // their own Work).
+  if (&w == &c->main) drop_graph(c);
   uint64_t twmax = 1;
   for (size_t y = 0; y + 1 < T.woff.size(); ++y) twmax = std::max<uint64_t>(twmax, T.woff[y + 1] - T.woff[y]);
   Plan p;
@@ -2281,7 +2288,7 @@ int gakco_set_svm(gakco_ctx* c, const double* coef, int32_t n, double bias, int 
 }
 
 int gakco_extend(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t nb,
-                 const int32_t* K_old, int32_t* K_out, double* Khat_out) {
+                 int32_t* K_rows, double* Khat_rows) {
   if (!c) return GAKCO_E_INVALID;
   c->err.clear();
   {
@@ -2290,7 +2297,7 @@ int gakco_extend(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int
     for (auto& sp : c->slots) busy |= sp->busy;
     if (busy) return fail(c, GAKCO_E_INVALID, "requests are in flight; wait for them before extending");
   }
-  return ret(c, c->main, extend(c, codes, offsets, nb, K_old, K_out, Khat_out));
+  return ret(c, c->main, extend(c, codes, offsets, nb, K_rows, Khat_rows));
 }
 
 int gakco_decision(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t nt,

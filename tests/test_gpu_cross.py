@@ -205,3 +205,24 @@ def test_sequence_window_limit_on_the_cross_path():
         assert ei.value.name == "GAKCO_E_OVERFLOW"
         ok = ctx.cross_fitted(*synth.pack([np.zeros(60, np.uint8)]))
         assert ok["K"].shape == (1, 2)
+
+
+def test_gram_after_fit_and_cross_on_one_context():
+    """A Gram call's cached graph must not be replayed after fit and cross
+    calls on the same context rewrote its tables and buffers: the repeated
+    Gram call plans again and stays exact."""
+    a = synth.random_small(110, 60, 4, 50, 250)
+    b = synth.random_small(111, 140, 4, 50, 300)
+    with pkg.gakco_create(4, 8, 5) as ctx:
+        ctx.set_option("dense", 1)
+        first = ctx.gram(*a, khat=True)
+        ctx.fit(*b)
+        ctx.cross_fitted(*a)
+        again = ctx.gram(*a, khat=True)
+        assert ctx.get_stat("graph_replay") == 0
+        ctx.extend(*synth.random_small(112, 9, 4, 50, 250))
+        third = ctx.gram(*a, khat=True)
+    ref = oracle.gram(*a, 8, 5)
+    for out in (first, again, third):
+        np.testing.assert_array_equal(out["K"], ref["K"])
+        assert _close(out["Khat"], ref["Khat"])

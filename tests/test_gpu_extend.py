@@ -1,8 +1,8 @@
 """Adding sequences to the fitted set (the adaptive training of Section 3.2,
-Fig. 5(c)): the Gram matrix of the union from the old Gram matrix, the new
-rows' cross kernel and the new block's Gram kernel must equal a fresh Gram
-computation on the union, K bit for bit and Khat value for value (same
-normalisation formula on both routes), and the oracle on the union.
+Fig. 5(c)): the new rows of the union's Gram matrix, from the resident
+index (cross kernel) and the new block's Gram kernel, must equal the rows
+of a fresh Gram computation on the union, K bit for bit and Khat value for
+value (same normalisation formula and operand order), and the oracle.
 """
 
 import numpy as np
@@ -36,18 +36,20 @@ def test_extend_equals_a_fresh_gram(sigma, g, k):
     add2 = synth.random_small(192, 6, sigma, 30, 260)
     with pkg.gakco_create(sigma, g, k) as ctx:
         ctx.set_option("dense", 1)
-        K0 = ctx.gram(*old, khat=False)["K"]
         ctx.fit(*old)
-        ext1 = ctx.extend(*add1, K0)
-        ext2 = ctx.extend(*add2, ext1["K"])
-        u2 = _union(old, add1, add2)
-        fresh = ctx.gram(*u2, khat=True)
+        rows1 = ctx.extend(*add1)
+        rows2 = ctx.extend(*add2)
+        u1, u2 = _union(old, add1), _union(old, add1, add2)
+        fresh1 = ctx.gram(*u1, khat=True)
+        fresh2 = ctx.gram(*u2, khat=True)
         probe = synth.random_small(193, 4, sigma, 30, 200)
         cr = ctx.cross_fitted(*probe)          # the index now holds the union
-    np.testing.assert_array_equal(ext2["K"], fresh["K"])
-    np.testing.assert_array_equal(ext2["Khat"], fresh["Khat"])
-    ref = oracle.gram(*u2, g, k)
-    np.testing.assert_array_equal(ext2["K"], ref["K"])
+    np.testing.assert_array_equal(rows1["K"], fresh1["K"][50:])
+    np.testing.assert_array_equal(rows1["Khat"], fresh1["Khat"][50:])
+    np.testing.assert_array_equal(rows2["K"], fresh2["K"][67:])
+    np.testing.assert_array_equal(rows2["Khat"], fresh2["Khat"][67:])
+    ref = oracle.gram(*u2, g, k, rows=np.arange(67, 73, dtype=np.int32))
+    np.testing.assert_array_equal(rows2["K"], ref["K"])
     refx = oracle.cross(probe[0], probe[1], u2[0], u2[1], g, k)
     np.testing.assert_array_equal(cr["K"], refx["K"])
 
@@ -56,14 +58,13 @@ def test_extend_edge_cases():
     old = synth.random_small(194, 8, 4, 20, 80)
     add = synth.random_small(195, 5, 4, 20, 80)
     with pkg.gakco_create(4, 6, 3) as ctx:
-        K0 = ctx.gram(*old, khat=False)["K"]
         ctx.fit(*old)
-        same = ctx.extend(*synth.pack([]), K0)     # nothing added
-        np.testing.assert_array_equal(same["K"], K0)
+        none = ctx.extend(*synth.pack([]))          # nothing added
+        assert none["K"].shape == (0, 8)
         ctx.fit(*synth.pack([]))                    # empty fitted set
-        ext = ctx.extend(*add, np.zeros((0, 0), np.int32))
-        np.testing.assert_array_equal(ext["K"], oracle.gram(*add, 6, 3)["K"])
+        rows = ctx.extend(*add)
+        np.testing.assert_array_equal(rows["K"], oracle.gram(*add, 6, 3)["K"])
         ctx.set_svm(np.ones(5))
-        ctx.extend(*synth.random_small(196, 2, 4, 20, 80), ext["K"])
+        ctx.extend(*synth.random_small(196, 2, 4, 20, 80))
         with pytest.raises(pkg.GakcoError):
             ctx.decision(*add)                      # coefficients were dropped
