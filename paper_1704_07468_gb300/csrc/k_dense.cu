@@ -228,34 +228,35 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
       }
     }
     __syncthreads();
-    uint4* out = (uint4*)(P.A + (uint64_t)x * ld + c0);
-    for (uint32_t j = tid; j < ncol / 16; j += kScatterThreads) {
-      uint4* cw = (uint4*)cnt + 2 * j;
-      const uint4 a = cw[0], b = cw[1];
-      cw[0] = make_uint4(0, 0, 0, 0);
-      cw[1] = make_uint4(0, 0, 0, 0);
-      const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-      uint32_t m = 0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) m = __vmaxu2(m, w[q]);
+    // Eight columns (one 16-byte word of counts) per thread and step:
+    // consecutive threads take consecutive words, so every shared-memory
+    // access of a warp covers 512 contiguous bytes and every global store
+    // 256 contiguous bytes.
+    uint2* out = (uint2*)(P.A + (uint64_t)x * ld + c0);
+    uint4* cw = (uint4*)cnt;
+    for (uint32_t u = tid; u < ncol / 8; u += kScatterThreads) {
+      const uint4 a = cw[u];
+      cw[u] = make_uint4(0, 0, 0, 0);
+      const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+      const uint32_t m = __vmaxu2(__vmaxu2(w[0], w[1]), __vmaxu2(w[2], w[3]));
       mx2 = __vmaxu2(mx2, m);
-      uint32_t e[8];
+      uint32_t e[4];
       if ((m & 0xFFFFu) <= 16u && (m >> 16) <= 16u) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) e[q] = e4m3x2_of_counts(w[q]);
+        for (int q = 0; q < 4; ++q) e[q] = e4m3x2_of_counts(w[q]);
       } else {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) e[q] = e4m3x2_of_counts(__vminu2(w[q], 0x00100010u));
+        for (int q = 0; q < 4; ++q) e[q] = e4m3x2_of_counts(__vminu2(w[q], 0x00100010u));
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
+        for (int q = 0; q < 8; ++q) {
           const uint32_t c = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
           if (c > 16) {
             const uint32_t slot = atomicAdd(ovf_n, 1u);
-            if (slot < ovf_cap) ovf[slot] = DenseOvf{p0 + lo, x, (uint32_t)(c0 + 16 * j + q), c};
+            if (slot < ovf_cap) ovf[slot] = DenseOvf{p0 + lo, x, (uint32_t)(c0 + 8 * u + q), c};
           }
         }
       }
-      out[j] = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16), e[6] | (e[7] << 16));
+      out[u] = make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
     }
     // The next chunk's counting waits at its first barrier for this
     // conversion (and its clearing) to finish.
