@@ -134,6 +134,9 @@ const char *gakco_last_error(const gakco_ctx *ctx);
  * computes every level as usual.  This identity is derived here; the paper
  * computes all levels.  Default 0. */
 #define GAKCO_OPT_KERNEL_ONLY 18
+#define GAKCO_OPT_OVERLAP 19        /* 1 (default): a Gram call runs its dense levels and its
+                                       sparse levels as two concurrent branches */
+#define GAKCO_OPT_DENSE_SMS 20      /* CTAs of the dense GEMM (0 = one per SM, default) */
 int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 
 /*

@@ -102,6 +102,8 @@ double now_ms() {
 // Device buffers and stream of one pipeline instance.
 struct Work {
   cudaStream_t cs = nullptr;
+  cudaStream_t cs2 = nullptr;                      // second branch of a Gram call
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   DevBuf fullkey, wid, ewin, eseq, efe, keyA, keyB, valA, valB, hist, tcnt, segtot, estart,
       etseq, efid, fstart, tables, codes, outK, outKhat, outNm, rinv, status, Cplain, Cacc, ea, eb,
       Cd, Cx, Adense, dmaxc, dovf, outF;
@@ -110,6 +112,9 @@ struct Work {
   void* h_status = nullptr;
   void* h_io = nullptr;  // pinned staging of a serving slot
   size_t h_io_cap = 0;
+  void* h_out = nullptr;  // pinned staging of large host outputs (two chunks)
+  size_t h_out_cap = 0;
+  cudaEvent_t ev_out[2] = {nullptr, nullptr};
   int64_t launches = 0;
   bool dense_overflow = false;  // the last run's dense overflow list ran out of room
   std::string err;
@@ -200,6 +205,8 @@ struct gakco_ctx {
   // tiles and that concurrent tiles stay within one L2-sized window of A.
   int64_t dense_run_cols = 131072;
   int kernel_only = 0;  // 1: compute level M alone when N_m is not requested (K = C_M)
+  int overlap = 1;      // 1: dense and sparse levels of a Gram call run on two streams
+  int dense_sms = 0;    // CTAs of the dense GEMM (0: one per SM)
 
   std::string err;
   int device = 0;
@@ -299,10 +306,21 @@ void release(DevBuf& b) {
 
 void release_work(Work& w) {
   if (w.cs) cudaStreamSynchronize(w.cs);
+  if (w.cs2) cudaStreamSynchronize(w.cs2);
+  if (w.cs2) cudaStreamDestroy(w.cs2);
+  if (w.ev_fork) cudaEventDestroy(w.ev_fork);
+  if (w.ev_join) cudaEventDestroy(w.ev_join);
+  w.cs2 = nullptr;
+  w.ev_fork = w.ev_join = nullptr;
   for (DevBuf* b : w.all()) release(*b);
   if (w.h_tables) cudaFreeHost(w.h_tables);
   if (w.h_status) cudaFreeHost(w.h_status);
   if (w.h_io) cudaFreeHost(w.h_io);
+  if (w.h_out) cudaFreeHost(w.h_out);
+  for (cudaEvent_t& e : w.ev_out)
+    if (e) cudaEventDestroy(e), e = nullptr;
+  w.h_out = nullptr;
+  w.h_out_cap = 0;
   if (w.cs) cudaStreamDestroy(w.cs);
   w.h_tables = w.h_status = w.h_io = nullptr;
   w.cs = nullptr;
@@ -310,6 +328,9 @@ void release_work(Work& w) {
 
 int init_work(Work& w) {
   cudaError_t e = cudaStreamCreateWithFlags(&w.cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w.cs2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost(&w.h_status, 128);
   if (e != cudaSuccess) return wcuda(w, e, "work set-up");
   return GAKCO_OK;
@@ -329,6 +350,69 @@ int ensure_pinned(Work& w, void*& p, size_t& cap, size_t bytes, const char* what
   }
   cap = want;
   return GAKCO_OK;
+}
+
+struct Xfer {
+  void* dst;        // caller host buffer
+  const void* src;  // device
+  size_t bytes;
+};
+
+// Device results -> caller host buffers.  Large outputs go through two
+// pinned 32 MiB staging chunks: the copy engine fills one chunk while
+// several host threads move the previous one into the caller's (pageable)
+// memory, instead of the driver's own small bounce buffers.
+int copy_to_host(Work& w, const std::vector<Xfer>& xs) {
+  size_t total = 0;
+  for (const Xfer& x : xs) total += x.bytes;
+  cudaError_t e = cudaSuccess;
+  if (total < ((size_t)8 << 20)) {
+    for (const Xfer& x : xs)
+      if (x.bytes && e == cudaSuccess) e = cudaMemcpyAsync(x.dst, x.src, x.bytes, cudaMemcpyDeviceToHost, w.cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(w.cs);
+    return e == cudaSuccess ? GAKCO_OK : wcuda(w, e, "copy results to host");
+  }
+  constexpr size_t kChunk = (size_t)32 << 20;
+  int rc = ensure_pinned(w, w.h_out, w.h_out_cap, 2 * kChunk, "output staging");
+  if (rc != GAKCO_OK) return rc;
+  for (cudaEvent_t& ev : w.ev_out)
+    if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+      return wcuda(w, e, "output staging events");
+  struct Piece {
+    uint8_t* dst;
+    const uint8_t* src;
+    size_t n;
+  };
+  std::vector<Piece> ps;
+  for (const Xfer& x : xs)
+    for (size_t o = 0; o < x.bytes; o += kChunk)
+      ps.push_back({(uint8_t*)x.dst + o, (const uint8_t*)x.src + o, std::min(kChunk, x.bytes - o)});
+  uint8_t* stage = (uint8_t*)w.h_out;
+  auto issue = [&](size_t i) {
+    uint8_t* slot = stage + (i & 1) * kChunk;
+    cudaError_t r = cudaMemcpyAsync(slot, ps[i].src, ps[i].n, cudaMemcpyDeviceToHost, w.cs);
+    if (r == cudaSuccess) r = cudaEventRecord(w.ev_out[i & 1], w.cs);
+    return r;
+  };
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const unsigned nthr = std::min(8u, std::max(1u, hw / 2));
+  e = issue(0);
+  for (size_t i = 0; i < ps.size() && e == cudaSuccess; ++i) {
+    if (i + 1 < ps.size() && (e = issue(i + 1)) != cudaSuccess) break;
+    if ((e = cudaEventSynchronize(w.ev_out[i & 1])) != cudaSuccess) break;
+    const uint8_t* slot = stage + (i & 1) * kChunk;
+    uint8_t* dst = ps[i].dst;
+    const size_t n = ps[i].n, part = (n + nthr - 1) / nthr;
+    std::vector<std::thread> th;
+    for (unsigned t = 1; t < nthr; ++t) {
+      const size_t a = std::min(n, t * part), b = std::min(n, (t + 1) * part);
+      if (a < b) th.emplace_back([dst, slot, a, b] { memcpy(dst + a, slot + a, b - a); });
+    }
+    memcpy(dst, slot, std::min(n, part));
+    for (std::thread& t : th) t.join();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(w.cs);
+  return e == cudaSuccess ? GAKCO_OK : wcuda(w, e, "copy results to host");
 }
 
 void drop_graph(gakco_ctx* c) {
@@ -1001,8 +1085,18 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
   }
   AccParams a = acc_params(c, w, p, status + 8);
   if (!plain) {
-    for (const Chunk& ch : p.chunks) enqueue_chunk(c, w, p, ch, Tail::kGram);
     if (p.c_elems) cudaMemsetAsync(w.Cacc.p, 0, p.c_elems * 4, w.cs);
+    // Dense levels (tensor cores) and sparse levels (sort, run-length,
+    // on-chip accumulation) write disjoint levels of C and share only
+    // read-only inputs, so they run as two branches (except when profiling,
+    // where every launch is timed on one stream).
+    const bool fork = c->overlap && !c->profile && !p.dwaves.empty();
+    cudaStream_t ds = w.cs;
+    if (fork) {
+      cudaEventRecord(w.ev_fork, w.cs);
+      cudaStreamWaitEvent(w.cs2, w.ev_fork, 0);
+      ds = w.cs2;
+    }
     if (!p.dwaves.empty()) {
       // Dense levels: A = counts per (sequence, mask, key), C_m += A A^T.
       const DenseProb* probs = (const DenseProb*)(base + p.o_dprobs);
@@ -1010,26 +1104,31 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
       const size_t nmax_words = p.ds.size() * (size_t)(c->M + 1);
       uint32_t* ovf_n = (uint32_t*)w.dmaxc.p + nmax_words;
       const uint32_t cap = (uint32_t)c->dense_overflow;
-      cudaMemsetAsync(w.dmaxc.p, 0, nmax_words * 4, w.cs);
+      const int gemm_ctas = c->dense_sms > 0 ? std::min(c->dense_sms, c->nsm) : c->nsm;
+      cudaMemsetAsync(w.dmaxc.p, 0, nmax_words * 4, ds);
       for (const DenseWave& wv : p.dwaves) {
-        cudaMemsetAsync(ovf_n, 0, 4, w.cs);
+        cudaMemsetAsync(ovf_n, 0, 4, ds);
         {
           Bracket b(c, w, "dense_scatter", 1);
-          launch_dense_scatter(probs + wv.p0, wv.np, wv.p0, wv.rows, (const DsPack*)(base + p.o_pack), (const MaskDesc*)(base + p.o_masks),
-                               (const uint64_t*)w.fullkey.p, ovf_n, (DenseOvf*)w.dovf.p, cap, w.cs);
+          launch_dense_scatter(probs + wv.p0, wv.np, wv.p0, wv.rows, (const DsPack*)(base + p.o_pack),
+                               (const MaskDesc*)(base + p.o_masks), (const uint64_t*)w.fullkey.p, ovf_n,
+                               (DenseOvf*)w.dovf.p, cap, ds);
         }
         {
           Bracket b(c, w, "dense_gemm", 1);
-          launch_dense_gemm(probs, tiles + kDenseTileWords * (size_t)wv.t0, wv.nt, c->nsm, status, w.cs);
+          launch_dense_gemm(probs, tiles + kDenseTileWords * (size_t)wv.t0, wv.nt, gemm_ctas, status, ds);
         }
         Bracket b(c, w, "dense_fix", 1);
-        launch_dense_fix(probs, ovf_n, (const DenseOvf*)w.dovf.p, cap, status, w.cs);
+        launch_dense_fix(probs, ovf_n, (const DenseOvf*)w.dovf.p, cap, status, ds);
       }
     }
+    if (fork) cudaEventRecord(w.ev_join, w.cs2);
+    for (const Chunk& ch : p.chunks) enqueue_chunk(c, w, p, ch, Tail::kGram);
     {
       Bracket b(c, w, "accumulate", 1);
       launch_accum(a, c->accum_threads, p.acc_blocks, p.acc_smem, w.cs);
     }
+    if (fork) cudaStreamWaitEvent(w.cs, w.ev_join, 0);
     {
       Bracket b(c, w, "diag", 1);
       launch_diag((const DsInfo*)(base + p.o_info), (uint32_t)p.ds.size(), p.nseq, a, w.cs);
@@ -1069,9 +1168,9 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
 
 uint64_t plan_key(gakco_ctx* c, const Plan& p, bool plain) {
   uint64_t h = 1469598103934665603ull;
-  int64_t o[12] = {plain,           c->radix_bits, c->chunk_elems, c->accum_threads,  c->smem_cols,
+  int64_t o[14] = {plain,           c->radix_bits, c->chunk_elems, c->accum_threads,  c->smem_cols,
                    (int64_t)p.ds.size(), c->group_bytes, c->dense,    c->dense_bytes, c->dense_overflow,
-                   c->dense_run_cols, p.first_level};
+                   c->dense_run_cols, p.first_level, c->overlap, c->dense_sms};
   h = fnv1a(h, o, sizeof o);
   for (const DsHost& D : p.ds) {
     const void* ptrs[4] = {D.codes, D.K, D.Khat, D.Nm};
@@ -1272,18 +1371,16 @@ int gram_host(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64
   if (e != cudaSuccess) return wcuda(w, e, "copy codes to device");
   rc = run_gram(c, p, w.cs);
   if (rc != GAKCO_OK) return rc;
-  for (int32_t d = 0; d < nd && e == cudaSuccess; ++d) {
+  std::vector<Xfer> xs;
+  for (int32_t d = 0; d < nd; ++d) {
     const DsHost& D = p.ds[d];
     const size_t nn = (size_t)D.n * D.n;
-    if (K && K[d] && nn) e = cudaMemcpyAsync(K[d], D.K, nn * 4, cudaMemcpyDeviceToHost, w.cs);
-    if (e == cudaSuccess && Khat && Khat[d] && nn)
-      e = cudaMemcpyAsync(Khat[d], D.Khat, nn * 8, cudaMemcpyDeviceToHost, w.cs);
-    if (e == cudaSuccess && Nm && Nm[d] && nn)
-      e = cudaMemcpyAsync(Nm[d], D.Nm, (size_t)(c->M + 1) * nn * 4, cudaMemcpyDeviceToHost, w.cs);
+    if (!nn) continue;
+    if (K && K[d]) xs.push_back({K[d], D.K, nn * 4});
+    if (Khat && Khat[d]) xs.push_back({Khat[d], D.Khat, nn * 8});
+    if (Nm && Nm[d]) xs.push_back({Nm[d], D.Nm, (size_t)(c->M + 1) * nn * 4});
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(w.cs);
-  if (e != cudaSuccess) return wcuda(w, e, "copy results to host");
-  return GAKCO_OK;
+  return copy_to_host(w, xs);
 }
 
 // --------------------------------------------------------- training index --
@@ -1547,13 +1644,11 @@ int cross_host(gakco_ctx* c, const uint8_t* codes, const int64_t* off, int32_t n
                           Khat ? (double*)w.outKhat.p : nullptr, F ? (double*)w.outF.p : nullptr)) != GAKCO_OK)
     return rc;
   if ((rc = sync_and_check(c, w)) != GAKCO_OK) return rc;
-  if (K && nel) e = cudaMemcpyAsync(K, w.outK.p, nel * 4, cudaMemcpyDeviceToHost, w.cs);
-  if (e == cudaSuccess && Khat && nel)
-    e = cudaMemcpyAsync(Khat, w.outKhat.p, nel * 8, cudaMemcpyDeviceToHost, w.cs);
-  if (e == cudaSuccess && F) e = cudaMemcpyAsync(F, w.outF.p, (size_t)nt * 8, cudaMemcpyDeviceToHost, w.cs);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(w.cs);
-  if (e != cudaSuccess) return wcuda(w, e, "copy results to host");
-  return GAKCO_OK;
+  std::vector<Xfer> xs;
+  if (K && nel) xs.push_back({K, w.outK.p, nel * 4});
+  if (Khat && nel) xs.push_back({Khat, w.outKhat.p, nel * 8});
+  if (F) xs.push_back({F, w.outF.p, (size_t)nt * 8});
+  return copy_to_host(w, xs);
 }
 
 // ---------------------------------------------------------------- serving --
@@ -2082,6 +2177,14 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
     case GAKCO_OPT_DENSE_BYTES:
       if (v < 1) return fail(c, GAKCO_E_INVALID, "dense bytes must be >= 1");
       c->dense_bytes = v;
+      break;
+    case GAKCO_OPT_OVERLAP:
+      if (v != 0 && v != 1) return fail(c, GAKCO_E_INVALID, "overlap must be 0 or 1");
+      c->overlap = (int)v;
+      break;
+    case GAKCO_OPT_DENSE_SMS:
+      if (v < 0) return fail(c, GAKCO_E_INVALID, "dense SM count must be >= 0");
+      c->dense_sms = (int)v;
       break;
     case GAKCO_OPT_KERNEL_ONLY:
       if (v != 0 && v != 1) return fail(c, GAKCO_E_INVALID, "kernel-only must be 0 or 1");
