@@ -24,22 +24,35 @@ constexpr int kMaxRadixBits = 11;        // widest sort digit
 
 // How to cut the kept positions of one mask out of a packed g-mer key.
 // The full key holds symbol p of the window in bits
-// [b*(g-1-p), b*(g-p)); the masked key concatenates the kept symbols in
-// position order, so equal masked keys <=> equal (g-m)-mers.  Consecutive
-// kept positions form a run that moves with one shift and one mask.
+// [b*(g-1-p), b*(g-p)).  The masked key stands for the kept symbols in
+// position order, so equal masked keys <=> equal (g-m)-mers:
+//  - runs mode (fold == 0): the kept symbols' b-bit fields concatenated;
+//    consecutive kept positions form a run that moves with one shift and
+//    one mask;
+//  - fold mode (fold == sigma, used when sigma is not a power of two): the
+//    kept symbols as the digits of a base-sigma number, which needs
+//    ceil(log2(sigma^(g-m))) bits instead of b(g-m) (e.g. 6 protein or text
+//    symbols fit 32 bits).
 struct MaskDesc {
   uint32_t level;               // m = number of deleted positions
   uint32_t nruns;
-  uint32_t kbits;               // (g - m) * b
-  uint32_t pad;
+  uint32_t kbits;               // bits of the masked key
+  uint32_t fold;                // 0: runs mode; else the base (sigma)
   uint32_t sr[kMaxRuns];        // right shift of the run in the full key
   uint32_t sl[kMaxRuns];        // left shift of the run in the masked key
   uint64_t msk[kMaxRuns];       // run mask after the right shift
+  uint32_t nkeep;               // fold mode: kept positions
+  uint32_t symmask;             // fold mode: (1 << b) - 1
+  uint8_t ksh[64];              // fold mode: right shift of each kept symbol, in order
 };
 
 __device__ __forceinline__ uint64_t masked_key(uint64_t full,
                                                const MaskDesc& md) {
   uint64_t k = 0;
+  if (md.fold) {
+    for (uint32_t j = 0; j < md.nkeep; ++j) k = k * md.fold + ((full >> md.ksh[j]) & md.symmask);
+    return k;
+  }
   for (uint32_t r = 0; r < md.nruns; ++r)
     k |= ((full >> md.sr[r]) & md.msk[r]) << md.sl[r];
   return k;

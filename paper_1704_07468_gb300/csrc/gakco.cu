@@ -179,6 +179,7 @@ struct gakco_ctx {
   int sigma = 0, g = 0, k = 0, M = 0, bits = 0;
   std::vector<MaskDesc> masks;
   std::vector<uint32_t> mask_level;
+  int lkbits[kMaxLevels] = {};  // masked-key bits of each level
   uint32_t h[kMaxLevels] = {};
   uint32_t ie[kMaxLevels][kMaxLevels] = {};
   uint32_t maxC = 0;  // max_m C(g, m), m <= M
@@ -573,7 +574,7 @@ void plan_chunks(gakco_ctx* c, Plan& p, bool plain) {
   p.sort_bytes = 0;
   const uint64_t limit = plain ? 0 : (uint64_t)std::max<int64_t>(c->chunk_elems, kTile);
   for (int m = p.first_level; m <= c->M; ++m) {
-    const int kb = (c->g - m) * c->bits;
+    const int kb = c->lkbits[m];
     const int np = (kb + c->radix_bits - 1) / c->radix_bits;
     const int rb = (kb + np - 1) / np;
     std::vector<std::pair<int, int>> passes;
@@ -739,7 +740,7 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
     if (D.n == 0 || D.G == 0) continue;
     const uint32_t n_pad = (uint32_t)align_up((size_t)D.n, 128);
     for (int m = p.first_level; m <= c->M; ++m) {
-      const int kb = c->bits * (c->g - m);
+      const int kb = c->lkbits[m];
       if (kb > 16) continue;
       const uint64_t S = (uint64_t)1 << kb;
       const uint64_t per_mask = (uint64_t)n_pad * S;
@@ -2034,6 +2035,18 @@ int gakco_create(int sigma, int g, int k, gakco_ctx** out) {
   c->bits = bits;
   // Masks in level order; within a level, deleted position sets in
   // lexicographic order (Alg. 1: for m, for i < C(g, m)).
+  // A non-power-of-two alphabet folds the kept symbols in base sigma (see
+  // MaskDesc): ceil(log2(sigma^(g-m))) key bits.
+  const bool pow2 = (sigma & (sigma - 1)) == 0;
+  for (int m = 0; m <= M; ++m) {
+    int kw = (g - m) * bits;
+    if (!pow2) {
+      uint64_t v = 1;
+      for (int i = 0; i < g - m; ++i) v *= (uint64_t)sigma;  // < 2^(bits (g-m)) <= 2^64
+      kw = v > 1 ? 64 - __builtin_clzll(v - 1) : 1;
+    }
+    c->lkbits[m] = kw;
+  }
   for (int m = 0; m <= M; ++m) {
     std::vector<int> del(m);
     for (int i = 0; i < m; ++i) del[i] = i;
@@ -2047,8 +2060,14 @@ int gakco_create(int sigma, int g, int k, gakco_ctx** out) {
       }
       MaskDesc md{};
       md.level = (uint32_t)m;
-      md.kbits = (uint32_t)((g - m) * bits);
+      md.kbits = (uint32_t)c->lkbits[m];
       const int nk = (int)keep.size();
+      if (!pow2) {
+        md.fold = (uint32_t)sigma;
+        md.nkeep = (uint32_t)nk;
+        md.symmask = (1u << bits) - 1;
+        for (int j = 0; j < nk; ++j) md.ksh[j] = (uint8_t)(bits * (g - 1 - keep[j]));
+      }
       for (int i = 0; i < nk;) {
         int j = i;
         while (j + 1 < nk && keep[j + 1] == keep[j] + 1) ++j;

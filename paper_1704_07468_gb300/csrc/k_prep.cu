@@ -100,7 +100,7 @@ struct MaskRegs {
 };
 
 __device__ __forceinline__ void mask_regs(const MaskDesc& md, MaskRegs& r) {
-  r.fits = md.nruns <= (uint32_t)kRegRuns;
+  r.fits = md.fold == 0 && md.nruns <= (uint32_t)kRegRuns;
 #pragma unroll
   for (int i = 0; i < kRegRuns; ++i) {
     const bool on = (uint32_t)i < md.nruns;
