@@ -199,6 +199,18 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes (read + write) per unit of work from one ncu capture of the
+# same kernels on a smaller case (the DNA N = 4000 dataset, see
+# profiles/dense_scatter_gemm_accum_dna_4000.md), scaled to a launch of the
+# bench by its units; traffic grows in proportion to them.
+NCU_BYTES_PER_UNIT = {
+    "accumulate": (4.426e9 / 3.16e9, "pair update"),
+    "dense_gemm": (5.644e9 / 1.19e13, "flop"),
+    "dense_scatter": (3.504e9 / 3.46e9, "byte of A"),
+}
+NCU_SOURCE = "profiles/dense_scatter_gemm_accum_dna_4000.md (scaled by units)"
+
+
 def kernel_rooflines(timings, work, peaks, sm_count):
     """Roofline entry per timed stage with a known algorithmic work figure.
 
@@ -240,6 +252,12 @@ def kernel_rooflines(timings, work, peaks, sm_count):
             continue
         e["frac"] = e["achieved"] / e["peak"]
         e["traffic"] = None
+        units = {"accumulate": work["pairs"], "dense_gemm": work["dense_flops"],
+                 "dense_scatter": work["dense_bytes"]}.get(name)
+        if name in NCU_BYTES_PER_UNIT and units:
+            per, unit = NCU_BYTES_PER_UNIT[name]
+            e["traffic"] = per * units / n          # bytes per launch
+            e["traffic_source"] = f"{NCU_SOURCE}: {per:.4g} B per {unit}"
         e["launch_ms"] = ms / n
         e["launches"] = n
         out[name] = e
