@@ -20,6 +20,7 @@ constexpr int kMaxLevels = 16;            // M + 1 <= kMaxLevels
 constexpr int kSortThreads = 256;         // threads of the sort / RLE blocks
 constexpr int kSortIpt = 16;              // items per thread
 constexpr int kTile = kSortThreads * kSortIpt;  // elements per tile
+constexpr uint32_t kRecWords = 8;          // words of a run-length tile record
 constexpr int kMaxRadixBits = 11;        // widest sort digit
 
 // How to cut the kept positions of one mask out of a packed g-mer key.

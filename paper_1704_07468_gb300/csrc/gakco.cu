@@ -106,7 +106,7 @@ struct Work {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   DevBuf fullkey, wid, ewin, eseq, efe, keyA, keyB, valA, valB, hist, tcnt, segtot, estart,
       etseq, efid, fstart, tables, codes, outK, outKhat, outNm, rinv, status, Cplain, Cacc, ea, eb,
-      Cd, Cx, Adense, dmaxc, dovf, outF;
+      Cd, Cx, Adense, dmaxc, dovf, outF, trec;
   void* h_tables = nullptr;
   size_t h_tables_cap = 0;
   void* h_status = nullptr;
@@ -124,7 +124,7 @@ struct Work {
     return {&fullkey, &wid, &ewin,   &eseq,  &efe,  &keyA,  &keyB,  &valA,    &valB,
             &hist,    &tcnt,    &segtot, &estart, &etseq, &efid, &fstart, &tables, &codes,
             &outK,    &outKhat, &outNm,  &rinv,  &status, &Cplain, &Cacc, &ea,    &eb,
-            &Cd,      &Cx,      &Adense, &dmaxc,  &dovf,  &outF};
+            &Cd,      &Cx,      &Adense, &dmaxc,  &dovf,  &outF, &trec};
   }
   size_t bytes() {
     size_t s = 0;
@@ -876,6 +876,7 @@ int ensure_sort_buffers(gakco_ctx* c, Work& w, const Plan& p) {
   ENSURE(valB, ce * 4);
   ENSURE(hist, p.max_hist * 4);
   ENSURE(tcnt, p.max_chunk_tiles * 8);
+  ENSURE(trec, p.max_chunk_tiles * kRecWords * 4);
   ENSURE(segtot, p.max_chunk_nseg * 8);
   const uint64_t te = ce + p.max_chunk_nseg + 1;
   ENSURE(estart, te * 4);
@@ -1054,6 +1055,13 @@ void enqueue_chunk(gakco_ctx* c, Work& w, const Plan& p, const Chunk& ch, Tail t
     kin = kbuf[cur];
     vin = vbuf[cur];
     cur ^= 1;
+  }
+  if (tail == Tail::kGram) {
+    Bracket b(c, w, "run_length", 4);
+    launch_rle_gram(ch.wide, segs, ch.nseg, tseg, ch.ntiles, kin, vin, (const DsPack*)(base + p.o_pack),
+                    (uint32_t*)w.tcnt.p, (uint32_t*)w.segtot.p, (uint32_t*)w.trec.p, (uint32_t*)w.ewin.p,
+                    (uint32_t*)w.eseq.p, (uint32_t*)w.efe.p, w.cs);
+    return;
   }
   Bracket b(c, w, "run_length", tail == Tail::kFit ? 5 : 4);
   launch_rle_head(ch.wide, segs, ch.nseg, tseg, ch.ntiles, kin, vin, (const DsPack*)(base + p.o_pack),

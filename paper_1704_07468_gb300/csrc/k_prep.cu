@@ -184,6 +184,49 @@ k_seg_scan(const SegDesc* __restrict__ segs, uint32_t* __restrict__ hist,
   }
 }
 
+// Lanes of the warp holding the same digit as this lane: a warp multisplit
+// by bit-sliced ballots (Ashkiani et al., "GPU Multisplit", PPoPP 2016), one
+// ballot per digit bit plus one for validity, so that invalid lanes never
+// join a valid lane's group.  kBits may exceed the digit width (the extra
+// bits are zero in every lane).  On sm_103a this runs on the integer pipe;
+// match.any, its one-instruction alternative, saturated a much narrower
+// pipe and was slower.
+template <int kBits>
+__device__ __forceinline__ uint32_t digit_peers(uint32_t dg, bool valid) {
+  const uint32_t vb = __ballot_sync(0xffffffffu, valid);
+  uint32_t peers = valid ? vb : ~vb;
+#pragma unroll
+  for (int b = 0; b < kBits; ++b) {
+    const bool bit = (dg >> b) & 1u;
+    const uint32_t v = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? v : ~v;
+  }
+  return peers;
+}
+
+// Rank of each item of a warp among the warp's items with the same digit,
+// in element order: the group's leader reserves slots of the warp's running
+// count for the digit with an atomic add, and the shuffle of its result is
+// the convergence point that orders consecutive items.
+template <int kBits, typename KeyT>
+__device__ __forceinline__ void rank_items(const KeyT (&keys)[kSortIpt], uint32_t (&rk)[kSortIpt],
+                                           uint32_t cnt, int w, int lane, int shift,
+                                           uint32_t radix, uint32_t* wc) {
+  const uint32_t lt_mask = lanemask_lt();
+#pragma unroll
+  for (int j = 0; j < kSortIpt; ++j) {
+    const uint32_t idx = (uint32_t)w * 32 * kSortIpt + j * 32 + lane;
+    const bool valid = idx < cnt;
+    const uint32_t dg = valid ? ((uint32_t)(keys[j] >> shift) & (radix - 1)) : 0u;
+    const uint32_t peers = digit_peers<kBits>(dg, valid);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(&wc[w * radix + dg], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    rk[j] = base + __popc(peers & lt_mask);
+  }
+}
+
 // Shared-memory footprint of the scatter kernel for a digit width.
 __host__ __device__ constexpr size_t downsweep_smem(int rbits, int key_bytes) {
   return ((size_t)(kWarps + 2) << rbits) * 4 + (size_t)kTile * (key_bytes + 4);
@@ -191,10 +234,7 @@ __host__ __device__ constexpr size_t downsweep_smem(int rbits, int key_bytes) {
 
 // Stable scatter of one tile.  Warp w owns elements [w*32*IPT, (w+1)*32*IPT)
 // and visits them as j*32 + lane, so the visiting order is the element
-// order.  Elements with the same digit are ranked with match.any: the
-// group's leader reserves slots of the warp's running count for the digit
-// with an atomic add, and the shuffle of its result is the convergence
-// point that orders consecutive items.  The tile is then laid out in digit
+// order, and ranked within the warp by `rank_items`.  The tile is then laid out in digit
 // order in shared memory and written out with consecutive threads on
 // consecutive addresses of each digit's run.
 // Resident blocks per SM: four for 32-bit keys, three for 64-bit keys
@@ -223,7 +263,6 @@ k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint64_t beg = (uint64_t)lt * kTile;
   const uint32_t cnt = (uint32_t)min((uint64_t)kTile, sd.G - beg);
-  const uint32_t lt_mask = lanemask_lt();
   KeyT keys[kSortIpt];
   uint32_t vals[kSortIpt];
   uint32_t rk[kSortIpt];
@@ -233,18 +272,13 @@ k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
     keys[j] = idx < cnt ? kin[sd.base + beg + idx] : (KeyT)0;
     vals[j] = idx < cnt ? (kFirst ? vin[sd.win0 + beg + idx] : vin[sd.base + beg + idx]) : 0u;
   }
-#pragma unroll
-  for (int j = 0; j < kSortIpt; ++j) {
-    const uint32_t idx = (uint32_t)w * 32 * kSortIpt + j * 32 + lane;
-    const bool valid = idx < cnt;
-    const uint32_t dg = valid ? ((uint32_t)(keys[j] >> shift) & (radix - 1)) : radix;
-    const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-    const int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (valid && lane == leader) base = atomicAdd(&wc[w * radix + dg], (uint32_t)__popc(peers));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    rk[j] = base + __popc(peers & lt_mask);
-  }
+  // Ballots for 7, 8 or all digit bits (the digit width is uniform per launch).
+  if (rbits <= 7)
+    rank_items<7>(keys, rk, cnt, w, lane, shift, radix, wc);
+  else if (rbits == 8)
+    rank_items<8>(keys, rk, cnt, w, lane, shift, radix, wc);
+  else
+    rank_items<kMaxRadixBits>(keys, rk, cnt, w, lane, shift, radix, wc);
   __syncthreads();
   // Per digit: exclusive prefix over warps, and the digit's tile total.
   const uint32_t per = (radix + kSortThreads - 1) / kSortThreads;
@@ -504,6 +538,173 @@ k_rle_final(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
   }
 }
 
+// Gram-engine variant of k_rle_emit + k_rle_final: writes ewin and the
+// packed entries directly.  For an entry e starting at element i:
+//   eseq[e] = (sequence << 16) | count, count = (next entry start) - i;
+//   efe[e]  = first entry of the next feature.
+// Both "next" starts are found by a backward pass over the tile's items
+// (ballots within a warp, per-warp summaries across warps).  The last entry
+// of a tile, and the entries of the tile's last feature, may end in a later
+// tile: their count is left 0 / their efe unwritten, and the tile's record
+// trec[t * kRecWords ..] = {first entry element, last entry element, its
+// entry, first feature's entry, last feature's entry} (tile-local element
+// indices, kNone where absent) lets k_rle_fix complete them.
+template <typename KeyT>
+__global__ void __launch_bounds__(kSortThreads, 3)
+k_rle_emit_gram(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg,
+                const KeyT* __restrict__ keys, const uint32_t* __restrict__ vals,
+                const DsPack* __restrict__ dsp, const uint32_t* __restrict__ tcnt,
+                uint32_t* __restrict__ trec, uint32_t* __restrict__ ewin,
+                uint32_t* __restrict__ eseq, uint32_t* __restrict__ efe) {
+  // Per warp: entries, first / last entry element (warp-local), and the
+  // number of the warp's entries before its first / last feature start.
+  __shared__ uint32_t swe[kWarps], sfe[kWarps], sle[kWarps], sff[kWarps], slf[kWarps];
+  const uint32_t t = blockIdx.x;
+  const uint32_t s = tile_seg[t];
+  const SegDesc sd = segs[s];
+  const uint32_t lt = t - sd.tile0;
+  const uint64_t beg = (uint64_t)lt * kTile;
+  const uint32_t cnt = (uint32_t)min((uint64_t)kTile, sd.G - beg);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t lt_mask = lanemask_lt();
+  const uint32_t gt_mask = lane == 31 ? 0u : (0xFFFFFFFFu << (lane + 1));
+  const uint32_t* __restrict__ woff = dsp[sd.ds].woff;
+  uint32_t vv[kSortIpt], sq[kSortIpt], ne_bits, nf_bits;
+  rle_load_flags<KeyT>(sd, beg, cnt, w, lane, keys, vals, vv, sq, ne_bits, nf_bits);
+  {
+    uint32_t nen = 0, fe = kNone, le = kNone, ff = kNone, lf = kNone;
+#pragma unroll
+    for (int j = 0; j < kSortIpt; ++j) {
+      const uint32_t be = __ballot_sync(0xffffffffu, (ne_bits >> j) & 1u);
+      const uint32_t bf = __ballot_sync(0xffffffffu, (nf_bits >> j) & 1u);
+      if (be) {
+        if (fe == kNone) fe = j * 32 + __ffs(be) - 1;
+        le = j * 32 + 31 - __clz(be);
+      }
+      if (bf) {
+        const uint32_t l0 = __ffs(bf) - 1, l1 = 31 - __clz(bf);
+        if (ff == kNone) ff = nen + __popc(be & ((1u << l0) - 1u));
+        lf = nen + __popc(be & ((1u << l1) - 1u));
+      }
+      nen += __popc(be);
+    }
+    if (lane == 0) {
+      swe[w] = nen;
+      sfe[w] = fe;
+      sle[w] = le;
+      sff[w] = ff;
+      slf[w] = lf;
+    }
+  }
+  __syncthreads();
+  constexpr uint32_t kWarpElems = 32 * kSortIpt;
+  const uint32_t e0 = tcnt[2 * (uint64_t)t];  // entries of the segment before this tile
+  uint32_t re = e0;                           // entries before warp w
+  for (int i = 0; i < w; ++i) re += swe[i];
+  // First entry element (tile-local) and first feature start (entry index)
+  // after warp w.
+  uint32_t cne = kNone, cnf = kNone;
+  {
+    uint32_t r = re + swe[w];
+    for (int i = w + 1; i < kWarps; ++i) {
+      if (cne == kNone && sfe[i] != kNone) cne = i * kWarpElems + sfe[i];
+      if (cnf == kNone && sff[i] != kNone) cnf = r + sff[i];
+      r += swe[i];
+    }
+  }
+  if (threadIdx.x == 0) {
+    uint32_t r = e0, fe = kNone, le = kNone, le_e = kNone, ff = kNone, lf = kNone;
+    for (int i = 0; i < kWarps; ++i) {
+      if (sfe[i] != kNone) {
+        if (fe == kNone) fe = i * kWarpElems + sfe[i];
+        le = i * kWarpElems + sle[i];
+        le_e = r + swe[i] - 1;
+      }
+      if (sff[i] != kNone) {
+        if (ff == kNone) ff = r + sff[i];
+        lf = r + slf[i];
+      }
+      r += swe[i];
+    }
+    uint32_t* rec = trec + (uint64_t)t * kRecWords;
+    rec[0] = fe;
+    rec[1] = le;
+    rec[2] = le_e;
+    rec[3] = ff;
+    rec[4] = lf;
+  }
+  re += swe[w];  // entries before the item after the current one (walking back)
+#pragma unroll
+  for (int j = kSortIpt - 1; j >= 0; --j) {
+    const bool ne = (ne_bits >> j) & 1u, nf = (nf_bits >> j) & 1u;
+    const uint32_t be = __ballot_sync(0xffffffffu, ne);
+    const uint32_t bf = __ballot_sync(0xffffffffu, nf);
+    re -= __popc(be);  // entries before item j
+    const uint32_t item0 = (uint32_t)w * kWarpElems + j * 32;
+    const uint32_t idx = item0 + lane;
+    if (idx < cnt) {
+      const uint32_t e = re + __popc(be & lt_mask);
+      if (ne) {
+        const uint32_t hb = be & gt_mask;
+        const uint32_t nxt = hb ? item0 + __ffs(hb) - 1 : cne;
+        eseq[sd.pool + e] = (sq[j] << 16) | (nxt == kNone ? 0u : nxt - idx);
+        const uint32_t hf = bf & gt_mask;
+        const uint32_t fend = hf ? re + __popc(be & ((1u << (__ffs(hf) - 1)) - 1u)) : cnf;
+        if (fend != kNone) efe[sd.pool + e] = fend;
+      }
+      ewin[sd.pool + woff[vv[j] >> 16] + (vv[j] & 0xFFFFu)] = ne ? e : kNone;
+    }
+    if (be) cne = item0 + __ffs(be) - 1;
+    if (bf) cnf = re + __popc(be & ((1u << (__ffs(bf) - 1)) - 1u));
+  }
+}
+
+// Completes what k_rle_emit_gram left open at tile ends: one warp per
+// tile.  The tile's last entry runs to the first entry element of a later
+// tile of the segment (else to the segment's end); the entries of its last
+// feature, up to the first feature start of a later tile (else the
+// segment's entry count), get that start as their feature end.
+__global__ void __launch_bounds__(256)
+k_rle_fix(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg, uint32_t ntiles,
+          const uint32_t* __restrict__ segtot, const uint32_t* __restrict__ trec,
+          uint32_t* __restrict__ eseq, uint32_t* __restrict__ efe) {
+  const uint32_t t = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= ntiles) return;
+  const uint32_t s = tile_seg[t];
+  const SegDesc sd = segs[s];
+  const uint32_t tend = sd.tile0 + sd.ntiles;
+  const uint32_t* rec = trec + (uint64_t)t * kRecWords;
+  const uint32_t le = rec[1], le_e = rec[2], lf = rec[4];
+  if (le != kNone) {
+    uint32_t end = sd.G;
+    for (uint32_t u0 = t + 1; u0 < tend; u0 += 32) {
+      const uint32_t u = u0 + lane;
+      const uint32_t f = u < tend ? trec[(uint64_t)u * kRecWords] : kNone;
+      const uint32_t b = __ballot_sync(0xffffffffu, f != kNone);
+      if (b) {
+        const uint32_t L = __ffs(b) - 1;
+        end = (u0 + L - sd.tile0) * (uint32_t)kTile + __shfl_sync(0xffffffffu, f, L);
+        break;
+      }
+    }
+    if (lane == 0) eseq[sd.pool + le_e] += end - ((t - sd.tile0) * (uint32_t)kTile + le);
+  }
+  if (lf != kNone) {
+    uint32_t fend = segtot[2 * (uint64_t)s];
+    for (uint32_t u0 = t + 1; u0 < tend; u0 += 32) {
+      const uint32_t u = u0 + lane;
+      const uint32_t f = u < tend ? trec[(uint64_t)u * kRecWords + 3] : kNone;
+      const uint32_t b = __ballot_sync(0xffffffffu, f != kNone);
+      if (b) {
+        fend = __shfl_sync(0xffffffffu, f, __ffs(b) - 1);
+        break;
+      }
+    }
+    for (uint32_t e = lf + lane; e < fend; e += 32) efe[sd.pool + e] = fend;
+  }
+}
+
 template <typename KeyT>
 void sort_pass_t(bool first, const SegDesc* segs, uint32_t nsegs,
                  const uint32_t* tile_seg, uint32_t ntiles,
@@ -542,6 +743,19 @@ void rle_head_t(const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg,
   k_rle_scan<<<nsegs, kSortThreads, 0, st>>>(segs, tcnt, segtot);
   k_rle_emit<KeyT><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, k, vals, dsp, tcnt,
                                                     estart, etseq, efid, fstart, ewin);
+}
+
+template <typename KeyT>
+void rle_gram_t(const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg, uint32_t ntiles,
+                const void* keys, const uint32_t* vals, const DsPack* dsp, uint32_t* tcnt,
+                uint32_t* segtot, uint32_t* trec, uint32_t* ewin, uint32_t* eseq, uint32_t* efe,
+                cudaStream_t st) {
+  const KeyT* k = (const KeyT*)keys;
+  k_rle_count<KeyT><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, k, vals, tcnt);
+  k_rle_scan<<<nsegs, kSortThreads, 0, st>>>(segs, tcnt, segtot);
+  k_rle_emit_gram<KeyT><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, k, vals, dsp, tcnt, trec,
+                                                         ewin, eseq, efe);
+  k_rle_fix<<<(ntiles + 7) / 8, 256, 0, st>>>(segs, tile_seg, ntiles, segtot, trec, eseq, efe);
 }
 
 }  // namespace
@@ -591,6 +805,19 @@ void launch_rle_head(bool wide, const SegDesc* segs, uint32_t nsegs,
   else
     rle_head_t<uint32_t>(segs, nsegs, tile_seg, ntiles, keys, vals, dsp, tcnt, segtot, estart,
                          etseq, efid, fstart, ewin, st);
+}
+
+void launch_rle_gram(bool wide, const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg,
+                     uint32_t ntiles, const void* keys, const uint32_t* vals, const DsPack* dsp,
+                     uint32_t* tcnt, uint32_t* segtot, uint32_t* trec, uint32_t* ewin,
+                     uint32_t* eseq, uint32_t* efe, cudaStream_t st) {
+  if (ntiles == 0) return;
+  if (wide)
+    rle_gram_t<uint64_t>(segs, nsegs, tile_seg, ntiles, keys, vals, dsp, tcnt, segtot, trec, ewin,
+                         eseq, efe, st);
+  else
+    rle_gram_t<uint32_t>(segs, nsegs, tile_seg, ntiles, keys, vals, dsp, tcnt, segtot, trec, ewin,
+                         eseq, efe, st);
 }
 
 void launch_rle_final(const SegDesc* segs, const uint32_t* tile_seg, uint32_t ntiles,

@@ -93,6 +93,12 @@ void launch_rle_head(bool wide, const SegDesc* segs, uint32_t nsegs,
                      uint32_t* tcnt, uint32_t* segtot, uint32_t* estart,
                      uint32_t* etseq, uint32_t* efid, uint32_t* fstart,
                      uint32_t* ewin, cudaStream_t st);
+// Gram engine: count/scan, then ewin, eseq and efe written directly, and
+// the tile-end fix-up; trec holds kRecWords words per tile.
+void launch_rle_gram(bool wide, const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg,
+                     uint32_t ntiles, const void* keys, const uint32_t* vals, const DsPack* dsp,
+                     uint32_t* tcnt, uint32_t* segtot, uint32_t* trec, uint32_t* ewin,
+                     uint32_t* eseq, uint32_t* efe, cudaStream_t st);
 void launch_rle_final(const SegDesc* segs, const uint32_t* tile_seg, uint32_t ntiles,
                       const uint32_t* segtot, const uint32_t* estart,
                       const uint32_t* etseq, const uint32_t* efid,
