@@ -137,6 +137,21 @@ const char *gakco_last_error(const gakco_ctx *ctx);
 #define GAKCO_OPT_OVERLAP 19        /* 1 (default): a Gram call runs its dense levels and its
                                        sparse levels as two concurrent branches */
 #define GAKCO_OPT_DENSE_SMS 20      /* CTAs of the dense GEMM (0 = one per SM, default) */
+/* Heavy features (batched Gram engine, sparse levels).  A feature held by L
+ * sequences costs about L^2 / 2 pair updates in the on-chip accumulation,
+ * one column (n^2 multiply-adds) in a tensor-core contraction.  After a
+ * sparse level's run-length pass, every feature with at least
+ * T = ceil(GAKCO_OPT_HEAVY * n / 1000) entries (n = sequences of the
+ * dataset, T >= 8, datasets of at least 256 sequences) whose counts are
+ * all <= 16 becomes a column of an e4m3 count matrix A of its (dataset,
+ * level), and C_m += A A^T runs on the tensor cores beside the
+ * accumulation of the remaining features.  Results are identical.
+ * GAKCO_OPT_HEAVY: threshold in thousandths (0 = off, the default; 20 to
+ * 50 suits strongly skewed inputs).
+ * GAKCO_OPT_HEAVY_BYTES: device bytes of those matrices (default 4 GiB,
+ * at most 1/16 of the device); features beyond it stay sparse. */
+#define GAKCO_OPT_HEAVY 21
+#define GAKCO_OPT_HEAVY_BYTES 22
 int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 
 /*
@@ -164,6 +179,8 @@ int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 #define GAKCO_STAT_DENSE_BYTES 13     /* Gram: bytes of the dense count matrices written */
 #define GAKCO_STAT_SORT_BYTES 14      /* Gram: algorithmic bytes of every sort pass (keys and
                                          payloads read and written once per pass) */
+#define GAKCO_STAT_HEAVY_COLUMNS 15   /* Gram: heavy features moved to the tensor cores */
+#define GAKCO_STAT_HEAVY_FLOPS 16     /* Gram: flops of their contractions' upper triangles */
 int gakco_get_stat(const gakco_ctx *ctx, int key, double *value);
 
 /*

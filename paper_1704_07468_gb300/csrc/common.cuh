@@ -15,6 +15,10 @@
 namespace gk {
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;   // "no entry" marker
+// Window slot of a feature held by one sequence: kSingleTag | count (entry
+// indices stay below 2^31, kNone has bits 16..30 set).
+constexpr uint32_t kSingleTag = 0x80000000u;
+__host__ __device__ constexpr bool is_single(uint32_t v) { return (v >> 16) == (kSingleTag >> 16); }
 constexpr int kMaxRuns = 16;              // kept-position runs per mask
 constexpr int kMaxLevels = 16;            // M + 1 <= kMaxLevels
 constexpr int kSortThreads = 256;         // threads of the sort / RLE blocks

@@ -103,10 +103,10 @@ double now_ms() {
 struct Work {
   cudaStream_t cs = nullptr;
   cudaStream_t cs2 = nullptr;                      // second branch of a Gram call
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_heavy = nullptr;
   DevBuf fullkey, wid, ewin, eseq, efe, keyA, keyB, valA, valB, hist, tcnt, segtot, estart,
       etseq, efid, fstart, tables, codes, outK, outKhat, outNm, rinv, status, Cplain, Cacc, ea, eb,
-      Cd, Cx, Adense, dmaxc, dovf, outF, trec;
+      Cd, Cx, Adense, dmaxc, dovf, outF, trec, Aheavy, hctr, hlist;
   void* h_tables = nullptr;
   size_t h_tables_cap = 0;
   void* h_status = nullptr;
@@ -119,12 +119,13 @@ struct Work {
   bool dense_overflow = false;  // the last run's dense overflow list ran out of room
   std::string err;
   double pairs = 0, entries = 0, windows = 0;
+  double heavy_cols = 0, heavy_flops = 0;  // heavy-feature columns and their GEMM flops
 
   std::vector<DevBuf*> all() {
     return {&fullkey, &wid, &ewin,   &eseq,  &efe,  &keyA,  &keyB,  &valA,    &valB,
             &hist,    &tcnt,    &segtot, &estart, &etseq, &efid, &fstart, &tables, &codes,
             &outK,    &outKhat, &outNm,  &rinv,  &status, &Cplain, &Cacc, &ea,    &eb,
-            &Cd,      &Cx,      &Adense, &dmaxc,  &dovf,  &outF, &trec};
+            &Cd,      &Cx,      &Adense, &dmaxc,  &dovf,  &outF, &trec, &Aheavy, &hctr, &hlist};
   }
   size_t bytes() {
     size_t s = 0;
@@ -208,6 +209,11 @@ struct gakco_ctx {
   int kernel_only = 0;  // 1: compute level M alone when N_m is not requested (K = C_M)
   int overlap = 1;      // 1: dense and sparse levels of a Gram call run on two streams
   int dense_sms = 0;    // CTAs of the dense GEMM (0: one per SM)
+  // Heavy features of sparse levels go to the tensor cores: threshold on a
+  // feature's entries in thousandths of the dataset's sequences (0: off),
+  // and the bytes of their count matrices (capped at create).
+  int heavy = 0;
+  int64_t heavy_bytes = (int64_t)4 << 30;
 
   std::string err;
   int device = 0;
@@ -222,6 +228,7 @@ struct gakco_ctx {
   int64_t last_launches = 0, last_mask_passes = 0;
   int last_replay = 0;
   double last_pairs = 0, last_entries = 0, last_windows = 0;
+  double last_heavy_cols = 0, last_heavy_flops = 0;
   // Work figures of the last plan (kept for graph replays).
   double plan_dense_probs = 0, plan_dense_flops = 0, plan_dense_issued = 0, plan_dense_bytes = 0,
          plan_sort_bytes = 0;
@@ -311,8 +318,9 @@ void release_work(Work& w) {
   if (w.cs2) cudaStreamDestroy(w.cs2);
   if (w.ev_fork) cudaEventDestroy(w.ev_fork);
   if (w.ev_join) cudaEventDestroy(w.ev_join);
+  if (w.ev_heavy) cudaEventDestroy(w.ev_heavy);
   w.cs2 = nullptr;
-  w.ev_fork = w.ev_join = nullptr;
+  w.ev_fork = w.ev_join = w.ev_heavy = nullptr;
   for (DevBuf* b : w.all()) release(*b);
   if (w.h_tables) cudaFreeHost(w.h_tables);
   if (w.h_status) cudaFreeHost(w.h_status);
@@ -332,6 +340,7 @@ int init_work(Work& w) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w.cs2, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev_heavy, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost(&w.h_status, 128);
   if (e != cudaSuccess) return wcuda(w, e, "work set-up");
   return GAKCO_OK;
@@ -456,6 +465,15 @@ struct Bracket {
 struct DenseHost {
   uint32_t ds, level, mfirst, mcount, n, n_pad, key_bits, row0;
   uint64_t ld, a_off;  // columns; byte offset of A in the A buffer
+  uint32_t hidx = 0;   // heavy problem index (when heavy)
+  bool heavy = false;  // heavy-feature matrix: ld is its column capacity, the
+                       // columns in use are set on the device
+};
+
+// A heavy-feature problem of one sparse (dataset, level).
+struct HeavyHost {
+  uint32_t ds, level, n, n_pad, T, prob;
+  uint64_t cap, a_off;  // columns (= row stride); byte offset in the heavy A buffer
 };
 
 struct DenseWave {
@@ -496,6 +514,14 @@ struct Plan {
   std::vector<DenseWave> dwaves;
   std::vector<uint32_t> dtiles;
   uint64_t dense_abytes = 0;
+  // Heavy features: problems, (dataset, level) -> problem map, GEMM tiles
+  // [heavy_t0, heavy_t0 + heavy_nt) of dtiles.
+  std::vector<HeavyHost> heavy;
+  std::vector<uint32_t> hmap;
+  std::vector<uint8_t> heavy_level;  // levels with a heavy problem
+  uint32_t heavy_t0 = 0, heavy_nt = 0, heavy_rows = 0;
+  uint64_t heavy_abytes = 0, heavy_list = 0;
+  size_t o_hprobs = 0, o_hmap = 0;
   double dense_flops = 0;         // upper triangle of A A^T, unpadded: 2 mcount S n(n+1)/2 per problem
   double dense_issued = 0;        // what the 128 x 256 tiles issue, padding included
   double dense_bytes = 0;         // A written by the scatter
@@ -831,6 +857,99 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
   close();
 }
 
+constexpr uint32_t kHeavyMinSeqs = 256;  // smaller datasets keep every feature sparse
+constexpr uint32_t kHeavyMinT = 8;       // smallest entry threshold
+
+// Heavy features (see HeavyProb): one problem per sparse (dataset, level)
+// of a dataset with at least kHeavyMinSeqs sequences.  Its column capacity
+// is a share of the byte budget in proportion to the most heavy features
+// the level can hold (masks x windows / T), at most that number; its GEMM
+// macro tiles follow the regular dense tiles, largest problems first.  A
+// feature of the dataset is heavy when it has at least T = ceil(heavy n /
+// 1000) entries (and at least kHeavyMinT); the break-even of a tensor-core
+// column (n^2 flops) against L^2 / 2 pair updates lies near L = 0.02 n.
+void plan_heavy(gakco_ctx* c, Plan& p, bool plain) {
+  const int L = c->M + 1;
+  p.heavy.clear();
+  p.hmap.assign(p.ds.size() * (size_t)L, kNone);
+  p.heavy_level.assign((size_t)L, 0);
+  p.heavy_t0 = (uint32_t)(p.dtiles.size() / kDenseTileWords);
+  p.heavy_nt = 0;
+  p.heavy_rows = 0;
+  p.heavy_abytes = p.heavy_list = 0;
+  if (plain || c->heavy <= 0) return;
+  const std::vector<uint32_t> lf = level_firsts(c);
+  struct Cand {
+    HeavyHost h;
+    double most;
+  };
+  std::vector<Cand> cand;
+  double wsum = 0;
+  for (size_t d = 0; d < p.ds.size(); ++d) {
+    const DsHost& D = p.ds[d];
+    if ((uint64_t)D.n < kHeavyMinSeqs || D.G == 0 || D.G >= (uint64_t)kHeavyBit) continue;
+    const uint32_t T =
+        std::max<uint32_t>(kHeavyMinT, (uint32_t)(((uint64_t)c->heavy * (uint64_t)D.n + 999) / 1000));
+    for (int m = p.first_level; m <= c->M; ++m) {
+      if (p.is_dense(d, m, c->M)) continue;
+      HeavyHost h{};
+      h.ds = (uint32_t)d;
+      h.level = (uint32_t)m;
+      h.n = (uint32_t)D.n;
+      h.n_pad = (uint32_t)align_up((size_t)D.n, 128);
+      h.T = T;
+      const double most = (double)(lf[m + 1] - lf[m]) * (double)D.G / (double)T;
+      cand.push_back({h, most});
+      wsum += most;
+    }
+  }
+  const double budget = (double)std::max<int64_t>(c->heavy_bytes, 0);
+  std::vector<double> cost;
+  for (const Cand& k : cand) {
+    HeavyHost h = k.h;
+    uint64_t cap = (uint64_t)(budget * k.most / wsum / (double)h.n_pad) / 128 * 128;
+    cap = std::min<uint64_t>(cap, align_up((size_t)std::ceil(k.most), 128));
+    cap = std::min<uint64_t>(cap, (uint64_t)1 << 30);
+    if (cap < 128) continue;
+    h.cap = cap;
+    h.a_off = p.heavy_abytes;
+    h.prob = (uint32_t)p.dprobs.size();
+    p.heavy_abytes += align_up((size_t)(cap * h.n_pad), 128);
+    p.heavy_list += cap;
+    DenseHost q{};
+    q.ds = h.ds;
+    q.level = h.level;
+    q.n = h.n;
+    q.n_pad = h.n_pad;
+    q.ld = cap;
+    q.a_off = h.a_off;
+    q.hidx = (uint32_t)p.heavy.size();
+    q.heavy = true;
+    p.dprobs.push_back(q);
+    p.hmap[(size_t)h.ds * L + h.level] = (uint32_t)p.heavy.size();
+    p.heavy_level[h.level] = 1;
+    p.heavy_rows = std::max(p.heavy_rows, h.n_pad);
+    p.heavy.push_back(h);
+    cost.push_back(k.most);
+  }
+  struct Part {
+    std::array<uint32_t, kDenseTileWords> w;
+    double cost;
+  };
+  std::vector<Part> parts;
+  for (size_t i = 0; i < p.heavy.size(); ++i) {
+    const HeavyHost& h = p.heavy[i];
+    const uint32_t R = (h.n_pad + 255) / 256;
+    for (uint32_t I2 = 0; I2 < R; ++I2)
+      for (uint32_t J2 = I2; J2 < R; ++J2)
+        if (I2 * 256 < h.n)
+          parts.push_back({{h.prob, 1u, I2, J2}, cost[i] * (double)h.n * (I2 * 256 + 128 < h.n ? 2.0 : 1.0)});
+  }
+  std::stable_sort(parts.begin(), parts.end(), [](const Part& x, const Part& y) { return x.cost > y.cost; });
+  for (const Part& pt : parts) p.dtiles.insert(p.dtiles.end(), pt.w.begin(), pt.w.end());
+  p.heavy_nt = (uint32_t)parts.size();
+}
+
 struct Tables {
   std::vector<uint8_t> buf;
   size_t add(const void* src, size_t bytes, size_t align = 16) {
@@ -909,6 +1028,10 @@ void add_common_tables(gakco_ctx* c, Plan& p, Tables& t) {
     p.o_dtiles = t.add(p.dtiles.data(), p.dtiles.size() * 4);
     p.o_tmaps = t.reserve(p.dprobs.size() * kDenseTmapBytes, 64);
   }
+  if (!p.heavy.empty()) {
+    p.o_hprobs = t.reserve(p.heavy.size() * sizeof(HeavyProb));
+    p.o_hmap = t.add(p.hmap.data(), p.hmap.size() * 4);
+  }
 }
 
 // Dense problem records and their TMA descriptors, once the A buffer and
@@ -920,12 +1043,13 @@ int fill_dense(gakco_ctx* c, Work& w, Plan& p, Tables& t) {
     cacc[d] = cacc[d - 1] + (uint64_t)(c->M + 1) * p.ds[d - 1].n * p.ds[d - 1].n;
   for (size_t i = 0; i < p.dprobs.size(); ++i) {
     const DenseHost& h = p.dprobs[i];
+    const uint32_t nh = (uint32_t)p.heavy.size();
     DenseProb q{};
-    q.A = (uint8_t*)w.Adense.p + h.a_off;
+    q.A = (h.heavy ? (uint8_t*)w.Aheavy.p : (uint8_t*)w.Adense.p) + h.a_off;
     q.C = (uint32_t*)w.Cacc.p + cacc[h.ds] + (uint64_t)h.level * h.n * h.n;
-    q.maxc = (uint32_t*)w.dmaxc.p + (size_t)h.ds * (c->M + 1) + h.level;
+    q.maxc = h.heavy ? (uint32_t*)w.hctr.p + nh + h.hidx : (uint32_t*)w.dmaxc.p + (size_t)h.ds * (c->M + 1) + h.level;
     q.tmap = base + p.o_tmaps + i * kDenseTmapBytes;
-    q.ld = h.ld;
+    q.ld = h.heavy ? 0 : h.ld;  // heavy: the columns in use, set on the device
     q.n = h.n;
     q.n_pad = h.n_pad;
     q.ds = h.ds;
@@ -936,6 +1060,20 @@ int fill_dense(gakco_ctx* c, Work& w, Plan& p, Tables& t) {
     memcpy(t.buf.data() + p.o_dprobs + i * sizeof(DenseProb), &q, sizeof q);
     const int r = dense_encode_tmap(t.buf.data() + p.o_tmaps + i * kDenseTmapBytes, q.A, h.ld, h.n_pad);
     if (r != 0) return wfail(w, GAKCO_E_CUDA, "TMA descriptor of dense problem %zu failed (%d)", i, r);
+  }
+  for (size_t i = 0; i < p.heavy.size(); ++i) {
+    const HeavyHost& h = p.heavy[i];
+    HeavyProb r{};
+    r.A = (uint8_t*)w.Aheavy.p + h.a_off;
+    r.ncols = (uint32_t*)w.hctr.p + i;
+    r.maxc = (uint32_t*)w.hctr.p + p.heavy.size() + i;
+    r.stride = h.cap;
+    r.cap = (uint32_t)h.cap;
+    r.T = h.T;
+    r.n = h.n;
+    r.n_pad = h.n_pad;
+    r.prob = h.prob;
+    memcpy(t.buf.data() + p.o_hprobs + i * sizeof(HeavyProb), &r, sizeof r);
   }
   return GAKCO_OK;
 }
@@ -1003,6 +1141,11 @@ int plan_memory_and_tables(gakco_ctx* c, Work& w, Plan& p, bool plain) {
     ENSURE(dmaxc, (p.ds.size() * (c->M + 1) + 1) * 4);  // per (dataset, level), + the overflow counter
     ENSURE(dovf, (size_t)c->dense_overflow * sizeof(DenseOvf));
   }
+  if (!p.heavy.empty()) {
+    ENSURE(Aheavy, p.heavy_abytes);
+    ENSURE(hctr, (2 * p.heavy.size() + 1) * 4);  // columns and largest count per problem, list length
+    ENSURE(hlist, p.heavy_list * sizeof(HeavyItem));
+  }
   Tables t;
   add_common_tables(c, p, t);
   if ((rc = ensure(c, w, w.tables, t.buf.size(), "tables")) != GAKCO_OK) return rc;
@@ -1057,10 +1200,20 @@ void enqueue_chunk(gakco_ctx* c, Work& w, const Plan& p, const Chunk& ch, Tail t
     cur ^= 1;
   }
   if (tail == Tail::kGram) {
-    Bracket b(c, w, "run_length", 4);
-    launch_rle_gram(ch.wide, segs, ch.nseg, tseg, ch.ntiles, kin, vin, (const DsPack*)(base + p.o_pack),
-                    (uint32_t*)w.tcnt.p, (uint32_t*)w.segtot.p, (uint32_t*)w.trec.p, (uint32_t*)w.ewin.p,
-                    (uint32_t*)w.eseq.p, (uint32_t*)w.efe.p, w.cs);
+    {
+      Bracket b(c, w, "run_length", 4);
+      launch_rle_gram(ch.wide, segs, ch.nseg, tseg, ch.ntiles, kin, vin, (const DsPack*)(base + p.o_pack),
+                      (uint32_t*)w.tcnt.p, (uint32_t*)w.segtot.p, (uint32_t*)w.trec.p, (uint32_t*)w.ewin.p,
+                      (uint32_t*)w.eseq.p, (uint32_t*)w.efe.p, w.cs);
+    }
+    if (!p.heavy.empty() && p.heavy_level[ch.level]) {
+      Bracket b(c, w, "heavy_mark", 1);
+      launch_heavy_mark(segs, tseg, ch.ntiles, (const uint32_t*)w.segtot.p, levels,
+                        (const uint32_t*)(base + p.o_hmap), (uint32_t)(c->M + 1),
+                        (const HeavyProb*)(base + p.o_hprobs), (const uint32_t*)w.eseq.p,
+                        (const uint32_t*)w.efe.p, (HeavyItem*)w.hlist.p,
+                        (uint32_t*)w.hctr.p + 2 * p.heavy.size(), w.cs);
+    }
     return;
   }
   Bracket b(c, w, "run_length", tail == Tail::kFit ? 5 : 4);
@@ -1095,11 +1248,16 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
   AccParams a = acc_params(c, w, p, status + 8);
   if (!plain) {
     if (p.c_elems) cudaMemsetAsync(w.Cacc.p, 0, p.c_elems * 4, w.cs);
+    const uint32_t nh = (uint32_t)p.heavy.size();
+    if (nh) cudaMemsetAsync(w.hctr.p, 0, (2 * (size_t)nh + 1) * 4, w.cs);
     // Dense levels (tensor cores) and sparse levels (sort, run-length,
     // on-chip accumulation) write disjoint levels of C and share only
     // read-only inputs, so they run as two branches (except when profiling,
-    // where every launch is timed on one stream).
-    const bool fork = c->overlap && !c->profile && !p.dwaves.empty();
+    // where every launch is timed on one stream).  The heavy features'
+    // contraction joins the dense branch once the sparse branch has built
+    // its matrices; it and the accumulation add disjoint pairs of features
+    // into the same C_m with atomics.
+    const bool fork = c->overlap && !c->profile && (!p.dwaves.empty() || nh > 0);
     cudaStream_t ds = w.cs;
     if (fork) {
       cudaEventRecord(w.ev_fork, w.cs);
@@ -1131,8 +1289,30 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
         launch_dense_fix(probs, ovf_n, (const DenseOvf*)w.dovf.p, cap, status, ds);
       }
     }
-    if (fork) cudaEventRecord(w.ev_join, w.cs2);
     for (const Chunk& ch : p.chunks) enqueue_chunk(c, w, p, ch, Tail::kGram);
+    if (nh) {
+      const HeavyProb* hp = (const HeavyProb*)(base + p.o_hprobs);
+      const uint32_t* nitems = (const uint32_t*)w.hctr.p + 2 * nh;
+      {
+        Bracket b(c, w, "heavy_prep", 2);
+        launch_heavy_zero(hp, nh, p.heavy_rows, (DenseProb*)(base + p.o_dprobs),
+                          (unsigned long long*)((uint8_t*)w.status.p + 96), w.cs);
+        launch_heavy_scatter(hp, (const HeavyItem*)w.hlist.p, nitems, (uint32_t*)w.eseq.p, (uint32_t*)w.efe.p,
+                             c->nsm, w.cs);
+      }
+      cudaStream_t hs = w.cs;
+      if (fork) {
+        cudaEventRecord(w.ev_heavy, w.cs);
+        cudaStreamWaitEvent(w.cs2, w.ev_heavy, 0);
+        hs = w.cs2;
+      }
+      Bracket b(c, w, "heavy_gemm", 1);
+      const int gemm_ctas = c->dense_sms > 0 ? std::min(c->dense_sms, c->nsm) : c->nsm;
+      launch_dense_gemm((const DenseProb*)(base + p.o_dprobs),
+                        (const uint32_t*)(base + p.o_dtiles) + kDenseTileWords * (size_t)p.heavy_t0, p.heavy_nt,
+                        gemm_ctas, status, hs);
+    }
+    if (fork) cudaEventRecord(w.ev_join, w.cs2);
     {
       Bracket b(c, w, "accumulate", 1);
       launch_accum(a, c->accum_threads, p.acc_blocks, p.acc_smem, w.cs);
@@ -1177,9 +1357,9 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
 
 uint64_t plan_key(gakco_ctx* c, const Plan& p, bool plain) {
   uint64_t h = 1469598103934665603ull;
-  int64_t o[14] = {plain,           c->radix_bits, c->chunk_elems, c->accum_threads,  c->smem_cols,
+  int64_t o[16] = {plain,           c->radix_bits, c->chunk_elems, c->accum_threads,  c->smem_cols,
                    (int64_t)p.ds.size(), c->group_bytes, c->dense,    c->dense_bytes, c->dense_overflow,
-                   c->dense_run_cols, p.first_level, c->overlap, c->dense_sms};
+                   c->dense_run_cols, p.first_level, c->overlap, c->dense_sms, c->heavy, c->heavy_bytes};
   h = fnv1a(h, o, sizeof o);
   for (const DsHost& D : p.ds) {
     const void* ptrs[4] = {D.codes, D.K, D.Khat, D.Nm};
@@ -1197,6 +1377,8 @@ int check_status(gakco_ctx* c, Work& w) {
   w.pairs = (double)wk[0];
   w.entries = (double)wk[1];
   w.windows = (double)wk[2];
+  w.heavy_cols = (double)wk[4];
+  w.heavy_flops = (double)wk[5];
   if (st & kErrBadCode) return wfail(w, GAKCO_E_INVALID, "input holds a symbol >= sigma (%d)", c->sigma);
   if (st & kErrKneCM) return wfail(w, GAKCO_E_INTERNAL, "internal check failed: sum h_m N_m != C_M");
   if (st & kErrBadEntry) return wfail(w, GAKCO_E_INTERNAL, "internal check failed: entry out of range");
@@ -1291,8 +1473,9 @@ int run_gram_once(gakco_ctx* c, Plan& p, cudaStream_t user) {
   } else {
     drop_graph(c);
     plan_dense(c, p, plain);
-    plan_chunks(c, p, plain);
     c->plan_dense_probs = (double)p.dprobs.size();
+    plan_heavy(c, p, plain);
+    plan_chunks(c, p, plain);
     c->plan_dense_flops = p.dense_flops;
     c->plan_dense_issued = p.dense_issued;
     c->plan_dense_bytes = p.dense_bytes;
@@ -1334,6 +1517,8 @@ int run_gram_once(gakco_ctx* c, Plan& p, cudaStream_t user) {
   c->last_pairs = w.pairs;
   c->last_entries = w.entries;
   c->last_windows = w.windows;
+  c->last_heavy_cols = w.heavy_cols;
+  c->last_heavy_flops = w.heavy_flops;
   e = cudaEventRecord(c->ev_out, w.cs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(user, c->ev_out, 0);
   if (e != cudaSuccess && rc == GAKCO_OK) rc = wcuda(w, e, "stream ordering");
@@ -1982,7 +2167,7 @@ int autotune(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64_
   int64_t best_gb = c->group_bytes;
   best = 1e30;
   for (int th : {256, 512}) {
-    for (int64_t gb : {(int64_t)32 << 20, (int64_t)64 << 20, (int64_t)128 << 20}) {
+    for (int64_t gb : {(int64_t)64 << 20, (int64_t)128 << 20, (int64_t)256 << 20, (int64_t)512 << 20}) {
       if (rc != GAKCO_OK) break;
       c->accum_threads = th;
       c->group_bytes = gb;
@@ -2113,7 +2298,10 @@ int gakco_create(int sigma, int g, int k, gakco_ctx** out) {
   if (e == cudaSuccess) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && tot > 0)
+    {
       c->dense_bytes = std::min<int64_t>(c->dense_bytes, (int64_t)(tot / 4));
+      c->heavy_bytes = std::min<int64_t>(c->heavy_bytes, (int64_t)(tot / 16));
+    }
     cudaGetLastError();
   }
   if (e == cudaSuccess && init_work(c->main) != GAKCO_OK) e = cudaErrorMemoryAllocation;
@@ -2209,6 +2397,14 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
       if (v != 0 && v != 1) return fail(c, GAKCO_E_INVALID, "overlap must be 0 or 1");
       c->overlap = (int)v;
       break;
+    case GAKCO_OPT_HEAVY:
+      if (v < 0 || v > 1000) return fail(c, GAKCO_E_INVALID, "heavy threshold must be 0..1000 (thousandths)");
+      c->heavy = (int)v;
+      break;
+    case GAKCO_OPT_HEAVY_BYTES:
+      if (v < 0) return fail(c, GAKCO_E_INVALID, "heavy bytes must be >= 0");
+      c->heavy_bytes = v;
+      break;
     case GAKCO_OPT_DENSE_SMS:
       if (v < 0) return fail(c, GAKCO_E_INVALID, "dense SM count must be >= 0");
       c->dense_sms = (int)v;
@@ -2274,6 +2470,12 @@ int gakco_get_stat(const gakco_ctx* c, int key, double* v) {
       return GAKCO_OK;
     case GAKCO_STAT_DENSE_BYTES:
       *v = c->plan_dense_bytes;
+      return GAKCO_OK;
+    case GAKCO_STAT_HEAVY_COLUMNS:
+      *v = c->last_heavy_cols;
+      return GAKCO_OK;
+    case GAKCO_STAT_HEAVY_FLOPS:
+      *v = c->last_heavy_flops;
       return GAKCO_OK;
     case GAKCO_STAT_SORT_BYTES:
       *v = c->plan_sort_bytes;

@@ -13,8 +13,12 @@
 // warps walk the group's masks over the windows of x, and for each entry
 // (f, x, c_x) of the row add c_x * c_y for every entry (f, y, c_y) of the
 // same feature with y >= x.  Entries of a feature are sorted by sequence,
-// so y >= x is the tail of the feature's entry range.  The row is then
-// added to the global C_m with coalesced reductions.  Items are handed out
+// so y >= x is the tail of the feature's entry range.  A window slot
+// tagged as a one-sequence feature (kSingleTag | count) only adds count^2
+// to the diagonal: summed in registers, added once per item.  The row is then
+// added to the global C_m with coalesced reductions.  Entries of heavy
+// features (kHeavyBit in their feature end) are skipped: the tensor cores
+// add those features' pairs.  Items are handed out
 // group by group, so the rows being processed at any moment read the same
 // few masks' entry arrays, which stay in L2.
 #include <cstdint>
@@ -89,6 +93,7 @@ k_accum(const AccParams p) {
     const bool lo_cut = c0 > x, hi_cut = c1 < ds.n;
     const uint32_t nch = (wend - wbeg + 31) / 32;
     uint32_t n_pairs = 0, n_ent = 0;    // work counters of this thread
+    uint32_t dsum = 0;                  // diagonal from one-sequence features
     for (uint32_t ch = w; ch < mcount * nch; ch += kWarps) {
       const uint32_t mu = mfirst + ch / nch;
       const uint32_t wi = wbeg + (ch % nch) * 32 + lane;
@@ -97,10 +102,19 @@ k_accum(const AccParams p) {
       const uint32_t* __restrict__ es = p.eseq + pool;
       const uint32_t* __restrict__ ef = p.efe + pool;
       uint32_t e = wi < wend ? ew[wi] : kNone;
+      if (is_single(e)) {
+        const uint32_t cs = e & 0xFFFFu;
+        dsum += cs * cs;
+        ++n_pairs;
+        ++n_ent;
+        e = kNone;
+      }
       uint32_t lo = 0, cnt = 0, c = 0;
       if (e != kNone) {
         const uint32_t hi0 = e < gd ? ef[e] : 0;
-        if (e >= gd || hi0 > gd || hi0 <= e) {
+        if (hi0 & kHeavyBit) {
+          e = kNone;  // a heavy feature: the dense contraction adds its pairs
+        } else if (e >= gd || hi0 > gd || hi0 <= e) {
           atomicOr(p.status, kErrBadEntry);  // corrupt entry: skip it
           e = kNone;
         } else {
@@ -176,6 +190,9 @@ k_accum(const AccParams p) {
         }
       }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
+    if (lane == 0 && dsum && x >= c0 && x < c1) atomicAdd(&acc[x - c0], dsum);
     if (p.work) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {

@@ -506,6 +506,119 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
   }
 }
 
+// ------------------------------------------------------- heavy features --
+
+// One block per tile of a run-length chunk, over the tile's range of the
+// segment's entries.  A feature starts at entry e when e = 0 or the
+// previous entry's feature end differs (all entries of a feature share
+// it); a warp checks its 32 entries, then examines each qualifying start
+// together (the largest count of the feature must be <= 16, so that A
+// holds the counts exactly).
+__global__ void __launch_bounds__(256)
+k_heavy_mark(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg,
+             const uint32_t* __restrict__ segtot, const uint32_t* __restrict__ mask_level,
+             const uint32_t* __restrict__ hmap, uint32_t levels, const HeavyProb* __restrict__ hprobs,
+             const uint32_t* __restrict__ eseq, const uint32_t* __restrict__ efe,
+             HeavyItem* __restrict__ items, uint32_t* __restrict__ nitems) {
+  const uint32_t t = blockIdx.x;
+  const uint32_t s = tile_seg[t];
+  const SegDesc sd = segs[s];
+  const uint32_t hp = hmap[sd.ds * levels + mask_level[sd.mask]];
+  if (hp == kNone) return;
+  const HeavyProb& H = hprobs[hp];
+  const uint32_t E = segtot[2 * (uint64_t)s];
+  const uint64_t e_beg = (uint64_t)(t - sd.tile0) * kTile;
+  if (e_beg >= E) return;
+  const uint32_t e_end = (uint32_t)min((uint64_t)E, e_beg + kTile);
+  const uint32_t* __restrict__ es = eseq + sd.pool;
+  const uint32_t* __restrict__ ef = efe + sd.pool;
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (uint32_t b = (uint32_t)e_beg + w * 32; b < e_end; b += blockDim.x) {
+    const uint32_t e = b + lane;
+    uint32_t fe = 0;
+    bool cand = false;
+    if (e < e_end) {
+      fe = ef[e];
+      cand = (e == 0 || ef[e - 1] != fe) && fe > e && fe <= E && fe - e >= H.T;
+    }
+    uint32_t bm = __ballot_sync(0xffffffffu, cand);
+    while (bm) {
+      const int L0 = __ffs(bm) - 1;
+      bm &= bm - 1;
+      const uint32_t e0 = __shfl_sync(0xffffffffu, e, L0), f0 = __shfl_sync(0xffffffffu, fe, L0);
+      uint32_t mx = 0;
+      for (uint32_t q = e0 + lane; q < f0; q += 32) mx = max(mx, es[q] & 0xFFFFu);
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      if (mx <= 16 && lane == 0) {
+        const uint32_t col = atomicAdd(H.ncols, 1u);
+        if (col < H.cap) {
+          const uint32_t slot = atomicAdd(nitems, 1u);
+          items[slot] = HeavyItem{sd.pool, e0, f0 - e0, col, hp, {0u, 0u}};
+          atomicMax(H.maxc, mx);
+        }
+      }
+    }
+  }
+}
+
+// Grid (rows, problems): clears the used columns of one row of A.
+__global__ void __launch_bounds__(256)
+k_heavy_zero(const HeavyProb* __restrict__ hprobs, DenseProb* __restrict__ dprobs,
+             unsigned long long* __restrict__ work) {
+  const uint32_t hp = blockIdx.y, row = blockIdx.x;
+  const HeavyProb& H = hprobs[hp];
+  if (row >= H.n_pad) return;
+  const uint32_t used = min(*H.ncols, H.cap);
+  const uint32_t K = (used + 127u) & ~127u;
+  uint4* a = (uint4*)(H.A + (uint64_t)row * H.stride);
+  for (uint32_t i = threadIdx.x; i < K / 16; i += blockDim.x) a[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (row == 0 && threadIdx.x == 0) {
+    dprobs[H.prob].ld = K;
+    atomicAdd(&work[0], (unsigned long long)used);
+    atomicAdd(&work[1], (unsigned long long)used * H.n * (H.n + 1ull));
+  }
+}
+
+// One warp per listed feature.
+__global__ void __launch_bounds__(256)
+k_heavy_scatter(const HeavyProb* __restrict__ hprobs, const HeavyItem* __restrict__ items,
+                const uint32_t* __restrict__ nitems, const uint32_t* __restrict__ eseq,
+                uint32_t* __restrict__ efe) {
+  const uint32_t N = *nitems;
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint32_t i = blockIdx.x * 8 + (threadIdx.x >> 5); i < N; i += gridDim.x * 8) {
+    const HeavyItem it = items[i];
+    const HeavyProb& H = hprobs[it.hp];
+    const uint32_t* __restrict__ es = eseq + it.pool;
+    uint32_t* __restrict__ ef = efe + it.pool;
+    for (uint32_t q = it.fs + lane; q < it.fs + it.L; q += 32) {
+      const uint32_t v = es[q];
+      H.A[(uint64_t)(v >> 16) * H.stride + it.col] = (uint8_t)e4m3x2_of_counts(v & 0xFFFFu);
+      ef[q] |= kHeavyBit;
+    }
+  }
+}
+
+void launch_heavy_mark(const SegDesc* segs, const uint32_t* tile_seg, uint32_t ntiles,
+                       const uint32_t* segtot, const uint32_t* mask_level, const uint32_t* hmap,
+                       uint32_t levels, const HeavyProb* hprobs, const uint32_t* eseq,
+                       const uint32_t* efe, HeavyItem* items, uint32_t* nitems, cudaStream_t st) {
+  if (ntiles == 0) return;
+  k_heavy_mark<<<ntiles, 256, 0, st>>>(segs, tile_seg, segtot, mask_level, hmap, levels, hprobs, eseq, efe,
+                                       items, nitems);
+}
+
+void launch_heavy_zero(const HeavyProb* hprobs, uint32_t nh, uint32_t max_rows, DenseProb* dprobs,
+                       unsigned long long* work, cudaStream_t st) {
+  if (nh == 0 || max_rows == 0) return;
+  k_heavy_zero<<<dim3(max_rows, nh), 256, 0, st>>>(hprobs, dprobs, work);
+}
+
+void launch_heavy_scatter(const HeavyProb* hprobs, const HeavyItem* items, const uint32_t* nitems,
+                          uint32_t* eseq, uint32_t* efe, int nsm, cudaStream_t st) {
+  k_heavy_scatter<<<nsm * 4, 256, 0, st>>>(hprobs, items, nitems, eseq, efe);
+}
+
 size_t dense_scatter_smem() { return (size_t)kDenseScatterCols * 2; }
 size_t dense_gemm_smem() { return (size_t)kStages * kStageBytes + 1024; }
 

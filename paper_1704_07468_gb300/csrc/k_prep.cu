@@ -542,6 +542,9 @@ k_rle_final(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
 // packed entries directly.  For an entry e starting at element i:
 //   eseq[e] = (sequence << 16) | count, count = (next entry start) - i;
 //   efe[e]  = first entry of the next feature.
+// A feature held by one sequence only adds count^2 to that sequence's
+// diagonal; when its count is known here, ewin of its first window holds
+// kSingleTag | count instead of the entry (see k_accum).
 // Both "next" starts are found by a backward pass over the tile's items
 // (ballots within a warp, per-warp summaries across warps).  The last entry
 // of a tile, and the entries of the tile's last feature, may end in a later
@@ -644,15 +647,18 @@ k_rle_emit_gram(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ t
     const uint32_t idx = item0 + lane;
     if (idx < cnt) {
       const uint32_t e = re + __popc(be & lt_mask);
+      uint32_t wv = kNone;
       if (ne) {
         const uint32_t hb = be & gt_mask;
         const uint32_t nxt = hb ? item0 + __ffs(hb) - 1 : cne;
-        eseq[sd.pool + e] = (sq[j] << 16) | (nxt == kNone ? 0u : nxt - idx);
+        const uint32_t cv = nxt == kNone ? 0u : nxt - idx;
+        eseq[sd.pool + e] = (sq[j] << 16) | cv;
         const uint32_t hf = bf & gt_mask;
         const uint32_t fend = hf ? re + __popc(be & ((1u << (__ffs(hf) - 1)) - 1u)) : cnf;
         if (fend != kNone) efe[sd.pool + e] = fend;
+        wv = (nf && fend == e + 1 && cv != 0u) ? (kSingleTag | cv) : e;
       }
-      ewin[sd.pool + woff[vv[j] >> 16] + (vv[j] & 0xFFFFu)] = ne ? e : kNone;
+      ewin[sd.pool + woff[vv[j] >> 16] + (vv[j] & 0xFFFFu)] = wv;
     }
     if (be) cne = item0 + __ffs(be) - 1;
     if (bf) cnf = re + __popc(be & ((1u << (__ffs(bf) - 1)) - 1u));

@@ -218,6 +218,50 @@ void launch_dense_gemm(const DenseProb* d_probs, const uint32_t* d_tiles, uint32
 void launch_dense_fix(const DenseProb* d_probs, const uint32_t* ovf_n, const DenseOvf* ovf, uint32_t ovf_cap,
                       uint32_t* status, cudaStream_t st);
 
+// Heavy features of sparse levels.  A feature held by many sequences costs
+// about L^2 / 2 pair updates on the sparse route (L = its entries) but only
+// one column of a dense contraction on the tensor cores.  After a sparse
+// level's run-length pass, features with at least T entries whose counts
+// are all <= 16 get a column of the (dataset, level)'s matrix A (e4m3,
+// n_pad rows); their entries are flagged (kHeavyBit in efe) so that the
+// on-chip accumulation skips them, and the dense GEMM adds A A^T to C_m.
+// Which features go dense changes no result.
+constexpr uint32_t kHeavyBit = 0x80000000u;
+struct HeavyProb {
+  uint8_t* A;          // n_pad x stride bytes
+  uint32_t* ncols;     // columns handed out so far (may run past cap)
+  uint32_t* maxc;      // largest count in A (for the GEMM's exact rounds)
+  uint64_t stride;     // row stride of A in bytes (a multiple of 128)
+  uint32_t cap;        // columns available (<= stride)
+  uint32_t T;          // threshold on a feature's entries
+  uint32_t n, n_pad;   // sequences; rows of A
+  uint32_t prob;       // index of the GEMM's DenseProb record
+  uint32_t pad;
+};
+// One heavy feature: entries [fs, fs + L) of the pool at `pool`, column col
+// of heavy problem hp.
+struct HeavyItem {
+  uint64_t pool;
+  uint32_t fs, L, col, hp;
+  uint32_t pad[2];
+};
+// Per tile of a run-length chunk: features starting in the tile's entry
+// range that qualify are appended to items[*nitems++] (nitems never
+// exceeds the sum of the caps).  hmap[ds * levels + level] is the heavy
+// problem of a (dataset, level) or kNone.
+void launch_heavy_mark(const SegDesc* segs, const uint32_t* tile_seg, uint32_t ntiles,
+                       const uint32_t* segtot, const uint32_t* mask_level, const uint32_t* hmap,
+                       uint32_t levels, const HeavyProb* hprobs, const uint32_t* eseq,
+                       const uint32_t* efe, HeavyItem* items, uint32_t* nitems, cudaStream_t st);
+// Zeroes the used columns (rounded up to 128) of every heavy problem's A
+// and sets the GEMM records' column counts; adds the columns and the
+// upper-triangle flops to work[0], work[1].
+void launch_heavy_zero(const HeavyProb* hprobs, uint32_t nh, uint32_t max_rows, DenseProb* dprobs,
+                       unsigned long long* work, cudaStream_t st);
+// Writes the listed features' counts into A and flags their entries.
+void launch_heavy_scatter(const HeavyProb* hprobs, const HeavyItem* items, const uint32_t* nitems,
+                          uint32_t* eseq, uint32_t* efe, int nsm, cudaStream_t st);
+
 // Plain per-mask path (Alg. 1 as written: countAndUpdate straight into the
 // global C_m with atomics, then inclusion-exclusion).
 void launch_pairs_global(const uint32_t* segtot_E, const uint32_t* eseq,
