@@ -238,6 +238,7 @@ struct gakco_ctx {
   std::vector<std::pair<std::string, std::pair<double, int64_t>>> timings;
 
   Train train;
+  Train train_add, train_merged;  // index of added sequences; merge target (swapped in)
 
   // serving
   std::mutex mu;
@@ -1579,8 +1580,7 @@ int gram_host(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64
 
 // --------------------------------------------------------- training index --
 
-TrainIndex train_index(gakco_ctx* c) {
-  Train& T = c->train;
+TrainIndex train_index(const Train& T) {
   TrainIndex tr{};
   tr.ukey = (uint64_t*)T.ukey.p;
   tr.ufirst = (uint32_t*)T.ufirst.p;
@@ -1593,6 +1593,8 @@ TrainIndex train_index(gakco_ctx* c) {
   return tr;
 }
 
+TrainIndex train_index(gakco_ctx* c) { return train_index(c->train); }
+
 CrossParams cross_params(gakco_ctx* c, Work& w) {
   CrossParams x{};
   x.tr = train_index(c);
@@ -1604,14 +1606,15 @@ CrossParams cross_params(gakco_ctx* c, Work& w) {
 }
 
 // Build the resident index of a training set (device codes, host offsets).
-int fit(gakco_ctx* c, const uint8_t* d_codes, const int64_t* off, int32_t n) {
+// The per-mask training index of a set of sequences (device codes, host
+// offsets) into T: sort and count every mask, keep the features, their
+// first entries and the entries, and the diagonal and norms.  Enqueued on
+// the main Work's stream; does not wait.
+int build_index(gakco_ctx* c, Train& T, const uint8_t* d_codes, const int64_t* off, int32_t n) {
   Work& w = c->main;
-  Train& T = c->train;
   // The cached Gram graph points into w's tables and buffers, which this
   // call rewrites and may reallocate.
   drop_graph(c);
-  T.ok = false;
-  T.svm_ok = false;  // coefficients belong to the previous training set
   Plan p;
   int rc = plan_datasets(c, w, p, 1, &d_codes, &off, &n, nullptr, nullptr, nullptr, false);
   if (rc != GAKCO_OK) return rc;
@@ -1648,13 +1651,24 @@ int fit(gakco_ctx* c, const uint8_t* d_codes, const int64_t* off, int32_t n) {
   cudaMemsetAsync(T.ufirst.p, 0, nm * stride * 4, w.cs);
   launch_pack((const DsPack*)(base + p.o_pack), 1, p.nseq, c->g, c->bits, c->sigma,
               (uint64_t*)w.fullkey.p, (uint32_t*)w.wid.p, status, w.cs);
-  const TrainIndex tr = train_index(c);
+  const TrainIndex tr = train_index(T);
   for (const Chunk& ch : p.chunks) enqueue_chunk(c, w, p, ch, Tail::kFit, &tr);
   CrossParams x = cross_params(c, w);
   launch_vec_diag(tr.diagC, (uint32_t)n, x, tr.rinv, w.cs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return wcuda(w, e, "kernel launch");
-  // Keep the training codes: adding sequences later refits on the union.
+  return GAKCO_OK;
+}
+
+int fit(gakco_ctx* c, const uint8_t* d_codes, const int64_t* off, int32_t n) {
+  Work& w = c->main;
+  Train& T = c->train;
+  T.ok = false;
+  T.svm_ok = false;  // coefficients belong to the previous training set
+  int rc = build_index(c, T, d_codes, off, n);
+  if (rc != GAKCO_OK) return rc;
+  cudaError_t e = cudaSuccess;
+  // Keep the training codes: adding sequences appends to them.
   const uint64_t cbytes = n > 0 ? (uint64_t)off[n] : 0;
   if ((rc = ensure(c, w, T.tcodes, cbytes + 16, "training codes")) != GAKCO_OK) return rc;
   if (cbytes && (e = cudaMemcpyAsync(T.tcodes.p, d_codes, cbytes, cudaMemcpyDeviceToDevice, w.cs)) != cudaSuccess)
@@ -1674,7 +1688,9 @@ int cross_host(gakco_ctx* c, const uint8_t* codes, const int64_t* off, int32_t n
 // sequences they are the cross kernel, among themselves the Gram kernel of
 // the new block.  Khat follows the Gram engine exactly: r = 1 / sqrt(K(x, x))
 // (the resident index keeps the old ones), (K * r_a) * r_b with a the
-// smaller index, 1 on a nonzero diagonal.  The fitted set becomes the union.
+// smaller index, 1 on a nonzero diagonal.  The fitted set becomes the
+// union: the new sequences' index is built and merged into the resident one
+// (launch_index_merge), which leaves it identical to a fit of the union.
 int extend(gakco_ctx* c, const uint8_t* codes, const int64_t* off, int32_t nb, int32_t* Krows,
            double* Khat) {
   Work& w = c->main;
@@ -1721,18 +1737,60 @@ int extend(gakco_ctx* c, const uint8_t* codes, const int64_t* off, int32_t nb, i
         hr[n + j] = ((double)v * rnew[i]) * rnew[j];
     }
   }
-  // Refit on the union: old codes (kept on the device) then the new ones.
-  std::vector<int64_t> uoff(T.toff);
-  const int64_t base = uoff.back();
-  for (int32_t x = 0; x < nb; ++x) uoff.push_back(base + off[x + 1]);
-  const uint64_t newbytes = nb > 0 ? (uint64_t)off[nb] : 0;
-  if ((rc = ensure(c, w, w.codes, (size_t)base + newbytes + 16, "codes")) != GAKCO_OK) return rc;
-  cudaError_t e = cudaSuccess;
-  if (base) e = cudaMemcpyAsync(w.codes.p, T.tcodes.p, (size_t)base, cudaMemcpyDeviceToDevice, w.cs);
-  if (e == cudaSuccess && newbytes)
-    e = cudaMemcpyAsync((uint8_t*)w.codes.p + base, codes, newbytes, cudaMemcpyHostToDevice, w.cs);
-  if (e != cudaSuccess) return wcuda(w, e, "stage the union's codes");
-  return fit(c, (const uint8_t*)w.codes.p, uoff.data(), (int32_t)N);
+  if (nb == 0) return GAKCO_OK;  // the fitted set is unchanged
+  // The union's index: the new sequences' own index, merged per mask into
+  // the resident one (their ids follow the old ones), then swapped in.
+  const uint64_t base = (uint64_t)T.toff.back();
+  const uint64_t newbytes = (uint64_t)off[nb];
+  if ((rc = ensure(c, w, w.codes, newbytes + 16, "codes")) != GAKCO_OK) return rc;
+  cudaError_t e = cudaMemcpyAsync(w.codes.p, codes, newbytes, cudaMemcpyHostToDevice, w.cs);
+  if (e != cudaSuccess) return wcuda(w, e, "upload the new codes");
+  Train& B = c->train_add;
+  if ((rc = build_index(c, B, (const uint8_t*)w.codes.p, off, nb)) != GAKCO_OK) return rc;
+  Train& U = c->train_merged;
+  const uint64_t nm = c->masks.size(), L = (uint64_t)(c->M + 1);
+  const uint64_t GU = T.G + B.G, su = GU + 1;
+  if ((rc = ensure(c, w, U.ukey, nm * su * 8, "merged keys")) != GAKCO_OK) return rc;
+  if ((rc = ensure(c, w, U.ufirst, nm * su * 4, "merged features")) != GAKCO_OK) return rc;
+  if ((rc = ensure(c, w, U.eseq, nm * su * 4, "merged entries")) != GAKCO_OK) return rc;
+  if ((rc = ensure(c, w, U.nfeat, nm * 4, "merged feature counts")) != GAKCO_OK) return rc;
+  if ((rc = ensure(c, w, U.diagC, L * N * 4, "merged diagonal")) != GAKCO_OK) return rc;
+  if ((rc = ensure(c, w, U.rinv, N * 8, "merged norms")) != GAKCO_OK) return rc;
+  if ((rc = ensure(c, w, U.tcodes, base + newbytes + 16, "merged codes")) != GAKCO_OK) return rc;
+  if ((rc = ensure(c, w, w.ea, nm * (B.G + 1) * 4, "merge ranks")) != GAKCO_OK) return rc;
+  if ((rc = ensure(c, w, w.eb, nm * (B.G + 1) * 4, "merge flags")) != GAKCO_OK) return rc;
+  U.n = (int32_t)N;
+  U.G = GU;
+  launch_index_merge(train_index(T), train_index(B), train_index(U), (uint32_t)nm, (uint32_t*)w.ea.p,
+                     (uint32_t*)w.eb.p, (uint32_t)n, w.cs);
+  if (n > 0) {
+    e = cudaMemcpy2DAsync(U.diagC.p, N * 4, T.diagC.p, (size_t)n * 4, (size_t)n * 4, L, cudaMemcpyDeviceToDevice, w.cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(U.rinv.p, T.rinv.p, (size_t)n * 8, cudaMemcpyDeviceToDevice, w.cs);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync((uint32_t*)U.diagC.p + n, N * 4, B.diagC.p, (size_t)nb * 4, (size_t)nb * 4, L,
+                          cudaMemcpyDeviceToDevice, w.cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync((double*)U.rinv.p + n, B.rinv.p, (size_t)nb * 8, cudaMemcpyDeviceToDevice, w.cs);
+  if (e == cudaSuccess && base) e = cudaMemcpyAsync(U.tcodes.p, T.tcodes.p, base, cudaMemcpyDeviceToDevice, w.cs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((uint8_t*)U.tcodes.p + base, w.codes.p, newbytes, cudaMemcpyDeviceToDevice, w.cs);
+  if (e != cudaSuccess) return wcuda(w, e, "assemble the merged index");
+  T.ok = false;
+  if ((rc = sync_and_check(c, w)) != GAKCO_OK) return rc;
+  std::swap(T.ukey, U.ukey);
+  std::swap(T.ufirst, U.ufirst);
+  std::swap(T.eseq, U.eseq);
+  std::swap(T.nfeat, U.nfeat);
+  std::swap(T.diagC, U.diagC);
+  std::swap(T.rinv, U.rinv);
+  std::swap(T.tcodes, U.tcodes);
+  for (int32_t x = 1; x <= nb; ++x) T.woff.push_back((uint32_t)(T.G + B.woff[x]));
+  for (int32_t x = 1; x <= nb; ++x) T.toff.push_back((int64_t)base + off[x]);
+  T.n = (int32_t)N;
+  T.G = GU;
+  T.svm_ok = false;  // coefficients belong to the previous training set
+  T.ok = true;
+  return GAKCO_OK;
 }
 
 // Enqueue the cross kernel of one test batch on w (device codes, host
@@ -2320,9 +2378,10 @@ void gakco_destroy(gakco_ctx* c) {
   if (c->main.cs) cudaStreamSynchronize(c->main.cs);
   drop_graph(c);
   release_work(c->main);
-  Train& T = c->train;
-  DevBuf* tb[] = {&T.ukey, &T.ufirst, &T.eseq, &T.nfeat, &T.diagC, &T.rinv, &T.svm, &T.tcodes};
-  for (DevBuf* b : tb) release(*b);
+  for (Train* T : {&c->train, &c->train_add, &c->train_merged}) {
+    DevBuf* tb[] = {&T->ukey, &T->ufirst, &T->eseq, &T->nfeat, &T->diagC, &T->rinv, &T->svm, &T->tcodes};
+    for (DevBuf* b : tb) release(*b);
+  }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
@@ -2440,8 +2499,9 @@ int gakco_get_stat(const gakco_ctx* c, int key, double* v) {
       return GAKCO_OK;
     case GAKCO_STAT_DEVICE_BYTES: {
       double s = (double)cc->main.bytes();
-      const Train& T = c->train;
-      s += (double)(T.ukey.cap + T.ufirst.cap + T.eseq.cap + T.nfeat.cap + T.diagC.cap + T.rinv.cap);
+      for (const Train* T : {&c->train, &c->train_add, &c->train_merged})
+        s += (double)(T->ukey.cap + T->ufirst.cap + T->eseq.cap + T->nfeat.cap + T->diagC.cap + T->rinv.cap +
+                      T->tcodes.cap);
       std::lock_guard<std::mutex> lk(cc->mu);
       for (auto& sp : cc->slots) s += (double)sp->w.bytes();
       *v = s;

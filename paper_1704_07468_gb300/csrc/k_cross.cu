@@ -316,6 +316,164 @@ k_svm_decision(const CrossParams p, const double* __restrict__ coef, double bias
   if (threadIdx.x == 0) f[t] = red[0] + bias;
 }
 
+// ----------------------------------------------------- merging indexes --
+//
+// Adding sequences to a fitted set (Section 3.2, Fig. 5(c)): the index b of
+// the new sequences (their ids offset by seq_off) is merged into the
+// resident index a.  Per mask the merged features are the union of both
+// key lists in key order, and each feature's entries are a's followed by
+// b's (the new sequences have the larger ids), which is the index a fit of
+// the union builds.  With rb(j) = features of a with a smaller key than
+// b's feature j, ra(i) the same for a's feature i in b, and cb(j) = b's
+// features before j whose key a also holds:
+//   merged position of a's feature i      i + ra(i) - cb(ra(i))
+//   merged position of b's feature j      rb(j) + j - cb(j)   (key not in a)
+//   first entry of a's feature i          a.first(i) + b.first(ra(i))
+//   first entry of b's feature j          a.first(rb(j)) + b.first(j)
+// and an entry of a's feature i moves by b.first(ra(i)).
+
+__device__ __forceinline__ uint32_t lower_bound_key(const uint64_t* __restrict__ k, uint32_t n, uint64_t key) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (k[mid] < key)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Grid (blocks, masks): rb(j), and a flag "a holds the key" in cb (scanned
+// in place by k_merge_scan).
+__global__ void __launch_bounds__(256)
+k_merge_rank(const TrainIndex a, const TrainIndex b, uint32_t* __restrict__ rb, uint32_t* __restrict__ cb) {
+  const uint32_t mu = blockIdx.y;
+  const uint32_t Fa = a.nfeat[mu], Fb = b.nfeat[mu];
+  const uint64_t* __restrict__ ka = a.ukey + (uint64_t)mu * a.stride;
+  const uint64_t ob = (uint64_t)mu * b.stride;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < Fb; j += gridDim.x * blockDim.x) {
+    const uint64_t k = b.ukey[ob + j];
+    const uint32_t r = lower_bound_key(ka, Fa, k);
+    rb[ob + j] = r;
+    cb[ob + j] = (r < Fa && ka[r] == k) ? 1u : 0u;
+  }
+}
+
+// One block per mask: exclusive scan of the flags (their total at cb(Fb)),
+// then the merged feature count and the merged end-of-entries sentinel.
+__global__ void __launch_bounds__(1024)
+k_merge_scan(const TrainIndex a, const TrainIndex b, TrainIndex m, uint32_t* __restrict__ cb) {
+  __shared__ uint32_t sw[33];
+  const uint32_t mu = blockIdx.x;
+  const uint32_t Fb = b.nfeat[mu];
+  uint32_t* __restrict__ c = cb + (uint64_t)mu * b.stride;
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < Fb; base += blockDim.x) {
+    const uint32_t j = base + threadIdx.x;
+    const uint32_t v = j < Fb ? c[j] : 0u;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= (uint32_t)o) incl += t;
+    }
+    if (lane == 31) sw[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      const uint32_t x = lane < nw ? sw[lane] : 0u;
+      uint32_t xi = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, xi, o);
+        if (lane >= (uint32_t)o) xi += t;
+      }
+      if (lane < nw) sw[lane] = xi - x;
+      if (lane == 31) sw[32] = xi;
+    }
+    __syncthreads();
+    if (j < Fb) c[j] = carry + sw[w] + incl - v;
+    carry += sw[32];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    c[Fb] = carry;
+    const uint32_t Fa = a.nfeat[mu];
+    const uint32_t Fm = Fa + Fb - carry;
+    m.nfeat[mu] = Fm;
+    m.ufirst[(uint64_t)mu * m.stride + Fm] =
+        a.ufirst[(uint64_t)mu * a.stride + Fa] + b.ufirst[(uint64_t)mu * b.stride + Fb];
+  }
+}
+
+// Grid (blocks, masks), a warp per 32 consecutive features of a: their
+// merged records, their entries (the warp copies the 32 features' entry
+// span with consecutive lanes on consecutive entries, each entry moved by
+// its feature's shift, found by a search over the lanes), then b's entries
+// of the features both indexes hold.
+__global__ void __launch_bounds__(256)
+k_merge_old(const TrainIndex a, const TrainIndex b, TrainIndex m, const uint32_t* __restrict__ cb,
+            uint32_t seq_off) {
+  const uint32_t mu = blockIdx.y;
+  const uint32_t Fa = a.nfeat[mu], Fb = b.nfeat[mu];
+  const uint64_t oa = (uint64_t)mu * a.stride, ob = (uint64_t)mu * b.stride, om = (uint64_t)mu * m.stride;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t i0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; i0 < Fa; i0 += nwarps * 32) {
+    const uint32_t i = i0 + lane;
+    const uint32_t nv = min(32u, Fa - i0);
+    uint32_t f0 = 0, f1 = 0, sh = 0, rn = 0;
+    uint64_t k = 0;
+    if (lane < nv) {
+      k = a.ukey[oa + i];
+      f0 = a.ufirst[oa + i];
+      f1 = a.ufirst[oa + i + 1];
+      rn = lower_bound_key(b.ukey + ob, Fb, k);
+      sh = b.ufirst[ob + rn];
+      const uint32_t pm = i + rn - cb[ob + rn];
+      m.ukey[om + pm] = k;
+      m.ufirst[om + pm] = f0 + sh;
+    }
+    const uint32_t s0 = __shfl_sync(kFull, f0, 0), s1 = __shfl_sync(kFull, f1, nv - 1);
+    for (uint32_t e0 = s0; e0 < s1; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      uint32_t L = 0;  // last valid lane whose first entry is <= e
+#pragma unroll
+      for (uint32_t step = 16; step >= 1; step >>= 1) {
+        const uint32_t t = __shfl_sync(kFull, f0, L + step);
+        if (L + step < nv && t <= e) L += step;
+      }
+      const uint32_t s = __shfl_sync(kFull, sh, L);
+      if (e < s1) m.eseq[om + e + s] = a.eseq[oa + e];
+    }
+    if (lane < nv && rn < Fb && b.ukey[ob + rn] == k) {
+      const uint32_t q0 = b.ufirst[ob + rn], q1 = b.ufirst[ob + rn + 1];
+      for (uint32_t q = q0; q < q1; ++q) m.eseq[om + f1 + sh + (q - q0)] = b.eseq[ob + q] + (seq_off << 16);
+    }
+  }
+}
+
+// Grid (blocks, masks): b's features whose key a does not hold.
+__global__ void __launch_bounds__(256)
+k_merge_new(const TrainIndex a, const TrainIndex b, TrainIndex m, const uint32_t* __restrict__ rb,
+            const uint32_t* __restrict__ cb, uint32_t seq_off) {
+  const uint32_t mu = blockIdx.y;
+  const uint32_t Fa = a.nfeat[mu], Fb = b.nfeat[mu];
+  const uint64_t oa = (uint64_t)mu * a.stride, ob = (uint64_t)mu * b.stride, om = (uint64_t)mu * m.stride;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < Fb; j += gridDim.x * blockDim.x) {
+    const uint32_t ro = rb[ob + j];
+    const uint64_t k = b.ukey[ob + j];
+    if (ro < Fa && a.ukey[oa + ro] == k) continue;  // placed with a's feature
+    const uint32_t pm = ro + j - cb[ob + j];
+    const uint32_t q0 = b.ufirst[ob + j], q1 = b.ufirst[ob + j + 1];
+    const uint32_t ef = a.ufirst[oa + ro] + q0;
+    m.ukey[om + pm] = k;
+    m.ufirst[om + pm] = ef;
+    for (uint32_t q = q0; q < q1; ++q) m.eseq[om + ef + (q - q0)] = b.eseq[ob + q] + (seq_off << 16);
+  }
+}
+
 }  // namespace
 
 void launch_svm_decision(const CrossParams& p, const double* coef, double bias, int kind, double* f,
@@ -373,6 +531,16 @@ void launch_cross_combine(const CrossParams& p, int32_t* K, double* Khat, cudaSt
   uint64_t blocks = (total + 255) / 256;
   if (blocks > 152ull * 64) blocks = 152ull * 64;
   k_cross_combine<<<(unsigned)blocks, 256, 0, st>>>(p, K, Khat);
+}
+
+void launch_index_merge(const TrainIndex& a, const TrainIndex& b, const TrainIndex& m, uint32_t nmasks,
+                        uint32_t* rb, uint32_t* cb, uint32_t seq_off, cudaStream_t st) {
+  if (nmasks == 0) return;
+  const dim3 grid(32, nmasks);
+  k_merge_rank<<<grid, 256, 0, st>>>(a, b, rb, cb);
+  k_merge_scan<<<nmasks, 1024, 0, st>>>(a, b, m, cb);
+  k_merge_old<<<grid, 256, 0, st>>>(a, b, m, cb, seq_off);
+  k_merge_new<<<grid, 256, 0, st>>>(a, b, m, rb, cb, seq_off);
 }
 
 }  // namespace gk

@@ -159,6 +159,14 @@ void launch_cross_final(bool wide, const SegDesc* segs, const uint32_t* tile_seg
                         const CrossOut& xo, cudaStream_t st);
 int cross_accum_blocks_per_sm(size_t smem);
 void launch_cross_accum(const CrossParams& p, int blocks, size_t smem, cudaStream_t st);
+// Merges training index b (its sequences numbered from seq_off on) into
+// index a, writing index m (stride >= a's + b's windows + 1); rb and cb hold
+// nmasks x b.stride words of scratch.  The four launches: ranks of b's keys
+// in a, a scan of the shared-key flags (also m's feature counts and
+// sentinels), a's features with their entries (and b's entries of shared
+// keys), then b's other features.
+void launch_index_merge(const TrainIndex& a, const TrainIndex& b, const TrainIndex& m, uint32_t nmasks,
+                        uint32_t* rb, uint32_t* cb, uint32_t seq_off, cudaStream_t st);
 void launch_vec_diag(const uint32_t* Cd, uint32_t n, const CrossParams& p, double* rinv,
                      cudaStream_t st);
 void launch_cross_combine(const CrossParams& p, int32_t* K, double* Khat, cudaStream_t st);
