@@ -51,6 +51,18 @@ struct MaskDesc {
   uint8_t ksh[64];              // fold mode: right shift of each kept symbol, in order
 };
 
+// The same in 32-bit arithmetic, for full keys of at most 32 bits (every
+// shift is then below 32 and every run mask fits 32 bits).
+__device__ __forceinline__ uint32_t masked_key32(uint32_t full, const MaskDesc& md) {
+  uint32_t k = 0;
+  if (md.fold) {
+    for (uint32_t j = 0; j < md.nkeep; ++j) k = k * md.fold + ((full >> md.ksh[j]) & md.symmask);
+    return k;
+  }
+  for (uint32_t r = 0; r < md.nruns; ++r) k |= ((full >> md.sr[r]) & (uint32_t)md.msk[r]) << md.sl[r];
+  return k;
+}
+
 __device__ __forceinline__ uint64_t masked_key(uint64_t full,
                                                const MaskDesc& md) {
   uint64_t k = 0;

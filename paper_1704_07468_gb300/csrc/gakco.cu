@@ -1279,8 +1279,8 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
         {
           Bracket b(c, w, "dense_scatter", 1);
           launch_dense_scatter(probs + wv.p0, wv.np, wv.p0, wv.rows, (const DsPack*)(base + p.o_pack),
-                               (const MaskDesc*)(base + p.o_masks), (const uint64_t*)w.fullkey.p, ovf_n,
-                               (DenseOvf*)w.dovf.p, cap, ds);
+                               (const MaskDesc*)(base + p.o_masks), (const uint64_t*)w.fullkey.p,
+                               (uint32_t)(c->g * c->bits), ovf_n, (DenseOvf*)w.dovf.p, cap, ds);
         }
         {
           Bracket b(c, w, "dense_gemm", 1);

@@ -166,7 +166,10 @@ __device__ __forceinline__ uint32_t e4m3_small_value(uint32_t b) {
 // column chunks of kDenseScatterCols.  Counts are gathered in shared memory
 // and each chunk is written out whole (zeros included), so A needs no
 // separate clearing; padded rows come out all zero.  The conversion loop
-// clears the counts it has read, ready for the next chunk.
+// clears the counts it has read, ready for the next chunk.  kNarrow: the
+// full g-mer keys have at most 32 bits (masked keys cut in 32-bit
+// arithmetic).
+template <bool kNarrow>
 __global__ void __launch_bounds__(kScatterThreads, 3)
 k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p0, const DsPack* __restrict__ dsp,
                 const MaskDesc* __restrict__ masks, const uint64_t* __restrict__ fullkey, uint32_t* __restrict__ ovf_n,
@@ -218,7 +221,7 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
     uint32_t mi = nw ? tid / nw : 0, w = nw ? tid - mi * nw : 0;
     for (uint32_t i = tid; i < nw * nmu; i += kScatterThreads) {
       const MaskDesc& md = staged ? smask[mi] : masks[P.mfirst + mu0 + mi];
-      const uint64_t key = masked_key(fk[w], md);
+      const uint64_t key = kNarrow ? (uint64_t)masked_key32((uint32_t)fk[w], md) : masked_key(fk[w], md);
       const uint64_t col = (((uint64_t)(mu0 + mi) << kb) | key) - c0;
       if (col < ncol) atomicAdd(&cnt[col >> 1], 1u << (16 * (uint32_t)(col & 1)));
       w += kScatterThreads;
@@ -626,7 +629,10 @@ int dense_init() {
   cudaError_t e = cudaFuncSetAttribute(k_dense_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)dense_gemm_smem());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_dense_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_dense_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dense_scatter_smem());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_dense_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)dense_scatter_smem());
   return (int)e;
 }
@@ -670,10 +676,15 @@ int dense_encode_tmap(void* out, void* A, uint64_t ld, uint64_t rows) {
 
 void launch_dense_scatter(const DenseProb* d_probs, uint32_t nprobs, uint32_t p0, uint32_t rows,
                           const DsPack* dsp, const MaskDesc* masks, const uint64_t* fullkey,
-                          uint32_t* ovf_n, DenseOvf* ovf, uint32_t ovf_cap, cudaStream_t st) {
+                          uint32_t full_bits, uint32_t* ovf_n, DenseOvf* ovf, uint32_t ovf_cap,
+                          cudaStream_t st) {
   if (nprobs == 0 || rows == 0) return;
-  k_dense_scatter<<<rows, kScatterThreads, dense_scatter_smem(), st>>>(
-      d_probs, nprobs, p0, dsp, masks, fullkey, ovf_n, ovf, ovf_cap);
+  if (full_bits <= 32)
+    k_dense_scatter<true><<<rows, kScatterThreads, dense_scatter_smem(), st>>>(
+        d_probs, nprobs, p0, dsp, masks, fullkey, ovf_n, ovf, ovf_cap);
+  else
+    k_dense_scatter<false><<<rows, kScatterThreads, dense_scatter_smem(), st>>>(
+        d_probs, nprobs, p0, dsp, masks, fullkey, ovf_n, ovf, ovf_cap);
 }
 
 void launch_dense_fix(const DenseProb* d_probs, const uint32_t* ovf_n, const DenseOvf* ovf, uint32_t ovf_cap,

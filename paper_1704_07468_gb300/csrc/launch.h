@@ -212,9 +212,11 @@ int dense_encode_tmap(void* out, void* A, uint64_t ld, uint64_t rows);
 // d_probs: the wave's problems (row0 relative to the wave), p0 the plan
 // index of the first; overflow entries go to ovf[*ovf_n++] while below
 // ovf_cap.
+// full_bits: bits of the packed g-mer keys (g * bits per symbol).
 void launch_dense_scatter(const DenseProb* d_probs, uint32_t nprobs, uint32_t p0, uint32_t rows,
                           const DsPack* dsp, const MaskDesc* masks, const uint64_t* fullkey,
-                          uint32_t* ovf_n, DenseOvf* ovf, uint32_t ovf_cap, cudaStream_t st);
+                          uint32_t full_bits, uint32_t* ovf_n, DenseOvf* ovf, uint32_t ovf_cap,
+                          cudaStream_t st);
 // Macro tiles of kDenseTileWords words: first problem, problem count (the
 // consecutive problems of one dataset and level, whose columns the tile
 // sweeps), I2, J2 (256-row and 256-column blocks, I2 <= J2).
