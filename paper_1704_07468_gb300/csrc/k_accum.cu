@@ -15,7 +15,8 @@
 // same feature with y >= x.  Entries of a feature are sorted by sequence,
 // so y >= x is the tail of the feature's entry range.  A window slot
 // tagged as a one-sequence feature (kSingleTag | count) only adds count^2
-// to the diagonal: summed in registers, added once per item.  The row is then
+// to the diagonal: summed in registers with the diagonal pairs of the other
+// features, added once per item.  The row is then
 // added to the global C_m with coalesced reductions.  Entries of heavy
 // features (kHeavyBit in their feature end) are skipped: the tensor cores
 // add those features' pairs.  Items are handed out
@@ -128,6 +129,15 @@ k_accum(const AccParams p) {
       }
       n_pairs += cnt;
       n_ent += e != kNone;
+      // The range starts at x's own entry (the diagonal pair) unless the
+      // item's columns begin after x.  Every lane of the chunk would add it
+      // to the same counter acc[x] in one instruction; sum c^2 in
+      // registers instead.
+      if (e != kNone && lo == e && cnt > 0) {
+        dsum += c * c;
+        ++lo;
+        --cnt;
+      }
       // Long entry ranges: the whole warp walks one range at a time, lanes on
       // consecutive entries (every atomic instruction fully populated), four
       // loads in flight per lane.  Column indices are clamped to the trash
