@@ -249,7 +249,8 @@ k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
   __shared__ uint32_t sw[kWarps + 1];
   const uint32_t radix = 1u << rbits;
   uint32_t* wc = sh;                     // kWarps x radix running counts
-  uint32_t* gb = sh + kWarps * radix;    // global base of each digit in this tile
+  uint32_t* gb = sh + kWarps * radix;    // global base of each digit in this tile, then
+                                         // that base minus the digit's tile-local start
   uint32_t* ts = gb + radix;             // tile-local start of each digit
   KeyT* skey = (KeyT*)(ts + radix);      // tile in digit order
   uint32_t* sval = (uint32_t*)(skey + kTile);
@@ -263,14 +264,16 @@ k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint64_t beg = (uint64_t)lt * kTile;
   const uint32_t cnt = (uint32_t)min((uint64_t)kTile, sd.G - beg);
+  const KeyT* __restrict__ ki = kin + sd.base + beg;
+  const uint32_t* __restrict__ vi = vin + (kFirst ? sd.win0 : sd.base) + beg;
   KeyT keys[kSortIpt];
   uint32_t vals[kSortIpt];
   uint32_t rk[kSortIpt];
 #pragma unroll
   for (int j = 0; j < kSortIpt; ++j) {
     const uint32_t idx = (uint32_t)w * 32 * kSortIpt + j * 32 + lane;
-    keys[j] = idx < cnt ? kin[sd.base + beg + idx] : (KeyT)0;
-    vals[j] = idx < cnt ? (kFirst ? vin[sd.win0 + beg + idx] : vin[sd.base + beg + idx]) : 0u;
+    keys[j] = idx < cnt ? ki[idx] : (KeyT)0;
+    vals[j] = idx < cnt ? vi[idx] : 0u;
   }
   // Ballots for 7, 8 or all digit bits (the digit width is uniform per launch).
   if (rbits <= 7)
@@ -297,14 +300,16 @@ k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
     ts[dg] = run;
     mysum += run;
   }
-  // Tile-local digit starts: exclusive scan of the totals.
+  // Tile-local digit starts: exclusive scan of the totals, folded into
+  // every warp's offsets and into the global bases.
   uint32_t pre = block_excl_scan(mysum, sw, nullptr);
   for (uint32_t q = 0; q < per; ++q) {
     const uint32_t dg = d0 + q;
     if (dg >= radix) break;
-    const uint32_t c = ts[dg];
-    ts[dg] = pre;
-    pre += c;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) wc[ww * radix + dg] += pre;
+    gb[dg] -= pre;
+    pre += ts[dg];
   }
   __syncthreads();
 #pragma unroll
@@ -312,18 +317,19 @@ k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
     const uint32_t idx = (uint32_t)w * 32 * kSortIpt + j * 32 + lane;
     if (idx < cnt) {
       const uint32_t dg = (uint32_t)(keys[j] >> shift) & (radix - 1);
-      const uint32_t lpos = ts[dg] + wc[w * radix + dg] + rk[j];
+      const uint32_t lpos = wc[w * radix + dg] + rk[j];
       skey[lpos] = keys[j];
       sval[lpos] = vals[j];
     }
   }
   __syncthreads();
+  KeyT* __restrict__ ko = kout + sd.base;
+  uint32_t* __restrict__ vo = vout + sd.base;
   for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
     const KeyT k = skey[i];
-    const uint32_t dg = (uint32_t)(k >> shift) & (radix - 1);
-    const uint64_t pos = sd.base + gb[dg] + (i - ts[dg]);
-    kout[pos] = k;
-    vout[pos] = sval[i];
+    const uint32_t pos = gb[(uint32_t)(k >> shift) & (radix - 1)] + i;
+    ko[pos] = k;
+    vo[pos] = sval[i];
   }
 }
 
