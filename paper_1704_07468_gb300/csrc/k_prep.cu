@@ -345,8 +345,8 @@ __device__ __forceinline__ void rle_load_flags(const SegDesc& sd, uint64_t beg, 
                                                int w, int lane,
                                                const KeyT* __restrict__ keys,
                                                const uint32_t* __restrict__ vals,
-                                               uint32_t (&vv)[kSortIpt], uint32_t (&sq)[kSortIpt],
-                                               uint32_t& ne_bits, uint32_t& nf_bits) {
+                                               uint32_t (&vv)[kSortIpt], uint32_t& ne_bits,
+                                               uint32_t& nf_bits) {
   // Predecessor of the warp's first element.
   const uint64_t first = beg + (uint64_t)w * 32 * kSortIpt;
   KeyT k_prev = 0;
@@ -361,16 +361,15 @@ __device__ __forceinline__ void rle_load_flags(const SegDesc& sd, uint64_t beg, 
     const uint32_t idx = (uint32_t)w * 32 * kSortIpt + j * 32 + lane;
     KeyT kj = 0;
     vv[j] = 0;
-    sq[j] = kNone;
     if (idx < cnt) {
       kj = keys[sd.base + beg + idx];
       vv[j] = vals[sd.base + beg + idx];
-      sq[j] = vv[j] >> 16;
     }
+    const uint32_t sj = vv[j] >> 16;  // the sequence (only read where idx < cnt)
     KeyT kp = __shfl_up_sync(0xffffffffu, kj, 1);
-    uint32_t sp = __shfl_up_sync(0xffffffffu, sq[j], 1);
+    uint32_t sp = __shfl_up_sync(0xffffffffu, sj, 1);
     const KeyT k31 = __shfl_sync(0xffffffffu, kj, 31);
-    const uint32_t s31 = __shfl_sync(0xffffffffu, sq[j], 31);
+    const uint32_t s31 = __shfl_sync(0xffffffffu, sj, 31);
     if (lane == 0) {
       kp = k_prev;
       sp = s_prev;
@@ -378,7 +377,7 @@ __device__ __forceinline__ void rle_load_flags(const SegDesc& sd, uint64_t beg, 
     if (idx < cnt) {
       const bool at0 = beg + idx == 0;
       const bool nf = at0 || kj != kp;
-      const bool ne = nf || sq[j] != sp;
+      const bool ne = nf || sj != sp;
       nf_bits |= (uint32_t)nf << j;
       ne_bits |= (uint32_t)ne << j;
     }
@@ -399,8 +398,8 @@ k_rle_count(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
   const uint64_t beg = (uint64_t)lt * kTile;
   const uint32_t cnt = (uint32_t)min((uint64_t)kTile, sd.G - beg);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t vv[kSortIpt], sq[kSortIpt], ne_bits, nf_bits;
-  rle_load_flags<KeyT>(sd, beg, cnt, w, lane, keys, vals, vv, sq, ne_bits, nf_bits);
+  uint32_t vv[kSortIpt], ne_bits, nf_bits;
+  rle_load_flags<KeyT>(sd, beg, cnt, w, lane, keys, vals, vv, ne_bits, nf_bits);
   uint32_t ce = __popc(ne_bits), cf = __popc(nf_bits);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -473,8 +472,8 @@ k_rle_emit(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_s
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t lt_mask = lanemask_lt();
   const uint32_t* __restrict__ woff = dsp[sd.ds].woff;
-  uint32_t vv[kSortIpt], sq[kSortIpt], ne_bits, nf_bits;
-  rle_load_flags<KeyT>(sd, beg, cnt, w, lane, keys, vals, vv, sq, ne_bits, nf_bits);
+  uint32_t vv[kSortIpt], ne_bits, nf_bits;
+  rle_load_flags<KeyT>(sd, beg, cnt, w, lane, keys, vals, vv, ne_bits, nf_bits);
   uint32_t we = __popc(ne_bits), wf = __popc(nf_bits);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -506,7 +505,7 @@ k_rle_emit(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_s
       ewin[sd.pool + woff[vv[j] >> 16] + (vv[j] & 0xFFFFu)] = ne ? e : kNone;
       if (ne) {
         estart[tb + e] = i;
-        etseq[tb + e] = sq[j];
+        etseq[tb + e] = vv[j] >> 16;
         efid[tb + e] = f;
       }
       if (nf) fstart[tb + f] = e;
@@ -559,7 +558,7 @@ k_rle_final(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
 // entry, first feature's entry, last feature's entry} (tile-local element
 // indices, kNone where absent) lets k_rle_fix complete them.
 template <typename KeyT>
-__global__ void __launch_bounds__(kSortThreads, 3)
+__global__ void __launch_bounds__(kSortThreads, 4)
 k_rle_emit_gram(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg,
                 const KeyT* __restrict__ keys, const uint32_t* __restrict__ vals,
                 const DsPack* __restrict__ dsp, const uint32_t* __restrict__ tcnt,
@@ -578,8 +577,8 @@ k_rle_emit_gram(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ t
   const uint32_t lt_mask = lanemask_lt();
   const uint32_t gt_mask = lane == 31 ? 0u : (0xFFFFFFFFu << (lane + 1));
   const uint32_t* __restrict__ woff = dsp[sd.ds].woff;
-  uint32_t vv[kSortIpt], sq[kSortIpt], ne_bits, nf_bits;
-  rle_load_flags<KeyT>(sd, beg, cnt, w, lane, keys, vals, vv, sq, ne_bits, nf_bits);
+  uint32_t vv[kSortIpt], ne_bits, nf_bits;
+  rle_load_flags<KeyT>(sd, beg, cnt, w, lane, keys, vals, vv, ne_bits, nf_bits);
   {
     uint32_t nen = 0, fe = kNone, le = kNone, ff = kNone, lf = kNone;
 #pragma unroll
@@ -658,7 +657,7 @@ k_rle_emit_gram(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ t
         const uint32_t hb = be & gt_mask;
         const uint32_t nxt = hb ? item0 + __ffs(hb) - 1 : cne;
         const uint32_t cv = nxt == kNone ? 0u : nxt - idx;
-        eseq[sd.pool + e] = (sq[j] << 16) | cv;
+        eseq[sd.pool + e] = (vv[j] & 0xFFFF0000u) | cv;
         const uint32_t hf = bf & gt_mask;
         const uint32_t fend = hf ? re + __popc(be & ((1u << (__ffs(hf) - 1)) - 1u)) : cnf;
         if (fend != kNone) efe[sd.pool + e] = fend;
