@@ -152,6 +152,12 @@ const char *gakco_last_error(const gakco_ctx *ctx);
  * at most 1/16 of the device); features beyond it stay sparse. */
 #define GAKCO_OPT_HEAVY 21
 #define GAKCO_OPT_HEAVY_BYTES 22
+/* Host-buffer outputs: -1 (default) = copy straight into the caller's
+ * buffers when the GPU reaches pageable memory through the host page tables
+ * (the pages are first touched by host threads while the GPU computes),
+ * else through two pinned staging chunks; 0 = always staging; 1 = always
+ * direct. */
+#define GAKCO_OPT_DIRECT_D2H 23
 int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 
 /*

@@ -213,6 +213,11 @@ struct gakco_ctx {
   // feature's entries in thousandths of the dataset's sequences (0: off),
   // and the bytes of their count matrices (capped at create).
   int heavy = 0;
+  // Host outputs: -1 (default) copies straight into the caller's buffers
+  // where the GPU uses the host page tables for pageable memory, else
+  // through pinned staging; 0 = always staging, 1 = always direct.
+  int direct_d2h = -1;
+  bool pageable_ats = false;
   int64_t heavy_bytes = (int64_t)4 << 30;
 
   std::string err;
@@ -369,15 +374,52 @@ struct Xfer {
   size_t bytes;
 };
 
-// Device results -> caller host buffers.  Large outputs go through two
-// pinned 32 MiB staging chunks: the copy engine fills one chunk while
-// several host threads move the previous one into the caller's (pageable)
-// memory, instead of the driver's own small bounce buffers.
-int copy_to_host(Work& w, const std::vector<Xfer>& xs) {
+// First touch of large caller buffers (one write per 4 KiB) by host
+// threads, started before the GPU work and joined before the copies: where
+// the GPU reaches pageable memory through the host page tables, copying
+// into touched pages runs at DMA speed, and the page faults of fresh
+// buffers are taken by these threads while the GPU computes.
+class PageTouch {
+ public:
+  PageTouch(bool on, const std::vector<Xfer>& xs) {
+    size_t total = 0;
+    for (const Xfer& x : xs) total += x.bytes;
+    if (!on || total < ((size_t)8 << 20)) return;
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const unsigned nthr = std::min(16u, hw);
+    for (unsigned t = 0; t < nthr; ++t)
+      th_.emplace_back([xs, t, nthr] {
+        for (const Xfer& x : xs) {
+          const size_t pages = (x.bytes + 4095) / 4096, per = (pages + nthr - 1) / nthr;
+          volatile uint8_t* b = (volatile uint8_t*)x.dst;
+          for (size_t pg = t * per; pg < std::min(pages, (t + 1) * per); ++pg) b[pg * 4096] = 0;
+        }
+      });
+  }
+  void wait() {
+    for (std::thread& t : th_) t.join();
+    th_.clear();
+  }
+  ~PageTouch() { wait(); }
+
+ private:
+  std::vector<std::thread> th_;
+};
+
+// Whether host outputs are copied straight into the caller's buffers.
+bool direct_copies(const gakco_ctx* c) { return c->direct_d2h == 1 || (c->direct_d2h < 0 && c->pageable_ats); }
+
+// Device results -> caller host buffers.  `direct`: one copy per buffer
+// straight into the caller's (touched, see PageTouch) memory.  Otherwise
+// large outputs go through two pinned 32 MiB staging chunks: the copy
+// engine fills one chunk while several host threads move the previous one
+// into the caller's (pageable) memory, instead of the driver's own small
+// bounce buffers.
+int copy_to_host(Work& w, const std::vector<Xfer>& xs, bool direct) {
   size_t total = 0;
   for (const Xfer& x : xs) total += x.bytes;
   cudaError_t e = cudaSuccess;
-  if (total < ((size_t)8 << 20)) {
+  if (direct || total < ((size_t)8 << 20)) {
     for (const Xfer& x : xs)
       if (x.bytes && e == cudaSuccess) e = cudaMemcpyAsync(x.dst, x.src, x.bytes, cudaMemcpyDeviceToHost, w.cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(w.cs);
@@ -1564,8 +1606,6 @@ int gram_host(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64
     D.Nm = D.Nm ? (int32_t*)w.outNm.p + nmoff[d] : nullptr;
   }
   if (e != cudaSuccess) return wcuda(w, e, "copy codes to device");
-  rc = run_gram(c, p, w.cs);
-  if (rc != GAKCO_OK) return rc;
   std::vector<Xfer> xs;
   for (int32_t d = 0; d < nd; ++d) {
     const DsHost& D = p.ds[d];
@@ -1575,7 +1615,12 @@ int gram_host(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64
     if (Khat && Khat[d]) xs.push_back({Khat[d], D.Khat, nn * 8});
     if (Nm && Nm[d]) xs.push_back({Nm[d], D.Nm, (size_t)(c->M + 1) * nn * 4});
   }
-  return copy_to_host(w, xs);
+  const bool direct = direct_copies(c);
+  PageTouch touch(direct, xs);
+  rc = run_gram(c, p, w.cs);
+  touch.wait();
+  if (rc != GAKCO_OK) return rc;
+  return copy_to_host(w, xs, direct);
 }
 
 // --------------------------------------------------------- training index --
@@ -1892,15 +1937,19 @@ int cross_host(gakco_ctx* c, const uint8_t* codes, const int64_t* off, int32_t n
   cudaError_t e = cudaSuccess;
   if (cbytes) e = cudaMemcpyAsync(w.codes.p, codes, cbytes, cudaMemcpyHostToDevice, w.cs);
   if (e != cudaSuccess) return wcuda(w, e, "copy codes to device");
-  if ((rc = enqueue_cross(c, w, (const uint8_t*)w.codes.p, off, nt, K ? (int32_t*)w.outK.p : nullptr,
-                          Khat ? (double*)w.outKhat.p : nullptr, F ? (double*)w.outF.p : nullptr)) != GAKCO_OK)
-    return rc;
-  if ((rc = sync_and_check(c, w)) != GAKCO_OK) return rc;
   std::vector<Xfer> xs;
   if (K && nel) xs.push_back({K, w.outK.p, nel * 4});
   if (Khat && nel) xs.push_back({Khat, w.outKhat.p, nel * 8});
   if (F) xs.push_back({F, w.outF.p, (size_t)nt * 8});
-  return copy_to_host(w, xs);
+  const bool direct = direct_copies(c);
+  PageTouch touch(direct, xs);
+  if ((rc = enqueue_cross(c, w, (const uint8_t*)w.codes.p, off, nt, K ? (int32_t*)w.outK.p : nullptr,
+                          Khat ? (double*)w.outKhat.p : nullptr, F ? (double*)w.outF.p : nullptr)) != GAKCO_OK)
+    return rc;
+  rc = sync_and_check(c, w);
+  touch.wait();
+  if (rc != GAKCO_OK) return rc;
+  return copy_to_host(w, xs, direct);
 }
 
 // ---------------------------------------------------------------- serving --
@@ -2355,6 +2404,10 @@ int gakco_create(int sigma, int g, int k, gakco_ctx** out) {
   if (e == cudaSuccess) e = (cudaError_t)dense_init();
   if (e == cudaSuccess) {
     size_t fr = 0, tot = 0;
+    int ats = 0, pma = 0;
+    if (cudaDeviceGetAttribute(&pma, cudaDevAttrPageableMemoryAccess, c->device) == cudaSuccess &&
+        cudaDeviceGetAttribute(&ats, cudaDevAttrPageableMemoryAccessUsesHostPageTables, c->device) == cudaSuccess)
+      c->pageable_ats = pma == 1 && ats == 1;
     if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && tot > 0)
     {
       c->dense_bytes = std::min<int64_t>(c->dense_bytes, (int64_t)(tot / 4));
@@ -2459,6 +2512,10 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
     case GAKCO_OPT_HEAVY:
       if (v < 0 || v > 1000) return fail(c, GAKCO_E_INVALID, "heavy threshold must be 0..1000 (thousandths)");
       c->heavy = (int)v;
+      break;
+    case GAKCO_OPT_DIRECT_D2H:
+      if (v < -1 || v > 1) return fail(c, GAKCO_E_INVALID, "direct copies must be -1, 0 or 1");
+      c->direct_d2h = (int)v;
       break;
     case GAKCO_OPT_HEAVY_BYTES:
       if (v < 0) return fail(c, GAKCO_E_INVALID, "heavy bytes must be >= 0");
