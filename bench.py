@@ -206,7 +206,7 @@ def run_reference(args):
 NCU_BYTES_PER_UNIT = {
     "accumulate": (4.426e9 / 3.16e9, "pair update"),
     "dense_gemm": (5.644e9 / 1.19e13, "flop"),
-    "dense_scatter": (3.504e9 / 3.46e9, "byte of A"),
+    "dense_scatter": (3.506e9 / 3.46e9, "byte of A"),
 }
 NCU_SOURCE = "profiles/dense_scatter_gemm_accum_dna_4000.md (scaled by units)"
 
