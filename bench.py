@@ -640,8 +640,8 @@ def main():
                     help="also time the K = C_M mode (level-M masks only); 0 to skip")
     ap.add_argument("--dense", type=int, default=None, choices=[0, 1, 2],
                     help="dense-level mode after autotuning: 0 never, 1 cost model, 2 every qualifying level")
-    ap.add_argument("--serve-requests", type=int, default=300)
-    ap.add_argument("--serve-warmup", type=int, default=50)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--dna-sizes", type=lambda v: [int(t) for t in v.split(",")], default=None,
                     help="subset of DNA dataset sizes (small cases for profiling)")
     args = ap.parse_args()
