@@ -236,7 +236,7 @@ def kernel_rooflines(timings, work, peaks, sm_count):
         elif name == "sort_pass" and work["sort_bytes"] > 0:
             a = work["sort_bytes"] / sec / 1e9
             e = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                 "kernel": "k_sort_upsweep + k_sort_scan + k_sort_downsweep"}
+                 "kernel": "k_upsweep + k_digit_scan + k_digit_base + k_downsweep"}
         elif name == "dense_gemm" and work["dense_flops"] > 0:
             a = work["dense_flops"] / sec / 1e12
             e = {"bound": "tensor", "achieved": a, "peak": tensor_peak, "unit": "TFLOP/s",

@@ -106,7 +106,7 @@ struct Work {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_heavy = nullptr;
   DevBuf fullkey, wid, ewin, eseq, efe, keyA, keyB, valA, valB, hist, tcnt, segtot, estart,
       etseq, efid, fstart, tables, codes, outK, outKhat, outNm, rinv, status, Cplain, Cacc, ea, eb,
-      Cd, Cx, Adense, dmaxc, dovf, outF, trec, Aheavy, hctr, hlist;
+      Cd, Cx, Adense, dmaxc, dovf, outF, trec, Aheavy, hctr, hlist, dtot;
   void* h_tables = nullptr;
   size_t h_tables_cap = 0;
   void* h_status = nullptr;
@@ -125,7 +125,7 @@ struct Work {
     return {&fullkey, &wid, &ewin,   &eseq,  &efe,  &keyA,  &keyB,  &valA,    &valB,
             &hist,    &tcnt,    &segtot, &estart, &etseq, &efid, &fstart, &tables, &codes,
             &outK,    &outKhat, &outNm,  &rinv,  &status, &Cplain, &Cacc, &ea,    &eb,
-            &Cd,      &Cx,      &Adense, &dmaxc,  &dovf,  &outF, &trec, &Aheavy, &hctr, &hlist};
+            &Cd,      &Cx,      &Adense, &dmaxc,  &dovf,  &outF, &trec, &Aheavy, &hctr, &hlist, &dtot};
   }
   size_t bytes() {
     size_t s = 0;
@@ -1037,6 +1037,7 @@ int ensure_sort_buffers(gakco_ctx* c, Work& w, const Plan& p) {
   ENSURE(valA, ce * 4);
   ENSURE(valB, ce * 4);
   ENSURE(hist, p.max_hist * 4);
+  ENSURE(dtot, (p.max_chunk_nseg << kMaxRadixBits) * 4);
   ENSURE(tcnt, p.max_chunk_tiles * 8);
   ENSURE(trec, p.max_chunk_tiles * kRecWords * 4);
   ENSURE(segtot, p.max_chunk_nseg * 8);
@@ -1234,10 +1235,10 @@ void enqueue_chunk(gakco_ctx* c, Work& w, const Plan& p, const Chunk& ch, Tail t
   const uint32_t* vin = (const uint32_t*)w.wid.p;  // first-pass payload: window ids
   int cur = 0;
   for (size_t q = 0; q < ch.passes.size(); ++q) {
-    Bracket b(c, w, "sort_pass", 3);
+    Bracket b(c, w, "sort_pass", 4);
     launch_sort_pass(ch.wide, q == 0, segs, ch.nseg, tseg, ch.ntiles, masks,
                      (const uint64_t*)w.fullkey.p, kin, vin, kbuf[cur], vbuf[cur],
-                     (uint32_t*)w.hist.p, ch.passes[q].first, ch.passes[q].second, w.cs);
+                     (uint32_t*)w.hist.p, (uint32_t*)w.dtot.p, ch.passes[q].first, ch.passes[q].second, w.cs);
     kin = kbuf[cur];
     vin = vbuf[cur];
     cur ^= 1;

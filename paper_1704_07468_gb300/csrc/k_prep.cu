@@ -155,31 +155,52 @@ k_upsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_se
     hist[sd.hist + (uint64_t)i * sd.ntiles + lt] = sh[i];
 }
 
-// Exclusive scan of each segment's digit-major counters, in place.
+// Grid (segments, digits): exclusive scan of one digit's per-tile counts
+// of one segment (contiguous in the digit-major layout), in place; the
+// digit's total to dtot[segment * radix + digit].
 __global__ void __launch_bounds__(kSortThreads)
-k_seg_scan(const SegDesc* __restrict__ segs, uint32_t* __restrict__ hist,
-           int rbits) {
+k_digit_scan(const SegDesc* __restrict__ segs, uint32_t* __restrict__ hist, uint32_t* __restrict__ dtot,
+             int rbits) {
   __shared__ uint32_t sw[kWarps + 1];
-  const SegDesc sd = segs[blockIdx.x];
-  const uint64_t len = ((uint64_t)1 << rbits) * sd.ntiles;
-  uint32_t* __restrict__ h = hist + sd.hist;
+  const uint32_t s = blockIdx.x, d = blockIdx.y;
+  const SegDesc sd = segs[s];
+  uint32_t* __restrict__ h = hist + sd.hist + (uint64_t)d * sd.ntiles;
   uint32_t carry = 0;
-  for (uint64_t b = 0; b < len; b += (uint64_t)kSortThreads * 4) {
-    uint32_t v[4], s = 0;
+  for (uint32_t b = 0; b < sd.ntiles; b += kSortThreads * 4) {
+    uint32_t v[4], sum = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      uint64_t i = b + (uint64_t)threadIdx.x * 4 + q;
-      v[q] = i < len ? h[i] : 0;
-      s += v[q];
+      const uint32_t i = b + threadIdx.x * 4 + q;
+      v[q] = i < sd.ntiles ? h[i] : 0u;
+      sum += v[q];
     }
     uint32_t tot;
-    uint32_t pre = block_excl_scan(s, sw, &tot) + carry;
+    uint32_t pre = block_excl_scan(sum, sw, &tot) + carry;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      uint64_t i = b + (uint64_t)threadIdx.x * 4 + q;
-      if (i < len) h[i] = pre;
+      const uint32_t i = b + threadIdx.x * 4 + q;
+      if (i < sd.ntiles) h[i] = pre;
       pre += v[q];
     }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) dtot[((uint64_t)s << rbits) + d] = carry;
+}
+
+// One block per segment: the digit totals become the digits' starts
+// (exclusive scan, in place).
+__global__ void __launch_bounds__(kSortThreads)
+k_digit_base(uint32_t* __restrict__ dtot, int rbits) {
+  __shared__ uint32_t sw[kWarps + 1];
+  const uint32_t radix = 1u << rbits;
+  uint32_t* __restrict__ t = dtot + ((uint64_t)blockIdx.x << rbits);
+  uint32_t carry = 0;
+  for (uint32_t b = 0; b < radix; b += kSortThreads) {
+    const uint32_t i = b + threadIdx.x;
+    const uint32_t v = i < radix ? t[i] : 0u;
+    uint32_t tot;
+    const uint32_t pre = block_excl_scan(v, sw, &tot) + carry;
+    if (i < radix) t[i] = pre;
     carry += tot;
   }
 }
@@ -251,7 +272,7 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4)
 k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg,
             const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin,
             KeyT* __restrict__ kout, uint32_t* __restrict__ vout,
-            const uint32_t* __restrict__ hist, int shift, int rbits) {
+            const uint32_t* __restrict__ hist, const uint32_t* __restrict__ dbase, int shift, int rbits) {
   extern __shared__ __align__(16) uint32_t sh[];
   __shared__ uint32_t sw[kWarps + 1];
   const uint32_t radix = 1u << rbits;
@@ -262,11 +283,12 @@ k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
   KeyT* skey = (KeyT*)(ts + radix);      // tile in digit order
   uint32_t* sval = (uint32_t*)(skey + kTile);
   const uint32_t t = blockIdx.x;
-  const SegDesc sd = segs[tile_seg[t]];
+  const uint32_t sx = tile_seg[t];
+  const SegDesc sd = segs[sx];
   const uint32_t lt = t - sd.tile0;
   for (uint32_t i = threadIdx.x; i < kWarps * radix; i += blockDim.x) wc[i] = 0;
   for (uint32_t i = threadIdx.x; i < radix; i += blockDim.x)
-    gb[i] = hist[sd.hist + (uint64_t)i * sd.ntiles + lt];
+    gb[i] = hist[sd.hist + (uint64_t)i * sd.ntiles + lt] + dbase[((uint64_t)sx << rbits) + i];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint64_t beg = (uint64_t)lt * kTile;
@@ -728,9 +750,10 @@ void sort_pass_t(bool first, const SegDesc* segs, uint32_t nsegs,
                  const uint32_t* tile_seg, uint32_t ntiles,
                  const MaskDesc* masks, const uint64_t* fullkey,
                  void* kin, const uint32_t* vin, void* kout,
-                 uint32_t* vout, uint32_t* hist, int shift, int rbits,
+                 uint32_t* vout, uint32_t* hist, uint32_t* dtot, int shift, int rbits,
                  cudaStream_t st) {
   const size_t radix = (size_t)1 << rbits;
+  const dim3 scan_grid(nsegs, (unsigned)radix);
   const size_t up_smem = radix * 4;
   const size_t dn_smem = downsweep_smem(rbits, (int)sizeof(KeyT));
   KeyT* ki = (KeyT*)kin;
@@ -738,15 +761,17 @@ void sort_pass_t(bool first, const SegDesc* segs, uint32_t nsegs,
   if (first) {
     k_upsweep<KeyT, true><<<ntiles, kSortThreads, up_smem, st>>>(segs, tile_seg, masks, fullkey, ki,
                                                                   hist, shift, rbits);
-    k_seg_scan<<<nsegs, kSortThreads, 0, st>>>(segs, hist, rbits);
+    k_digit_scan<<<scan_grid, kSortThreads, 0, st>>>(segs, hist, dtot, rbits);
+    k_digit_base<<<nsegs, kSortThreads, 0, st>>>(dtot, rbits);
     k_downsweep<KeyT, true><<<ntiles, kSortThreads, dn_smem, st>>>(segs, tile_seg, ki, vin, ko, vout,
-                                                                    hist, shift, rbits);
+                                                                    hist, dtot, shift, rbits);
   } else {
     k_upsweep<KeyT, false><<<ntiles, kSortThreads, up_smem, st>>>(segs, tile_seg, masks, fullkey, ki,
                                                                    hist, shift, rbits);
-    k_seg_scan<<<nsegs, kSortThreads, 0, st>>>(segs, hist, rbits);
+    k_digit_scan<<<scan_grid, kSortThreads, 0, st>>>(segs, hist, dtot, rbits);
+    k_digit_base<<<nsegs, kSortThreads, 0, st>>>(dtot, rbits);
     k_downsweep<KeyT, false><<<ntiles, kSortThreads, dn_smem, st>>>(segs, tile_seg, ki, vin, ko, vout,
-                                                                     hist, shift, rbits);
+                                                                     hist, dtot, shift, rbits);
   }
 }
 
@@ -801,14 +826,14 @@ void launch_sort_pass(bool wide, bool first, const SegDesc* segs,
                       uint32_t ntiles, const MaskDesc* masks,
                       const uint64_t* fullkey, void* kin,
                       const uint32_t* vin, void* kout, uint32_t* vout,
-                      uint32_t* hist, int shift, int rbits, cudaStream_t st) {
+                      uint32_t* hist, uint32_t* dtot, int shift, int rbits, cudaStream_t st) {
   if (ntiles == 0) return;
   if (wide)
     sort_pass_t<uint64_t>(first, segs, nsegs, tile_seg, ntiles, masks, fullkey, kin, vin, kout,
-                          vout, hist, shift, rbits, st);
+                          vout, hist, dtot, shift, rbits, st);
   else
     sort_pass_t<uint32_t>(first, segs, nsegs, tile_seg, ntiles, masks, fullkey, kin, vin, kout,
-                          vout, hist, shift, rbits, st);
+                          vout, hist, dtot, shift, rbits, st);
 }
 
 void launch_rle_head(bool wide, const SegDesc* segs, uint32_t nsegs,

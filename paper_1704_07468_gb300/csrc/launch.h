@@ -27,13 +27,14 @@ void launch_pack(const DsPack* d_ds, uint32_t nds, uint32_t nseq_total,
 // pass the keys are cut out of the full g-mer keys (`fullkey`) into `kin`
 // (which must not alias `kout`) and the payload is the window id read from
 // `vin` (the packing kernel's output, indexed by global window); later
-// passes read kin/vin.
+// passes read kin/vin.  dtot: nsegs << rbits words of scratch (each
+// segment's digit totals, then the digits' starts).
 void launch_sort_pass(bool wide, bool first, const SegDesc* segs,
                       uint32_t nsegs, const uint32_t* tile_seg,
                       uint32_t ntiles, const MaskDesc* masks,
                       const uint64_t* fullkey, void* kin,
                       const uint32_t* vin, void* kout, uint32_t* vout,
-                      uint32_t* hist, int shift, int rbits, cudaStream_t st);
+                      uint32_t* hist, uint32_t* dtot, int shift, int rbits, cudaStream_t st);
 
 // Run-length pass over sorted segments: entries (feature, sequence, count)
 // and features (runs of equal keys).  Writes, per segment, ewin / eseq /

@@ -190,6 +190,7 @@ extern "C" int gakco_gram_device_noalloc(int sigma, int g, int k, const uint8_t*
   const size_t o_valA = take(G * 4);
   const size_t o_valB = take(G * 4);
   const size_t o_hist = take(((size_t)1 << kRadixBits) * ntiles * 4);
+  const size_t o_dtot = take(((size_t)1 << kRadixBits) * 4);
   const size_t o_tcnt = take((size_t)ntiles * 8);
   const size_t o_segtot = take(64);
   const size_t o_estart = take((G + 2) * 4);
@@ -316,7 +317,7 @@ extern "C" int gakco_gram_device_noalloc(int sigma, int g, int k, const uint8_t*
         const int nb = rb < kbits - shift ? rb : kbits - shift;
         launch_sort_pass(w, q == 0, d_segs + mu, 1, d_tiles, ntiles, d_masks,
                          (const uint64_t*)(S + o_fullkey), kin, vin, kbuf[cur], vbuf[cur],
-                         (uint32_t*)(S + o_hist), shift, nb, st);
+                         (uint32_t*)(S + o_hist), (uint32_t*)(S + o_dtot), shift, nb, st);
         kin = kbuf[cur];
         vin = vbuf[cur];
         cur ^= 1;
