@@ -367,7 +367,7 @@ def run_extend(pkg, sigma, g, k, sets, add=100):
             "extend_ms": 1000 * t_ext, "fresh_gram_ms": 1000 * t_full,
             "equal_to_fresh_rows": bool(np.array_equal(rows["K"], full["K"][cut:]) and
                                         np.array_equal(rows["Khat"], full["Khat"][cut:])),
-            "timing": "wall clock through the host-buffer C ABI, copies and the refit on the union included"}
+            "timing": "wall clock through the host-buffer C ABI, copies and the merge of the new sequences into the index included"}
 
 
 def run_nsweep(pkg):
