@@ -1101,6 +1101,14 @@ int fill_dense(gakco_ctx* c, Work& w, Plan& p, Tables& t) {
     q.mcount = h.mcount;
     q.key_bits = h.key_bits;
     q.row0 = h.row0;
+    if (!h.heavy) {
+      const std::vector<uint32_t>& wo = p.ds[h.ds].woff;
+      uint64_t wmax = 0;
+      for (size_t x = 0; x + 1 < wo.size(); ++x) wmax = std::max<uint64_t>(wmax, wo[x + 1] - wo[x]);
+      const std::vector<uint32_t> lf = level_firsts(c);
+      const uint64_t wm = wmax * (uint64_t)(lf[h.level + 1] - lf[h.level]);
+      q.wmasks = wm <= 0xFFFFFFFFull ? (uint32_t)wm : 0u;
+    }
     memcpy(t.buf.data() + p.o_dprobs + i * sizeof(DenseProb), &q, sizeof q);
     const int r = dense_encode_tmap(t.buf.data() + p.o_tmaps + i * kDenseTmapBytes, q.A, h.ld, h.n_pad);
     if (r != 0) return wfail(w, GAKCO_E_CUDA, "TMA descriptor of dense problem %zu failed (%d)", i, r);

@@ -15,7 +15,8 @@
 // while they stay below 2^24, so the GEMM closes an accumulation "round"
 // and adds it into the int32 C every floor((2^24 - 1) / (128 maxD0^2))
 // stages of 128 columns, maxD0 being the largest D0 the scatter kernel
-// wrote.  A count c > 16 is also appended to an overflow list, and the fix
+// wrote -- or once per macro tile when maxD0 times a row's largest possible
+// sum (windows x masks) stays below 2^24, which bounds every partial sum.  A count c > 16 is also appended to an overflow list, and the fix
 // kernel adds the exact difference A A^T - D0 D0^T, which is nonzero only
 // in rows and columns of overflowing sequences:
 //   (x, y), y without overflow at the column:  (c_x - 16) D0(y)
@@ -131,10 +132,14 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// Stages (128 columns each) per exact accumulation round.
-__device__ __forceinline__ uint32_t stages_per_round(const uint32_t* maxc, uint32_t nk) {
+// Stages (128 columns each) per exact accumulation round.  Every partial
+// sum of a (x, y) entry is at most sum_k A[x,k] A[y,k] <= maxc * sum_k
+// A[y,k] <= maxc * wmasks (each window of y adds at most one to one column
+// of each mask), so when that stays below 2^24 the whole macro tile is one
+// round; otherwise a stage adds at most 128 maxc^2.
+__device__ __forceinline__ uint32_t stages_per_round(const uint32_t* maxc, uint32_t nk, uint32_t wmasks) {
   const uint32_t mc = *(const volatile uint32_t*)maxc;
-  if (mc == 0) return nk > 0 ? nk : 1;
+  if (mc == 0 || (wmasks != 0 && (uint64_t)mc * wmasks < (1ull << 24))) return nk > 0 ? nk : 1;
   uint64_t s = (uint64_t)((1u << 24) - 1) / (128ull * mc * mc);
   if (s < 1) s = 1;
   return (uint32_t)(s < nk ? s : nk);
@@ -393,7 +398,7 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
         const uint32_t st = row_halves(I2, probs[pa].n);
         uint32_t total = 0;
         for (uint32_t p = pa; p < pa + pn; ++p) total += (uint32_t)(probs[p].ld / 128);
-        const uint32_t spr = stages_per_round(probs[pa].maxc, total);
+        const uint32_t spr = stages_per_round(probs[pa].maxc, total, probs[pa].wmasks);
         uint32_t kr = 0;  // stages into the current round
         for (uint32_t p = pa; p < pa + pn && !stop; ++p) {
           const uint32_t nk = (uint32_t)(probs[p].ld / 128);
@@ -454,7 +459,7 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
       const uint32_t st = row_halves(I2, n);
       uint32_t total = 0;
       for (uint32_t p = pa; p < pa + pn; ++p) total += (uint32_t)(probs[p].ld / 128);
-      const uint32_t spr = stages_per_round(probs[pa].maxc, total);
+      const uint32_t spr = stages_per_round(probs[pa].maxc, total, probs[pa].wmasks);
       const uint32_t nr = (total + spr - 1) / spr;
       uint32_t* C = probs[pa].C;
       for (uint32_t r = 0; r < nr; ++r, ++round) {

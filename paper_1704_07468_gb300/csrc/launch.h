@@ -195,7 +195,8 @@ struct DenseProb {
   uint32_t mfirst, mcount;
   uint32_t key_bits;    // (g - m) * b
   uint32_t row0;        // first row of the problem in its wave's scatter grid
-  uint32_t pad;
+  uint32_t wmasks;      // windows of the longest sequence x masks of the (dataset, level):
+                        // a row of A sums to at most this over a macro tile (0 = unknown)
 };
 
 // A count above 16: problem (plan-wide index), row, column, count.
