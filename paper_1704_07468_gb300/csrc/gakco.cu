@@ -509,6 +509,8 @@ struct DenseHost {
   uint32_t ds, level, mfirst, mcount, n, n_pad, key_bits, row0;
   uint64_t ld, a_off;  // columns; byte offset of A in the A buffer
   uint32_t hidx = 0;   // heavy problem index (when heavy)
+  uint32_t nsib = 0;   // problems of its (dataset, level)
+  bool sole = false;   // its wave's run holds every problem of the (dataset, level)
   bool heavy = false;  // heavy-feature matrix: ld is its column capacity, the
                        // columns in use are set on the device
 };
@@ -833,6 +835,7 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
         h.n_pad = n_pad;
         h.key_bits = (uint32_t)kb;
         h.ld = align_up((size_t)h.mcount * S, 128);
+        h.nsib = ng;
         p.dprobs.push_back(h);
       }
     }
@@ -858,6 +861,7 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
     for (uint32_t g0 = wv.p0; g0 < wv.p0 + wv.np;) {
       uint32_t g1 = g0 + 1;
       while (g1 < wv.p0 + wv.np && p.dprobs[g1].ds == p.dprobs[g0].ds && p.dprobs[g1].level == p.dprobs[g0].level) ++g1;
+      for (uint32_t j = g0; j < g1; ++j) p.dprobs[j].sole = (g1 - g0) == p.dprobs[j].nsib;
       const DenseHost& h = p.dprobs[g0];
       double stages = 0;
       for (uint32_t j = g0; j < g1; ++j) stages += (double)(p.dprobs[j].ld / 128);
@@ -1101,6 +1105,7 @@ int fill_dense(gakco_ctx* c, Work& w, Plan& p, Tables& t) {
     q.mcount = h.mcount;
     q.key_bits = h.key_bits;
     q.row0 = h.row0;
+    q.sole = h.sole ? 1u : 0u;
     if (!h.heavy) {
       const std::vector<uint32_t>& wo = p.ds[h.ds].woff;
       uint64_t wmax = 0;

@@ -461,6 +461,9 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
       for (uint32_t p = pa; p < pa + pn; ++p) total += (uint32_t)(probs[p].ld / 128);
       const uint32_t spr = stages_per_round(probs[pa].maxc, total, probs[pa].wmasks);
       const uint32_t nr = (total + spr - 1) / spr;
+      // One round and no other writer: the tile's C entries are still zero,
+      // so plain (vector) stores replace the atomic adds.
+      const bool store = nr == 1 && probs[pa].sole != 0;
       uint32_t* C = probs[pa].C;
       for (uint32_t r = 0; r < nr; ++r, ++round) {
         if (!__all_sync(0xffffffffu, bar_wait(&tfull, round & 1, &abort_flag))) {
@@ -490,11 +493,23 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
                 : "r"(a));
             asm volatile("tcgen05.wait::ld.sync.aligned;");
             if (row < n) {
+              const uint32_t c0 = col0 + cb;
+              uint32_t* dst = crow + c0;
+              if (!store) {
 #pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                const uint32_t col = col0 + cb + j;
-                const uint32_t val = (uint32_t)__uint_as_float(v[j]);
-                if (col < n && col >= row && val) atomicAdd(&crow[col], val);
+                for (int j = 0; j < 32; ++j) {
+                  const uint32_t val = (uint32_t)__uint_as_float(v[j]);
+                  if (c0 + j < n && c0 + j >= row && val) atomicAdd(&dst[j], val);
+                }
+              } else if (c0 >= row && c0 + 32 <= n && ((uintptr_t)dst & 15u) == 0) {
+#pragma unroll
+                for (int j = 0; j < 32; j += 4)
+                  *(uint4*)(dst + j) = make_uint4((uint32_t)__uint_as_float(v[j]), (uint32_t)__uint_as_float(v[j + 1]),
+                                                  (uint32_t)__uint_as_float(v[j + 2]), (uint32_t)__uint_as_float(v[j + 3]));
+              } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                  if (c0 + j < n && c0 + j >= row) dst[j] = (uint32_t)__uint_as_float(v[j]);
               }
             }
           }

@@ -197,6 +197,9 @@ struct DenseProb {
   uint32_t row0;        // first row of the problem in its wave's scatter grid
   uint32_t wmasks;      // windows of the longest sequence x masks of the (dataset, level):
                         // a row of A sums to at most this over a macro tile (0 = unknown)
+  uint32_t sole;        // 1: a macro tile of this problem is the only writer of its C entries
+                        // until the GEMM ends (its run covers every problem of the level)
+  uint32_t pad;
 };
 
 // A count above 16: problem (plan-wide index), row, column, count.
