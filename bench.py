@@ -205,7 +205,7 @@ def run_reference(args):
 # bench by its units; traffic grows in proportion to them.
 NCU_BYTES_PER_UNIT = {
     "accumulate": (4.426e9 / 3.16e9, "pair update"),
-    "dense_gemm": (5.644e9 / 1.19e13, "flop"),
+    "dense_gemm": (3.534e9 / 1.19e13, "flop"),
     "dense_scatter": (3.506e9 / 3.46e9, "byte of A"),
 }
 NCU_SOURCE = "profiles/dense_scatter_gemm_accum_dna_4000.md (scaled by units)"
