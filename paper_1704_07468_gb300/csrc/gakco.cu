@@ -387,14 +387,18 @@ class PageTouch {
     if (!on || total < ((size_t)8 << 20)) return;
     const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
     const unsigned nthr = std::min(16u, hw);
-    for (unsigned t = 0; t < nthr; ++t)
-      th_.emplace_back([xs, t, nthr] {
-        for (const Xfer& x : xs) {
-          const size_t pages = (x.bytes + 4095) / 4096, per = (pages + nthr - 1) / nthr;
-          volatile uint8_t* b = (volatile uint8_t*)x.dst;
-          for (size_t pg = t * per; pg < std::min(pages, (t + 1) * per); ++pg) b[pg * 4096] = 0;
-        }
-      });
+    try {
+      for (unsigned t = 0; t < nthr; ++t)
+        th_.emplace_back([xs, t, nthr] {
+          for (const Xfer& x : xs) {
+            const size_t pages = (x.bytes + 4095) / 4096, per = (pages + nthr - 1) / nthr;
+            volatile uint8_t* b = (volatile uint8_t*)x.dst;
+            for (size_t pg = t * per; pg < std::min(pages, (t + 1) * per); ++pg) b[pg * 4096] = 0;
+          }
+        });
+    } catch (...) {
+      // No threads to spare: the copies then take the page faults themselves.
+    }
   }
   void wait() {
     for (std::thread& t : th_) t.join();
@@ -459,7 +463,12 @@ int copy_to_host(Work& w, const std::vector<Xfer>& xs, bool direct) {
     std::vector<std::thread> th;
     for (unsigned t = 1; t < nthr; ++t) {
       const size_t a = std::min(n, t * part), b = std::min(n, (t + 1) * part);
-      if (a < b) th.emplace_back([dst, slot, a, b] { memcpy(dst + a, slot + a, b - a); });
+      if (a >= b) continue;
+      try {
+        th.emplace_back([dst, slot, a, b] { memcpy(dst + a, slot + a, b - a); });
+      } catch (...) {
+        memcpy(dst + a, slot + a, b - a);  // no thread to spare: copy here
+      }
     }
     memcpy(dst, slot, std::min(n, part));
     for (std::thread& t : th) t.join();
@@ -2153,7 +2162,11 @@ int start_serving(gakco_ctx* c) {
     c->slots.push_back(std::move(s));
   }
   c->stopping = false;
-  c->dispatcher = std::thread(dispatcher_main, c);
+  try {
+    c->dispatcher = std::thread(dispatcher_main, c);
+  } catch (...) {
+    return fail(c, GAKCO_E_INTERNAL, "could not start the serving thread");
+  }
   c->serving = true;
   return GAKCO_OK;
 }
