@@ -58,3 +58,14 @@ def test_null_context_is_rejected(lib):
     assert lib.gakco_gram(None, None, None, 0, None, None, None) == -1
     assert lib.gakco_set_option(None, 1, 0) == -1
     lib.gakco_destroy(None)  # no-op
+
+
+def test_option_and_stat_numbers_match_the_header():
+    """The binding's option and statistic keys are the header's values."""
+    text = open(HEADER).read()
+    opts = {m.group(1).lower(): int(m.group(2))
+            for m in re.finditer(r"#define GAKCO_OPT_(\w+)\s+(\d+)", text)}
+    stats = {m.group(1).lower(): int(m.group(2))
+             for m in re.finditer(r"#define GAKCO_STAT_(\w+)\s+(\d+)", text)}
+    assert opts == pkg.OPT
+    assert stats == pkg.STAT
