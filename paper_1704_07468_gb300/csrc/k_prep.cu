@@ -587,7 +587,7 @@ k_rle_final(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
 // entry, first feature's entry, last feature's entry} (tile-local element
 // indices, kNone where absent) lets k_rle_fix complete them.
 template <typename KeyT>
-__global__ void __launch_bounds__(kSortThreads, 4)
+__global__ void __launch_bounds__(kSortThreads, 5)
 k_rle_emit_gram(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg,
                 const KeyT* __restrict__ keys, const uint32_t* __restrict__ vals,
                 const DsPack* __restrict__ dsp, const uint32_t* __restrict__ tcnt,
