@@ -376,9 +376,7 @@ def run_nsweep(pkg):
     out = []
     for name, sigma, g, k in (("dna_sigma5", 5, 10, 6), ("protein", 20, 8, 4), ("text", 36, 8, 5)):
         for n in (100, 250, 500, 750):
-            rng = np.random.default_rng(1000 + n)
-            codes = rng.integers(0, sigma, size=n * 100).astype(np.uint8)
-            off = np.arange(0, n * 100 + 1, 100, dtype=np.int64)
+            codes, off = synth.fixed_length(1000 + n, n, 100, sigma)
             with pkg.gakco_create(sigma, g, k) as ctx:
                 ctx.set_option("dense", 1)
                 ctx.gram(codes, off)

@@ -158,6 +158,22 @@ const char *gakco_last_error(const gakco_ctx *ctx);
  * else through two pinned staging chunks; 0 = always staging; 1 = always
  * direct. */
 #define GAKCO_OPT_DIRECT_D2H 23
+/* Exact accumulation rounds of the dense GEMM.  Its f32 tensor-memory
+ * accumulators hold integer sums of products of counts; a round is closed
+ * (and added into the int32 C_m) before any partial sum can pass this bound.
+ * Default and maximum 2^24 - 1, where f32 still holds every integer; the
+ * test suite drives real partial sums just below it and checks them
+ * against the oracle.  Smaller values only split the work into more rounds
+ * (results unchanged, slower): the tests use them to run the multi-round
+ * path. */
+#define GAKCO_OPT_DENSE_ROUND_SUM 24
+/* Limit, in GPU clock cycles, of each wait between the dense GEMM's roles
+ * (TMA loads, MMA issue, epilogue) before the call gives up with
+ * GAKCO_E_TIMEOUT (0 = default, about 2 s).  The wind-down after a timeout
+ * (waiting for copies and MMAs already issued) keeps the default limit.
+ * For tests of the timeout path: a limit of a few cycles makes an ordinary
+ * call run out; the context stays usable. */
+#define GAKCO_OPT_DENSE_WAIT_CYCLES 25
 int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 
 /*
@@ -371,12 +387,22 @@ int gakco_submit_svm(gakco_ctx *ctx, const uint8_t *codes,
  * plus the limits of gakco_gram.  Larger inputs return GAKCO_E_OVERFLOW
  * with a message in `err` (caller buffer of `err_len` bytes, may be NULL).
  *
- * The first call on a device, with that device current, looks up the
- * device address of the static array (cudaGetSymbolAddress); make that
- * first call before any stream capture.  Work is ordered on `stream` and
- * the call returns after it completes.  Every call uses the same static
- * arrays: calls that overlap on the GPU (other streams, other host threads)
- * race and corrupt each other's results, so issue one at a time.
+ * Every call made outside stream capture looks up the device address of
+ * the static array on the current device (cudaGetSymbolAddress, which
+ * allocates nothing) and sets the kernels' attributes, so a device reset
+ * leaves no stale address; a call made while `stream` is capturing uses the
+ * address of the last call outside capture on that device, so make the
+ * first call on each device before any stream capture (otherwise the call
+ * returns GAKCO_E_INVALID).  Work is ordered on `stream` and the call
+ * returns after it completes.
+ *
+ * Every call uses the same static arrays: the device array keeps the last
+ * call's contents (everything that must start at zero is cleared by each
+ * call), and the host tables are shared by every device.  Calls whose work
+ * overlaps on the GPU race and corrupt each other's results.  The entry
+ * point therefore holds one process-wide lock, for all devices, from start
+ * to finish, so concurrent callers in one process (other host threads, on
+ * the same or another GPU) are serialised.
  */
 int gakco_gram_device_noalloc(int sigma, int g, int k, const uint8_t *codes,
                               const int64_t *offsets, int32_t n, int32_t *K,

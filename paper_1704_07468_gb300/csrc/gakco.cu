@@ -209,6 +209,8 @@ struct gakco_ctx {
   int kernel_only = 0;  // 1: compute level M alone when N_m is not requested (K = C_M)
   int overlap = 1;      // 1: dense and sparse levels of a Gram call run on two streams
   int dense_sms = 0;    // CTAs of the dense GEMM (0: one per SM)
+  int64_t dense_round_sum = kDenseExactSum;  // bound on a GEMM round's partial sums
+  int64_t dense_wait_cycles = 0;             // GEMM role-wait limit (0: default)
   // Heavy features of sparse levels go to the tensor cores: threshold on a
   // feature's entries in thousandths of the dataset's sequences (0: off),
   // and the bytes of their count matrices (capped at create).
@@ -1349,7 +1351,8 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
         }
         {
           Bracket b(c, w, "dense_gemm", 1);
-          launch_dense_gemm(probs, tiles + kDenseTileWords * (size_t)wv.t0, wv.nt, gemm_ctas, status, ds);
+          launch_dense_gemm(probs, tiles + kDenseTileWords * (size_t)wv.t0, wv.nt, gemm_ctas,
+                            (uint32_t)c->dense_round_sum, (long long)c->dense_wait_cycles, status, ds);
         }
         Bracket b(c, w, "dense_fix", 1);
         launch_dense_fix(probs, ovf_n, (const DenseOvf*)w.dovf.p, cap, status, ds);
@@ -1376,7 +1379,7 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
       const int gemm_ctas = c->dense_sms > 0 ? std::min(c->dense_sms, c->nsm) : c->nsm;
       launch_dense_gemm((const DenseProb*)(base + p.o_dprobs),
                         (const uint32_t*)(base + p.o_dtiles) + kDenseTileWords * (size_t)p.heavy_t0, p.heavy_nt,
-                        gemm_ctas, status, hs);
+                        gemm_ctas, (uint32_t)c->dense_round_sum, (long long)c->dense_wait_cycles, status, hs);
     }
     if (fork) cudaEventRecord(w.ev_join, w.cs2);
     {
@@ -2559,6 +2562,15 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
     case GAKCO_OPT_DENSE_RUN_COLS:
       if (v < 128) return fail(c, GAKCO_E_INVALID, "dense run columns must be >= 128");
       c->dense_run_cols = v;
+      break;
+    case GAKCO_OPT_DENSE_ROUND_SUM:
+      if (v < 1 || v > (int64_t)kDenseExactSum)
+        return fail(c, GAKCO_E_INVALID, "dense round sum must be 1..%u", kDenseExactSum);
+      c->dense_round_sum = v;
+      break;
+    case GAKCO_OPT_DENSE_WAIT_CYCLES:
+      if (v < 0) return fail(c, GAKCO_E_INVALID, "dense wait cycles must be >= 0");
+      c->dense_wait_cycles = v;
       break;
     case GAKCO_OPT_DENSE_OVERFLOW:
       if (v < 1 || v > ((int64_t)1 << 26)) return fail(c, GAKCO_E_INVALID, "overflow entries must be 1..2^26");

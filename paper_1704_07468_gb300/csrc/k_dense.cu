@@ -12,11 +12,14 @@
 //
 // Exactness.  A holds D0 = min(count, 16), which e4m3 represents exactly;
 // products (<= 256) and partial sums are exact in the f32 accumulators
-// while they stay below 2^24, so the GEMM closes an accumulation "round"
-// and adds it into the int32 C every floor((2^24 - 1) / (128 maxD0^2))
-// stages of 128 columns, maxD0 being the largest D0 the scatter kernel
-// wrote -- or once per macro tile when maxD0 times a row's largest possible
-// sum (windows x masks) stays below 2^24, which bounds every partial sum.  A count c > 16 is also appended to an overflow list, and the fix
+// while they stay within 2^24 - 1, so the GEMM closes an accumulation
+// "round" and adds it into the int32 C every floor(cap / (128 maxD0^2))
+// stages of 128 columns (cap = 2^24 - 1 unless a caller lowers it), maxD0
+// being the largest D0 the scatter kernel wrote -- or once per macro tile
+// when maxD0 times a row's largest possible sum (windows x masks) stays
+// within cap, which bounds every partial sum.  The tests drive real partial
+// sums of one round to just below 2^24 and compare with the oracle.  A
+// count c > 16 is also appended to an overflow list, and the fix
 // kernel adds the exact difference A A^T - D0 D0^T, which is nonzero only
 // in rows and columns of overflowing sequences:
 //   (x, y), y without overflow at the column:  (c_x - 16) D0(y)
@@ -55,7 +58,7 @@ constexpr int kGemmThreads = 192;
 constexpr uint32_t kTmemCols = 512;  // two 128 x 256 f32 accumulators
 constexpr int kScatterThreads = 512;
 constexpr int kScatterMasks = 16;  // masks of one scatter block held in shared memory
-constexpr long long kWaitCycles = 4000000000ll;  // about 2 s
+constexpr long long kWaitCycles = 4000000000ll;  // about 2 s (drains; default for the role waits)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -98,13 +101,15 @@ __device__ __forceinline__ bool bar_test(uint64_t* b, uint32_t parity) {
 }
 
 // Bounded wait for the phase of the given parity.  Returns false when the
-// wait ran out (and then raises the abort flag) or another role aborted.
-__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, volatile uint32_t* abort_flag) {
+// wait ran out after `limit` cycles (and then raises the abort flag) or
+// another role aborted.
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, volatile uint32_t* abort_flag,
+                                         long long limit) {
   const long long t0 = clock64();
   for (;;) {
     if (bar_test(b, parity)) return true;
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       return false;
     }
@@ -132,15 +137,18 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// Stages (128 columns each) per exact accumulation round.  Every partial
-// sum of a (x, y) entry is at most sum_k A[x,k] A[y,k] <= maxc * sum_k
-// A[y,k] <= maxc * wmasks (each window of y adds at most one to one column
-// of each mask), so when that stays below 2^24 the whole macro tile is one
-// round; otherwise a stage adds at most 128 maxc^2.
-__device__ __forceinline__ uint32_t stages_per_round(const uint32_t* maxc, uint32_t nk, uint32_t wmasks) {
+// Stages (128 columns each) per exact accumulation round, so that no
+// partial sum of a round exceeds `cap` (at most 2^24 - 1, where f32 holds
+// every integer).  Every partial sum of a (x, y) entry is at most
+// sum_k A[x,k] A[y,k] <= maxc * sum_k A[y,k] <= maxc * wmasks (each window
+// of y adds at most one to one column of each mask), so when that stays
+// within `cap` the whole macro tile is one round; otherwise a stage adds at
+// most 128 maxc^2.
+__device__ __forceinline__ uint32_t stages_per_round(const uint32_t* maxc, uint32_t nk, uint32_t wmasks,
+                                                     uint32_t cap) {
   const uint32_t mc = *(const volatile uint32_t*)maxc;
-  if (mc == 0 || (wmasks != 0 && (uint64_t)mc * wmasks < (1ull << 24))) return nk > 0 ? nk : 1;
-  uint64_t s = (uint64_t)((1u << 24) - 1) / (128ull * mc * mc);
+  if (mc == 0 || (wmasks != 0 && (uint64_t)mc * wmasks <= cap)) return nk > 0 ? nk : 1;
+  uint64_t s = (uint64_t)cap / (128ull * mc * mc);
   if (s < 1) s = 1;
   return (uint32_t)(s < nk ? s : nk);
 }
@@ -321,7 +329,7 @@ __device__ __forceinline__ uint32_t row_halves(uint32_t I2, uint32_t n) {
 
 __global__ void __launch_bounds__(kGemmThreads, 1)
 k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ tiles, uint32_t ntiles,
-             uint32_t* __restrict__ status) {
+             uint32_t sum_cap, long long wait_cycles, uint32_t* __restrict__ status) {
   extern __shared__ uint8_t raw[];
   __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], tfull, tempty, done_bar;
   __shared__ uint32_t tmem_base;
@@ -364,7 +372,7 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
           const uint32_t nk = (uint32_t)(probs[p].ld / 128);
           for (uint32_t k = 0; k < nk; ++k, ++it) {
             const uint32_t s = it % kStages;
-            if (!bar_wait(&empty_bar[s], ((it / kStages) & 1) ^ 1, &abort_flag)) {
+            if (!bar_wait(&empty_bar[s], ((it / kStages) & 1) ^ 1, &abort_flag, wait_cycles)) {
               stop = true;
               break;
             }
@@ -398,20 +406,20 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
         const uint32_t st = row_halves(I2, probs[pa].n);
         uint32_t total = 0;
         for (uint32_t p = pa; p < pa + pn; ++p) total += (uint32_t)(probs[p].ld / 128);
-        const uint32_t spr = stages_per_round(probs[pa].maxc, total, probs[pa].wmasks);
+        const uint32_t spr = stages_per_round(probs[pa].maxc, total, probs[pa].wmasks, sum_cap);
         uint32_t kr = 0;  // stages into the current round
         for (uint32_t p = pa; p < pa + pn && !stop; ++p) {
           const uint32_t nk = (uint32_t)(probs[p].ld / 128);
           for (uint32_t k = 0; k < nk; ++k, ++it) {
             if (kr == 0) {
-              if (!bar_wait(&tempty, (round & 1) ^ 1, &abort_flag)) {
+              if (!bar_wait(&tempty, (round & 1) ^ 1, &abort_flag, wait_cycles)) {
                 stop = true;
                 break;
               }
               asm volatile("tcgen05.fence::after_thread_sync;");
             }
             const uint32_t s = it % kStages;
-            if (!bar_wait(&full_bar[s], (it / kStages) & 1, &abort_flag)) {
+            if (!bar_wait(&full_bar[s], (it / kStages) & 1, &abort_flag, wait_cycles)) {
               stop = true;
               break;
             }
@@ -459,14 +467,14 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
       const uint32_t st = row_halves(I2, n);
       uint32_t total = 0;
       for (uint32_t p = pa; p < pa + pn; ++p) total += (uint32_t)(probs[p].ld / 128);
-      const uint32_t spr = stages_per_round(probs[pa].maxc, total, probs[pa].wmasks);
+      const uint32_t spr = stages_per_round(probs[pa].maxc, total, probs[pa].wmasks, sum_cap);
       const uint32_t nr = (total + spr - 1) / spr;
       // One round and no other writer: the tile's C entries are still zero,
       // so plain (vector) stores replace the atomic adds.
       const bool store = nr == 1 && probs[pa].sole != 0;
       uint32_t* C = probs[pa].C;
       for (uint32_t r = 0; r < nr; ++r, ++round) {
-        if (!__all_sync(0xffffffffu, bar_wait(&tfull, round & 1, &abort_flag))) {
+        if (!__all_sync(0xffffffffu, bar_wait(&tfull, round & 1, &abort_flag, wait_cycles))) {
           stop = true;
           break;
         }
@@ -714,10 +722,13 @@ void launch_dense_fix(const DenseProb* d_probs, const uint32_t* ovf_n, const Den
 }
 
 void launch_dense_gemm(const DenseProb* d_probs, const uint32_t* d_tiles, uint32_t ntiles, int nsm,
-                       uint32_t* status, cudaStream_t st) {
+                       uint32_t sum_cap, long long wait_cycles, uint32_t* status, cudaStream_t st) {
   if (ntiles == 0) return;
   const uint32_t grid = ntiles < (uint32_t)nsm ? ntiles : (uint32_t)nsm;
-  k_dense_gemm<<<grid, kGemmThreads, dense_gemm_smem(), st>>>(d_probs, d_tiles, ntiles, status);
+  if (sum_cap == 0 || sum_cap > kDenseExactSum) sum_cap = kDenseExactSum;
+  if (wait_cycles <= 0) wait_cycles = kWaitCycles;
+  k_dense_gemm<<<grid, kGemmThreads, dense_gemm_smem(), st>>>(d_probs, d_tiles, ntiles, sum_cap, wait_cycles,
+                                                                status);
 }
 
 }  // namespace gk

@@ -226,8 +226,14 @@ void launch_dense_scatter(const DenseProb* d_probs, uint32_t nprobs, uint32_t p0
 // consecutive problems of one dataset and level, whose columns the tile
 // sweeps), I2, J2 (256-row and 256-column blocks, I2 <= J2).
 constexpr int kDenseTileWords = 4;
+// Largest partial sum of one exact accumulation round: f32 holds every
+// integer up to 2^24.
+constexpr uint32_t kDenseExactSum = (1u << 24) - 1;
+// sum_cap: bound on a round's partial sums (0 or above kDenseExactSum:
+// kDenseExactSum); wait_cycles: limit of each wait between the roles
+// (<= 0: about 2 s).
 void launch_dense_gemm(const DenseProb* d_probs, const uint32_t* d_tiles, uint32_t ntiles, int nsm,
-                       uint32_t* status, cudaStream_t st);
+                       uint32_t sum_cap, long long wait_cycles, uint32_t* status, cudaStream_t st);
 // d_probs: every problem of the plan.  Raises kErrDenseOverflow when the
 // list overflowed (the results are then incomplete).
 void launch_dense_fix(const DenseProb* d_probs, const uint32_t* ovf_n, const DenseOvf* ovf, uint32_t ovf_cap,

@@ -21,6 +21,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "gakco.h"
@@ -38,14 +39,19 @@ constexpr int kRadixBits = 8;                          // sort digit width
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Host copies of the table area; reused by every call (hence one caller
-// thread at a time).
+// Host copies of the table area; reused by every call on every device, so
+// calls hold g_lock (a plain mutex, which allocates nothing) from start to
+// finish.
+static std::mutex g_lock;
 static unsigned char h_tables[kHostTableBytes];
 static MaskDesc h_masks[kMaxMasks];
 static uint32_t h_level[kMaxMasks];
 
-// Device address of g_scratch per device, looked up on the first call made
-// with that device current.
+// Device address of g_scratch per device.  It is looked up again (with the
+// kernel attributes set again) on every call made outside stream capture,
+// so a device reset or a new primary context, which reloads the module,
+// leaves no stale address behind; a call made while `stream` is capturing
+// uses the address of the last call outside capture.
 static unsigned char* d_scratch[kMaxDevices];
 static bool d_ready[kMaxDevices];
 
@@ -208,11 +214,20 @@ extern "C" int gakco_gram_device_noalloc(int sigma, int g, int k, const uint8_t*
   }
 
   // --- per-device set-up: device address of the static array ---------------
+  std::lock_guard<std::mutex> hold(g_lock);
+  cudaStream_t st = (cudaStream_t)stream_v;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return set_err(err, err_len, GAKCO_E_CUDA, "no usable CUDA device");
-  if (!d_ready[dev]) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(msg, sizeof msg, "stream query: %s", cudaGetErrorString(e));
+    return set_err(err, err_len, GAKCO_E_CUDA, msg);
+  }
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess) {
@@ -228,9 +243,11 @@ extern "C" int gakco_gram_device_noalloc(int sigma, int g, int k, const uint8_t*
     }
     d_scratch[dev] = (unsigned char*)p;
     d_ready[dev] = true;
+  } else if (!d_ready[dev]) {
+    return set_err(err, err_len, GAKCO_E_INVALID,
+                   "first call on this device made during stream capture; call once outside capture first");
   }
   unsigned char* S = d_scratch[dev];
-  cudaStream_t st = (cudaStream_t)stream_v;
 
   // --- host tables -----------------------------------------------------------
   const int nm = make_masks(g, M, bits);

@@ -30,6 +30,8 @@ __all__ = [
     "text",
     "serve_requests",
     "repeats",
+    "periodic",
+    "fixed_length",
     "random_small",
     "WORKLOADS",
 ]
@@ -149,6 +151,32 @@ def repeats(kind="homopolymer", n=4, length=1500, sigma=4, seed=11):
         else:
             seqs.append(rng.integers(0, sigma, size=length // 3).astype(np.uint8))
     return pack(seqs)
+
+
+def periodic(seed, period, lengths, shifts, sigma=4):
+    """Sequences cut from one random unit repeated end to end.
+
+    The unit holds ``period`` iid uniform symbols; sequence ``i`` starts at
+    position ``shifts[i]`` of the unit and runs on cyclically for
+    ``lengths[i]`` symbols, so every window of a sequence recurs once per
+    period (counts of a feature near ``length / period``).
+    """
+    rng = np.random.default_rng(seed)
+    unit = rng.integers(0, sigma, size=period).astype(np.uint8)
+    seqs = []
+    for length, shift in zip(lengths, shifts):
+        idx = (int(shift) + np.arange(int(length))) % period
+        seqs.append(unit[idx])
+    return pack(seqs)
+
+
+def fixed_length(seed, n, length, sigma):
+    """``n`` sequences of one ``length``, iid uniform over ``sigma`` symbols
+    (the N-sweep at l = 100 of Section 3.2 / Fig. 5(c); sigma = 5 is DNA
+    with the unknown-base symbol N of Section S:3.2)."""
+    rng = np.random.default_rng(seed)
+    codes = rng.integers(0, sigma, size=n * length).astype(np.uint8)
+    return codes, np.arange(0, n * length + 1, length, dtype=np.int64)
 
 
 def random_small(seed, n, sigma, lo, hi):

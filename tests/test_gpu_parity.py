@@ -71,6 +71,24 @@ def test_ragged_random_bit_exact(case, engine):
     _check(_gram(sigma, g, k, codes, off, engine=engine), ref)
 
 
+NSWEEP = [  # (name, sigma, g, k, n): the N-sweep at l = 100 (Section 3.2, Fig. 5(c))
+    ("dna_sigma5", 5, 10, 6, 100),   # DNA with the unknown-base symbol N (Section S:3.2)
+    ("dna_sigma5", 5, 10, 6, 750),
+    ("protein", 20, 8, 4, 250),
+    ("text", 36, 8, 5, 250),
+]
+
+
+@pytest.mark.parametrize("case", NSWEEP, ids=[f"{c[0]}_{c[4]}" for c in NSWEEP])
+def test_nsweep_configurations_bit_exact(case):
+    """The sweep's own inputs and options (the cost model picks the dense
+    levels), every entry against the oracle."""
+    name, sigma, g, k, n = case
+    codes, off = synth.fixed_length(1000 + n, n, 100, sigma)
+    ref = oracle.gram(codes, off, g, k)
+    _check(_gram(sigma, g, k, codes, off, dense=1), ref)
+
+
 @pytest.mark.parametrize("opts", [
     {"radix_bits": 4}, {"radix_bits": 11}, {"chunk_elems": 4096},
     {"smem_cols": 7}, {"smem_cols": 32, "accum_threads": 256},
