@@ -211,13 +211,17 @@ NCU_BYTES_PER_UNIT = {
 NCU_SOURCE = "profiles/dense_scatter_gemm_accum_dna_4000.md (scaled by units)"
 
 
-def kernel_rooflines(timings, work, peaks, sm_count):
+def kernel_rooflines(timings, work, peaks, sm_count, smem_atomic_peak=None):
     """Roofline entry per timed stage with a known algorithmic work figure.
 
     ``work`` holds the engine's own counts for the step: pair updates of
     the accumulation, algorithmic sort bytes, dense-contraction flops
     (upper triangle, unpadded) and issued flops, dense A bytes."""
     out = {}
+    timings = dict(timings)
+    if "diag" in timings and "combine" in timings:
+        (ms_d, n_d), (ms_c, n_c) = timings.pop("diag"), timings.pop("combine")
+        timings["diag+combine"] = (ms_d + ms_c, max(n_d, n_c))
     # The dense contraction runs on e4m3 operands: its peak is the measured
     # bf16 figure times the nominal e4m3 / bf16 ratio (4.5 / 2.25 PFLOP/s).
     tensor_peak = peaks.get("bf16_tflops", 1900.0) * 2.0
@@ -227,12 +231,17 @@ def kernel_rooflines(timings, work, peaks, sm_count):
             continue
         e = None
         if name == "accumulate" and work["pairs"] > 0:
-            # One 32-bit shared-memory add per pair update; peak = banks x
-            # SMs x max SM clock.
-            peak = SMEM_BANKS * sm_count * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            # One 32-bit shared-memory atomic add per pair update; peak =
+            # the conflict-free shared-atomic rate measured on this GPU by
+            # the library's probe (else banks x SMs x max SM clock).
+            if smem_atomic_peak:
+                peak, src = smem_atomic_peak / 1e12, "measured: conflict-free shared-memory atomic adds (gakco_measure_smem_atomics)"
+            else:
+                peak = SMEM_BANKS * sm_count * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+                src = "derived: 32 shared-memory banks x SMs x max SM clock"
             a = work["pairs"] / sec / 1e12
             e = {"bound": "alu", "achieved": a, "peak": peak, "unit": "Tupdates/s",
-                 "kernel": "k_accum", "peak_source": "32 shared-memory banks x SMs x max SM clock"}
+                 "kernel": "k_accum", "peak_source": src}
         elif name == "sort_pass" and work["sort_bytes"] > 0:
             a = work["sort_bytes"] / sec / 1e9
             e = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -248,6 +257,18 @@ def kernel_rooflines(timings, work, peaks, sm_count):
             a = work["dense_bytes"] / sec / 1e9
             e = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                  "kernel": "k_dense_scatter"}
+        elif name == "run_length" and work.get("rle_bytes", 0) > 0:
+            a = work["rle_bytes"] / sec / 1e9
+            e = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "kernel": "k_rle_count + k_rle_scan + k_rle_emit_gram + k_rle_fix"}
+        elif name == "pack" and work.get("pack_bytes", 0) > 0:
+            a = work["pack_bytes"] / sec / 1e9
+            e = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "kernel": "k_pack"}
+        elif name == "diag+combine" and work.get("combine_bytes", 0) > 0:
+            a = work["combine_bytes"] / sec / 1e9
+            e = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "kernel": "k_diag + k_combine"}
         if e is None:
             continue
         e["frac"] = e["achieved"] / e["peak"]
@@ -261,6 +282,49 @@ def kernel_rooflines(timings, work, peaks, sm_count):
         e["launch_ms"] = ms / n
         e["launches"] = n
         out[name] = e
+    return out
+
+
+def run_configs(pkg, names, steps, flush):
+    """The other single-GPU workloads, each in its own batched device call
+    (autotuned, replayed from its graph, K and Khat outputs): ms per step,
+    CUDA events on the calling stream, the L2 flush between steps."""
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name in names:
+        desc, sigma, g, k, sets = make_workload(name)
+        ns = [len(o) - 1 for _, o in sets]
+        d_codes = [torch.from_numpy(c).to(dev) for c, _ in sets]
+        d_K = [torch.empty((n, n), dtype=torch.int32, device=dev) for n in ns]
+        d_Kh = [torch.empty((n, n), dtype=torch.float64, device=dev) for n in ns]
+        offs = [o for _, o in sets]
+        with pkg.gakco_create(sigma, g, k) as ctx:
+            ctx.autotune_device([t.data_ptr() for t in d_codes], offs, stream=stream.cuda_stream)
+
+            def step():
+                ctx.gram_batch_device([t.data_ptr() for t in d_codes], offs,
+                                      [t.data_ptr() for t in d_K], [t.data_ptr() for t in d_Kh],
+                                      None, stream=stream.cuda_stream)
+            for _ in range(3):
+                step()
+            ms = []
+            for _ in range(steps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            t = float(np.mean(ms))
+            out[name] = {"ms_per_step": t, "entries_per_s": sum(n * n for n in ns) / (t / 1000.0),
+                         "dense_problems": int(ctx.get_stat("dense_problems")), "workload": desc}
+        del d_codes, d_K, d_Kh
+        torch.cuda.empty_cache()
     return out
 
 
@@ -431,6 +495,9 @@ def run_ours(args):
     if args.dense is not None:
         ctx.set_option("dense", args.dense)
         tuned += f"; dense={args.dense} set by --dense"
+    if args.sort is not None:
+        ctx.set_option("sort", args.sort)
+        tuned += f"; sort={args.sort} set by --sort"
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -459,6 +526,9 @@ def run_ours(args):
             "dense_flops": ctx.get_stat("dense_flops"),
             "dense_issued": ctx.get_stat("dense_issued_flops"),
             "dense_bytes": ctx.get_stat("dense_bytes"),
+            "rle_bytes": ctx.get_stat("rle_bytes"),
+            "pack_bytes": ctx.get_stat("pack_bytes"),
+            "combine_bytes": ctx.get_stat("combine_bytes"),
             "dense_problems": int(ctx.get_stat("dense_problems"))}
     if ws > 1:
         step_ms = reduce_max(step_ms, dev)
@@ -529,6 +599,8 @@ def run_ours(args):
             kctx.autotune_device([t.data_ptr() for t in d_codes], offs, stream=stream.cuda_stream)
         if args.dense is not None:
             kctx.set_option("dense", args.dense)
+        if args.sort is not None:
+            kctx.set_option("sort", args.sort)
         kctx.set_option("kernel_only", 1)
         kk = [torch.empty((n, n), dtype=torch.int32, device=dev) for n in ns]
         kkh = [torch.empty((n, n), dtype=torch.float64, device=dev) for n in ns]
@@ -560,11 +632,15 @@ def run_ours(args):
     # headline entry.
     peaks, peak_kind = measured_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    roofs = kernel_rooflines(timings, work, peaks, sm_count)
+    try:
+        smem_peak = pkg.gakco_measure_smem_atomics(stream.cuda_stream)
+    except pkg.GakcoError:
+        smem_peak = None
+    roofs = kernel_rooflines(timings, work, peaks, sm_count, smem_peak)
     total_ms = sum(v[0] for v in timings.values())
     for name, e in roofs.items():
         e["peak_kind"] = peak_kind
-        e["share_of_step"] = timings[name][0] / total_ms
+        e["share_of_step"] = e["launch_ms"] * e["launches"] / total_ms
     dom_name = max(timings.items(), key=lambda kv: kv[1][0])[0]
     if dom_name in roofs:
         roof = dict(roofs[dom_name])
@@ -573,6 +649,20 @@ def run_ours(args):
                 "frac": None, "traffic": None, "kernel": dom_name, "peak_kind": peak_kind,
                 "share_of_step": timings[dom_name][0] / total_ms}
     roof["stage"] = dom_name
+    # Every stage in one compact table (ms, share of the serialised step,
+    # fraction of its roofline), kept inside the roofline entry.
+    roof["stages"] = {}
+    for name, (t_ms, _) in sorted(timings.items(), key=lambda kv: -kv[1][0]):
+        r = roofs.get(name) or roofs.get("diag+combine" if name in ("diag", "combine") else "")
+        row = {"ms": round(t_ms, 3), "share": round(t_ms / total_ms, 3)}
+        if r is not None:
+            row.update({"frac": round(r["frac"], 3), "bound": r["bound"],
+                        "achieved": round(r["achieved"], 3), "unit": r["unit"]})
+        roof["stages"][name] = row
+
+    configs = None
+    if args.config_steps > 0 and rank == 0 and args.workload == "dna_large":
+        configs = run_configs(pkg, ("dna_toy", "protein", "text"), args.config_steps, flush)
 
     serve = None
     if args.serve_requests > 0 and rank == 0:
@@ -614,7 +704,31 @@ def run_ours(args):
         "roofline_stages": roofs,
         "cpu_baseline": cpu,
         "clocks": clocks,
+        "configs": configs,
     }
+    # Compact figures last on the line, so that they survive a reader that
+    # keeps only the end of it.
+    summ = {"ms_per_step": round(step_ms, 3), "e2e_ms": round(e2e_step, 3),
+            "mask_passes_per_s": round(line["mask_passes_per_s"], 1)}
+    if plain:
+        summ.update({"plain_per_mask_ms": round(plain["ms_per_step"], 2),
+                     "batched_vs_plain": round(plain["ms_per_step"] / step_ms, 2),
+                     "plain_mask_passes_per_s": round(plain["mask_passes_per_s"], 1),
+                     "plain_bit_identical": plain["bit_identical_K"]})
+    if konly:
+        summ["kernel_only_ms"] = round(konly["ms_per_step"], 3)
+    if serve:
+        cb, pl = serve["continuous_batching"], serve["plain_per_request"]
+        summ["serve"] = {"p50_ms": round(cb["p50_ms"], 2), "p99_ms": round(cb["p99_ms"], 2),
+                         "rows_per_s": round(cb["rows_per_s"]),
+                         "plain_p50_ms": round(pl["p50_ms"], 2), "plain_p99_ms": round(pl["p99_ms"], 2),
+                         "plain_rows_per_s": round(pl["rows_per_s"]),
+                         "saturated_rows_per_s": round(serve["saturated_rows_per_s"]["continuous_batching"]),
+                         "plain_saturated_rows_per_s": round(serve["saturated_rows_per_s"]["plain_per_request"])}
+    if configs:
+        summ["configs_ms"] = {n: round(v["ms_per_step"], 3) for n, v in configs.items()}
+    summ["frac"] = {n: r["frac"] for n, r in roof["stages"].items() if "frac" in r}
+    line["summary"] = summ
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -640,6 +754,10 @@ def main():
                     help="also time the K = C_M mode (level-M masks only); 0 to skip")
     ap.add_argument("--dense", type=int, default=None, choices=[0, 1, 2],
                     help="dense-level mode after autotuning: 0 never, 1 cost model, 2 every qualifying level")
+    ap.add_argument("--config-steps", type=int, default=5,
+                    help="also time the toy, protein and text workloads (dna_large run only); 0 to skip")
+    ap.add_argument("--sort", type=int, default=None, choices=[0, 1],
+                    help="sort after autotuning: 0 upsweep/scan/downsweep per pass, 1 onesweep")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--dna-sizes", type=lambda v: [int(t) for t in v.split(",")], default=None,

@@ -174,6 +174,13 @@ const char *gakco_last_error(const gakco_ctx *ctx);
  * For tests of the timeout path: a limit of a few cycles makes an ordinary
  * call run out; the context stays usable. */
 #define GAKCO_OPT_DENSE_WAIT_CYCLES 25
+/* Sort of the masked keys (Alg. 1 "sort"; the non-swapping LSD radix sort
+ * of Section S:1.2), both stable and identical in result: 0 = per pass an
+ * upsweep histogram, digit scans and a downsweep scatter; 1 = onesweep:
+ * every pass's digit counts in one read of the keys, then one scatter per
+ * pass whose tiles find their digit offsets by a decoupled look-back
+ * (digits of at most 8 bits; wider digits use 0). */
+#define GAKCO_OPT_SORT 26
 int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 
 /*
@@ -203,6 +210,16 @@ int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
                                          payloads read and written once per pass) */
 #define GAKCO_STAT_HEAVY_COLUMNS 15   /* Gram: heavy features moved to the tensor cores */
 #define GAKCO_STAT_HEAVY_FLOPS 16     /* Gram: flops of their contractions' upper triangles */
+#define GAKCO_STAT_MASKS 20           /* c_gk: position masks of all levels (the units a
+                                         sharded Gram splits) */
+#define GAKCO_STAT_RLE_BYTES 17       /* Gram: algorithmic bytes of the run-length passes (each
+                                         element's key and payload read once, its ewin slot
+                                         written; 8 bytes per entry emitted) */
+#define GAKCO_STAT_PACK_BYTES 18      /* Gram: algorithmic bytes of the g-mer packing (symbols read
+                                         once; 8-byte key and 4-byte window id per window) */
+#define GAKCO_STAT_COMBINE_BYTES 19   /* Gram: algorithmic bytes of the diagonal and combine tail
+                                         (upper triangles of C_0..C_M read once, requested outputs
+                                         written in full) */
 int gakco_get_stat(const gakco_ctx *ctx, int key, double *value);
 
 /*
@@ -363,6 +380,49 @@ int gakco_decision(gakco_ctx *ctx, const uint8_t *codes,
 int gakco_submit_svm(gakco_ctx *ctx, const uint8_t *codes,
                      const int64_t *offsets, int32_t nt, int32_t *K,
                      double *Khat, double *decision, uint64_t *ticket);
+
+/*
+ * Sharded Gram computation (Section 2.2, "Parallelization"; S:5.3): every
+ * (level m, position mask) pass of countAndUpdate is independent, and C_m
+ * (Eq. 8) is the sum of the passes' contributions.  A dataset's c_gk masks
+ * (GAKCO_STAT_MASKS; level order, lexicographic within a level) can
+ * therefore be split into slices, one per GPU or process:
+ *
+ * gakco_gram_partial_device computes the contribution of masks
+ * [mask_begin, mask_end) to C_0..C_M for one dataset (device codes, host
+ * offsets as in gakco_gram_device) into C, a device buffer of (M+1) x n x n
+ * uint32 (C[(m n + x) n + y]), upper triangles (y >= x) only; the strict
+ * lower triangles are written as 0.  Work is ordered on `stream`; the call
+ * returns when it is done.  Batched engine only (GAKCO_OPT_ENGINE = 0).
+ *
+ * The slices' C buffers are summed element-wise with wrap-around uint32 (or
+ * int32) addition, e.g. by an all-reduce across ranks; integer addition is
+ * exact and order-independent, and the sum over all c_gk masks is the
+ * dataset's C.  gakco_combine_device then applies inclusion-exclusion
+ * (Eq. 9), the kernel K = sum_m h_m N_m (Eq. 6, Eq. 7) and the
+ * normalisation to a summed C (device pointer, read only), writing K (n x n
+ * int32, required), Khat and N_m (optional) exactly as gakco_gram_device
+ * does.  The sum must cover every mask exactly once: the combine step
+ * cannot tell a missing or repeated slice from a complete sum.
+ */
+int gakco_gram_partial_device(gakco_ctx *ctx, const uint8_t *codes,
+                              const int64_t *offsets, int32_t n,
+                              int32_t mask_begin, int32_t mask_end,
+                              uint32_t *C, void *stream);
+int gakco_combine_device(gakco_ctx *ctx, const uint32_t *C, int32_t n,
+                         int32_t *K, double *Khat, int32_t *Nm, void *stream);
+
+/*
+ * Measured ceiling of the sparse accumulation: the rate (atomic adds per
+ * second, whole device) at which the current GPU retires conflict-free
+ * 32-bit shared-memory atomic adds, the operation countAndUpdate (Alg. 1)
+ * performs once per pair update on the sparse route.  Runs a probe kernel
+ * of a few milliseconds on `stream` (a cudaStream_t, NULL = legacy stream)
+ * and waits for it; allocates and frees a small device buffer.  Returns
+ * GAKCO_OK and *updates_per_s, or GAKCO_E_CUDA.  Not part of the paper: the
+ * denominator of the accumulation's roofline.
+ */
+int gakco_measure_smem_atomics(void *stream, double *updates_per_s);
 
 /*
  * Gram kernel of one dataset that allocates nothing.  The paper has no

@@ -22,8 +22,10 @@ Every integer is int64; floating point is fp64.
 from __future__ import annotations
 
 import ctypes
+import itertools
 import os
 import subprocess
+from collections import Counter
 from math import comb
 
 import numpy as np
@@ -139,6 +141,44 @@ def normalise(K, diag_rows, diag_cols):
         out = np.asarray(K, dtype=np.float64) / np.sqrt(prod)
     out[prod == 0] = 0.0
     return out
+
+
+def position_masks(g, M):
+    """The deleted-position sets of levels m = 0..M (Section 2.2, step 3):
+    all C(g, m) sets of m of the g positions, level by level, each level in
+    lexicographic order."""
+    return [d for m in range(M + 1) for d in itertools.combinations(range(g), m)]
+
+
+def cumulative_profile(codes, offsets, g, M, deleted_sets=None):
+    """The contributions of the given masks (default: all of levels 0..M)
+    to the cumulative mismatch profiles C_m (Eq. 8), by the counting route
+    of Section 2.2 (Fig. 2, steps 3-5): delete the mask's positions from
+    every g-mer, count each remaining (g-m)-mer per sequence, and add
+    c_x * c_y to C_m(x, y) over the (g-m)-mers x and y share.  Plain Python
+    (tiny inputs only); shape (M+1, n, n), int64."""
+    codes, offsets = np.asarray(codes), np.asarray(offsets, dtype=np.int64)
+    n = len(offsets) - 1
+    seqs = [codes[offsets[i]:offsets[i + 1]] for i in range(n)]
+    wins = [[tuple(int(c) for c in s[i:i + g]) for i in range(len(s) - g + 1)] for s in seqs]
+    C = np.zeros((M + 1, n, n), dtype=np.int64)
+    for dele in (position_masks(g, M) if deleted_sets is None else deleted_sets):
+        m = len(dele)
+        keep = [p for p in range(g) if p not in dele]
+        cnt = [Counter(tuple(w[p] for p in keep) for w in ws) for ws in wins]
+        for x in range(n):
+            for y in range(n):
+                C[m, x, y] += sum(v * cnt[y].get(f, 0) for f, v in cnt[x].items())
+    return C
+
+
+def inclusion_exclusion(C, g):
+    """Eq. 9: N_m = C_m - sum_{j<m} C(g-j, m-j) N_j for m = 0..M."""
+    C = np.asarray(C, dtype=np.int64)
+    N = np.zeros_like(C)
+    for m in range(C.shape[0]):
+        N[m] = C[m] - sum(comb(g - j, m - j) * N[j] for j in range(m))
+    return N
 
 
 def _check_gk(g, k):

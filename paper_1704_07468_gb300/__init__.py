@@ -19,7 +19,7 @@ import os
 
 import numpy as np
 
-__all__ = ["gakco_create", "gakco_gram_device_noalloc", "Context", "GakcoError", "load_library",
+__all__ = ["gakco_create", "gakco_gram_device_noalloc", "gakco_measure_smem_atomics", "Context", "GakcoError", "load_library",
            "library_path", "OPT", "STAT", "ERRORS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -40,13 +40,14 @@ OPT = {"engine": 1, "radix_bits": 2, "chunk_elems": 3, "graph": 4,
        "dense": 14, "dense_bytes": 15, "dense_overflow": 16,
        "dense_run_cols": 17, "kernel_only": 18, "overlap": 19, "dense_sms": 20,
        "heavy": 21, "heavy_bytes": 22, "direct_d2h": 23,
-       "dense_round_sum": 24, "dense_wait_cycles": 25}
+       "dense_round_sum": 24, "dense_wait_cycles": 25, "sort": 26}
 STAT = {"launches": 1, "mask_passes": 2, "device_bytes": 3,
         "graph_replay": 4, "pair_updates": 5, "entries_visited": 6,
         "windows_visited": 7, "served_batches": 8, "served_requests": 9,
         "dense_problems": 10, "dense_flops": 11, "dense_issued_flops": 12,
         "dense_bytes": 13, "sort_bytes": 14, "heavy_columns": 15,
-        "heavy_flops": 16}
+        "heavy_flops": 16, "rle_bytes": 17, "pack_bytes": 18, "combine_bytes": 19,
+        "masks": 20}
 
 
 class GakcoError(RuntimeError):
@@ -102,6 +103,9 @@ def load_library(build_if_missing: bool = False):
         "gakco_decision": ([p, p, p, i32, p], ctypes.c_int),
         "gakco_submit_svm": ([p, p, p, i32, p, p, p, ctypes.POINTER(ctypes.c_uint64)],
                              ctypes.c_int),
+        "gakco_gram_partial_device": ([p, p, p, i32, i32, i32, p, p], ctypes.c_int),
+        "gakco_combine_device": ([p, p, i32, p, p, p, p], ctypes.c_int),
+        "gakco_measure_smem_atomics": ([p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "gakco_gram_device_noalloc": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, p, p, i32,
                                        p, p, p, p, ctypes.c_char_p, ctypes.c_int],
                                       ctypes.c_int),
@@ -259,6 +263,31 @@ class Context:
             ctypes.c_void_p(stream) if stream else None)
         self._check(rc)
 
+    def gram_partial_device(self, codes_ptr, offsets, mask_begin, mask_end, C_ptr, stream=None):
+        """Contribution of masks [mask_begin, mask_end) to C_0..C_M (C:
+        ``gakco_gram_partial_device``): ``C_ptr`` is a device buffer of
+        (M+1) x n x n uint32, upper triangles written, lower ones zero."""
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        rc = self._lib.gakco_gram_partial_device(
+            self._h, ctypes.c_void_p(codes_ptr), off.ctypes.data_as(ctypes.c_void_p),
+            len(off) - 1, int(mask_begin), int(mask_end), ctypes.c_void_p(C_ptr),
+            ctypes.c_void_p(stream) if stream else None)
+        self._check(rc)
+
+    def combine_device(self, C_ptr, n, K_ptr, Khat_ptr=None, Nm_ptr=None, stream=None):
+        """Eq. 9, Eq. 7 and the normalisation on a summed C (C:
+        ``gakco_combine_device``)."""
+        rc = self._lib.gakco_combine_device(
+            self._h, ctypes.c_void_p(C_ptr), int(n), ctypes.c_void_p(K_ptr),
+            ctypes.c_void_p(Khat_ptr) if Khat_ptr else None,
+            ctypes.c_void_p(Nm_ptr) if Nm_ptr else None,
+            ctypes.c_void_p(stream) if stream else None)
+        self._check(rc)
+
+    def num_masks(self) -> int:
+        """c_gk, the position masks of all levels (a sharded Gram's units)."""
+        return int(self.get_stat("masks"))
+
 
 def _add_cross_methods(cls):
     """Cross-kernel and serving methods (C: gakco_fit, gakco_cross_fitted,
@@ -390,6 +419,17 @@ def gakco_gram_device_noalloc(sigma, g, k, codes_ptr, offsets, K_ptr, Khat_ptr=N
 
 
 _add_cross_methods(Context)
+
+
+def gakco_measure_smem_atomics(stream=None) -> float:
+    """Conflict-free shared-memory atomic adds per second of the current
+    GPU (C: ``gakco_measure_smem_atomics``)."""
+    lib = load_library()
+    v = ctypes.c_double()
+    rc = lib.gakco_measure_smem_atomics(ctypes.c_void_p(stream) if stream else None, ctypes.byref(v))
+    if rc != GAKCO_OK:
+        raise GakcoError(rc, "shared-memory atomic probe failed")
+    return v.value
 
 
 def gakco_create(sigma: int, g: int, k: int) -> Context:

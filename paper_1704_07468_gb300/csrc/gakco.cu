@@ -59,6 +59,7 @@ struct Chunk {
   uint64_t hist_elems;
   bool wide;
   std::vector<std::pair<int, int>> passes;  // (shift, bits)
+  uint64_t pass0 = 0;                       // plan-wide number of the chunk's first pass
 };
 
 struct DsHost {
@@ -106,7 +107,7 @@ struct Work {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_heavy = nullptr;
   DevBuf fullkey, wid, ewin, eseq, efe, keyA, keyB, valA, valB, hist, tcnt, segtot, estart,
       etseq, efid, fstart, tables, codes, outK, outKhat, outNm, rinv, status, Cplain, Cacc, ea, eb,
-      Cd, Cx, Adense, dmaxc, dovf, outF, trec, Aheavy, hctr, hlist, dtot;
+      Cd, Cx, Adense, dmaxc, dovf, outF, trec, Aheavy, hctr, hlist, dtot, osst, osctr, oscnt;
   void* h_tables = nullptr;
   size_t h_tables_cap = 0;
   void* h_status = nullptr;
@@ -120,12 +121,14 @@ struct Work {
   std::string err;
   double pairs = 0, entries = 0, windows = 0;
   double heavy_cols = 0, heavy_flops = 0;  // heavy-feature columns and their GEMM flops
+  double rle_entries = 0;                   // (feature, sequence) entries the run-length pass emitted
 
   std::vector<DevBuf*> all() {
     return {&fullkey, &wid, &ewin,   &eseq,  &efe,  &keyA,  &keyB,  &valA,    &valB,
             &hist,    &tcnt,    &segtot, &estart, &etseq, &efid, &fstart, &tables, &codes,
             &outK,    &outKhat, &outNm,  &rinv,  &status, &Cplain, &Cacc, &ea,    &eb,
-            &Cd,      &Cx,      &Adense, &dmaxc,  &dovf,  &outF, &trec, &Aheavy, &hctr, &hlist, &dtot};
+            &Cd,      &Cx,      &Adense, &dmaxc,  &dovf,  &outF, &trec, &Aheavy, &hctr, &hlist, &dtot,
+            &osst,    &osctr,   &oscnt};
   }
   size_t bytes() {
     size_t s = 0;
@@ -209,6 +212,7 @@ struct gakco_ctx {
   int kernel_only = 0;  // 1: compute level M alone when N_m is not requested (K = C_M)
   int overlap = 1;      // 1: dense and sparse levels of a Gram call run on two streams
   int dense_sms = 0;    // CTAs of the dense GEMM (0: one per SM)
+  int sort_mode = 0;    // 0: upsweep / digit scans / downsweep per pass; 1: onesweep
   int64_t dense_round_sum = kDenseExactSum;  // bound on a GEMM round's partial sums
   int64_t dense_wait_cycles = 0;             // GEMM role-wait limit (0: default)
   // Heavy features of sparse levels go to the tensor cores: threshold on a
@@ -235,10 +239,10 @@ struct gakco_ctx {
   int64_t last_launches = 0, last_mask_passes = 0;
   int last_replay = 0;
   double last_pairs = 0, last_entries = 0, last_windows = 0;
-  double last_heavy_cols = 0, last_heavy_flops = 0;
+  double last_heavy_cols = 0, last_heavy_flops = 0, last_rle_entries = 0;
   // Work figures of the last plan (kept for graph replays).
   double plan_dense_probs = 0, plan_dense_flops = 0, plan_dense_issued = 0, plan_dense_bytes = 0,
-         plan_sort_bytes = 0;
+         plan_sort_bytes = 0, plan_rle_bytes = 0, plan_pack_bytes = 0, plan_combine_bytes = 0;
   std::vector<Timed> timed;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -552,6 +556,7 @@ struct Plan {
   std::vector<uint32_t> items;
   uint32_t ftiles = 0;
   uint64_t max_chunk_elems = 0, max_chunk_nseg = 0, max_chunk_tiles = 0, max_hist = 0;
+  uint64_t total_passes = 0;  // sort passes of all chunks
   bool any_wide = false;
   uint32_t ncols = 0;
   size_t acc_smem = 0;
@@ -563,6 +568,11 @@ struct Plan {
   // C_0..C_{M-1} may stay zero: Eq. 9 then gives N_M = C_M and Eq. 7
   // K = h_M C_M = C_M), else 0.
   int first_level = 0;
+  // Masks computed: [mask_lo, mask_hi) in level order (all by default; a
+  // slice for a partial Gram whose C_0..C_M one rank of a sharded
+  // computation adds), and where a partial call leaves its C.
+  uint32_t mask_lo = 0, mask_hi = 0xFFFFFFFFu;
+  uint32_t* partial_C = nullptr;
   // Dense (tensor-core) levels: flags per (dataset, level), problems,
   // waves of problems whose A matrices share the A buffer, GEMM tiles.
   std::vector<uint8_t> dense;
@@ -582,6 +592,9 @@ struct Plan {
   double dense_issued = 0;        // what the 128 x 256 tiles issue, padding included
   double dense_bytes = 0;         // A written by the scatter
   double sort_bytes = 0;          // algorithmic bytes of every sort pass
+  double rle_bytes = 0;           // run-length: (key, payload) read once + ewin written, per element
+  double pack_bytes = 0;          // packing: symbols read once + full key and window id written
+  double combine_bytes = 0;       // diag + combine: C_m upper triangles read, outputs written
   // device table offsets
   size_t o_masks, o_level, o_pack, o_info, o_segs, o_tiles, o_items, o_dprobs = 0, o_dtiles = 0, o_tmaps = 0;
   std::vector<size_t> o_coff, o_woff;
@@ -651,9 +664,26 @@ int plan_datasets(gakco_ctx* c, Work& w, Plan& p, int32_t nd, const uint8_t* con
   return GAKCO_OK;
 }
 
+// Algorithmic bytes of packing and of the diagonal / combine tail: symbols
+// read once, a full key (8 B) and a window id (4 B) written per window; the
+// upper triangles of C_0..C_M read once and every requested output written.
+void plan_io_bytes(gakco_ctx* c, Plan& p) {
+  p.pack_bytes = 0;
+  p.combine_bytes = 0;
+  const double L = (double)(c->M + 1);
+  for (const DsHost& D : p.ds) {
+    if (D.n <= 0) continue;
+    const double n = (double)D.n, nn = n * n;
+    p.pack_bytes += (double)(D.off[D.n] - D.off[0]) + 12.0 * (double)D.G;
+    p.combine_bytes += 4.0 * L * n * (n + 1.0) / 2.0 + (D.K ? 4.0 * nn : 0.0) + (D.Khat ? 8.0 * nn : 0.0) +
+                       (D.Nm ? 4.0 * L * nn : 0.0);
+  }
+}
+
 // Chunks of (dataset, mask) segments, all of one level per chunk.
 void plan_chunks(gakco_ctx* c, Plan& p, bool plain) {
   p.sort_bytes = 0;
+  p.total_passes = 0;
   const uint64_t limit = plain ? 0 : (uint64_t)std::max<int64_t>(c->chunk_elems, kTile);
   for (int m = p.first_level; m <= c->M; ++m) {
     const int kb = c->lkbits[m];
@@ -670,6 +700,9 @@ void plan_chunks(gakco_ctx* c, Plan& p, bool plain) {
       // and writes (key, payload); later passes read and write both.
       const double kbytes = wide ? 8.0 : 4.0;
       p.sort_bytes += (double)cur.elems * ((8.0 + 4.0 + kbytes + 4.0) + 2.0 * (kbytes + 4.0) * (np - 1));
+      p.rle_bytes += (double)cur.elems * (kbytes + 4.0 + 4.0);
+      cur.pass0 = p.total_passes;
+      p.total_passes += cur.passes.size();
       p.chunks.push_back(cur);
       p.max_chunk_elems = std::max(p.max_chunk_elems, cur.elems);
       p.max_chunk_nseg = std::max<uint64_t>(p.max_chunk_nseg, cur.nseg);
@@ -686,7 +719,7 @@ void plan_chunks(gakco_ctx* c, Plan& p, bool plain) {
     };
     fresh();
     for (uint32_t mu = 0; mu < c->masks.size(); ++mu) {
-      if ((int)c->mask_level[mu] != m) continue;
+      if ((int)c->mask_level[mu] != m || mu < p.mask_lo || mu >= p.mask_hi) continue;
       for (size_t d = 0; d < p.ds.size(); ++d) {
         const DsHost& D = p.ds[d];
         if (D.G == 0 || p.is_dense(d, m, c->M)) continue;
@@ -761,7 +794,13 @@ void add_items(gakco_ctx* c, std::vector<uint32_t>& items, uint32_t d, const std
       (uint32_t)std::max(1.0, std::floor((double)c->group_bytes / std::max(per_mask_bytes, 1.0)));
   for (int m = 0; m <= c->M; ++m) {
     if (skip && (m < skip->first_level || skip->is_dense(d, m, c->M))) continue;  // not needed / tensor cores
-    const uint32_t mf = lf[m], mc = lf[m + 1] - lf[m];
+    uint32_t mf = lf[m], me = lf[m + 1];
+    if (skip) {
+      mf = std::max(mf, skip->mask_lo);
+      me = std::min(me, skip->mask_hi);
+    }
+    if (me <= mf) continue;  // no mask of this level in the plan's slice
+    const uint32_t mc = me - mf;
     const uint32_t ng = (mc + gmax - 1) / gmax;
     for (uint32_t gi = 0; gi < ng; ++gi) {
       const uint32_t a = mf + (uint32_t)((uint64_t)mc * gi / ng);
@@ -827,9 +866,11 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
       const uint64_t S = (uint64_t)1 << kb;
       const uint64_t per_mask = (uint64_t)n_pad * S;
       if (per_mask > budget) continue;
+      const uint32_t mf = std::max(lf[m], p.mask_lo), me = std::min(lf[m + 1], p.mask_hi);
+      if (me <= mf) continue;  // no mask of this level in the plan's slice
       if (c->dense == 1 && !dense_is_cheaper(c, D, n_pad, kb)) continue;
       p.dense[d * L + m] = 1;
-      const uint32_t mf = lf[m], mc = lf[m + 1] - lf[m];
+      const uint32_t mc = me - mf;
       const uint64_t by_mem = std::max<uint64_t>(1, budget / per_mask);
       const uint64_t by_cols = std::max<uint64_t>(1, (uint64_t)c->dense_run_cols / S);
       const uint32_t gmax = (uint32_t)std::min<uint64_t>(mc, std::min(by_mem, by_cols));
@@ -956,7 +997,9 @@ void plan_heavy(gakco_ctx* c, Plan& p, bool plain) {
       h.n = (uint32_t)D.n;
       h.n_pad = (uint32_t)align_up((size_t)D.n, 128);
       h.T = T;
-      const double most = (double)(lf[m + 1] - lf[m]) * (double)D.G / (double)T;
+      const uint32_t mf = std::max(lf[m], p.mask_lo), me = std::min(lf[m + 1], p.mask_hi);
+      if (me <= mf) continue;
+      const double most = (double)(me - mf) * (double)D.G / (double)T;
       cand.push_back({h, most});
       wsum += most;
     }
@@ -1042,6 +1085,12 @@ int upload_tables(gakco_ctx* c, Work& w, Tables& t) {
     if ((rc = ensure(c, w, w.buf, (size_t)(bytes), #buf)) != GAKCO_OK) return rc; \
   } while (0)
 
+// The onesweep sort takes digits of at most 8 bits (one look-back thread
+// per digit) and at most kOsMaxPasses passes.
+bool use_onesweep(const gakco_ctx* c) {
+  return c->sort_mode == 1 && c->radix_bits <= 8 && (64 + c->radix_bits - 1) / c->radix_bits <= kOsMaxPasses;
+}
+
 // Sort / run-length buffers for the plan's largest chunk.
 int ensure_sort_buffers(gakco_ctx* c, Work& w, const Plan& p) {
   int rc;
@@ -1062,6 +1111,11 @@ int ensure_sort_buffers(gakco_ctx* c, Work& w, const Plan& p) {
   ENSURE(efid, te * 4);
   ENSURE(fstart, te * 4);
   ENSURE(status, 128);
+  if (use_onesweep(c)) {
+    ENSURE(osst, p.max_chunk_tiles * kOsRadix * 8);
+    ENSURE(osctr, (p.total_passes + 1) * 4);
+    ENSURE(oscnt, p.max_chunk_nseg * kOsMaxPasses * kOsRadix * 4);
+  }
   return GAKCO_OK;
 }
 
@@ -1258,21 +1312,60 @@ void enqueue_chunk(gakco_ctx* c, Work& w, const Plan& p, const Chunk& ch, Tail t
   void* kin = kbuf[1];  // the first pass extracts the masked keys here
   const uint32_t* vin = (const uint32_t*)w.wid.p;  // first-pass payload: window ids
   int cur = 0;
-  for (size_t q = 0; q < ch.passes.size(); ++q) {
-    Bracket b(c, w, "sort_pass", 4);
-    launch_sort_pass(ch.wide, q == 0, segs, ch.nseg, tseg, ch.ntiles, masks,
-                     (const uint64_t*)w.fullkey.p, kin, vin, kbuf[cur], vbuf[cur],
-                     (uint32_t*)w.hist.p, (uint32_t*)w.dtot.p, ch.passes[q].first, ch.passes[q].second, w.cs);
-    kin = kbuf[cur];
-    vin = vbuf[cur];
-    cur ^= 1;
+  if (use_onesweep(c) && ch.passes.size() <= (size_t)kOsMaxPasses) {
+    const int np = (int)ch.passes.size();
+    OsPasses ps{};
+    ps.np = np;
+    for (int q = 0; q < np; ++q) {
+      ps.shift[q] = ch.passes[q].first;
+      ps.bits[q] = ch.passes[q].second;
+    }
+    // Status words are told apart by their pass's epoch (1..65535); they
+    // are cleared at the plan's first chunk, whenever the epochs wrap and
+    // for every chunk of the plain engine (which visits chunks out of plan
+    // order).
+    constexpr uint64_t kEpochs = 65535;
+    const bool wrap = ch.pass0 > 0 && (ch.pass0 + np - 1) / kEpochs != (ch.pass0 - 1) / kEpochs;
+    if (ch.pass0 == 0 || wrap || c->engine == 1) {
+      cudaMemsetAsync(w.osst.p, 0, (size_t)p.max_chunk_tiles * kOsRadix * 8, w.cs);
+      if (ch.pass0 == 0 || c->engine == 1) cudaMemsetAsync(w.osctr.p, 0, (size_t)(p.total_passes + 1) * 4, w.cs);
+    }
+    cudaMemsetAsync(w.oscnt.p, 0, (size_t)ch.nseg * np * kOsRadix * 4, w.cs);
+    {
+      Bracket b(c, w, "sort_pass", 2);
+      launch_os_hist(ch.wide, segs, ch.nseg, tseg, ch.ntiles, masks, (const uint64_t*)w.fullkey.p, kin,
+                     (uint32_t*)w.oscnt.p, ps, w.cs);
+    }
+    for (int q = 0; q < np; ++q) {
+      Bracket b(c, w, "sort_pass", 1);
+      const uint64_t pass = ch.pass0 + (uint64_t)q;
+      launch_os_scatter(ch.wide, q == 0, segs, tseg, ch.ntiles, kin, vin, kbuf[cur], vbuf[cur],
+                        (const uint32_t*)w.oscnt.p, np, q, ch.passes[q].first, ch.passes[q].second,
+                        (uint64_t*)w.osst.p, (uint32_t*)w.osctr.p + pass, (uint32_t)(pass % kEpochs + 1),
+                        (uint32_t*)w.status.p, w.cs);
+      kin = kbuf[cur];
+      vin = vbuf[cur];
+      cur ^= 1;
+    }
+  } else {
+    for (size_t q = 0; q < ch.passes.size(); ++q) {
+      Bracket b(c, w, "sort_pass", 4);
+      launch_sort_pass(ch.wide, q == 0, segs, ch.nseg, tseg, ch.ntiles, masks,
+                       (const uint64_t*)w.fullkey.p, kin, vin, kbuf[cur], vbuf[cur],
+                       (uint32_t*)w.hist.p, (uint32_t*)w.dtot.p, ch.passes[q].first, ch.passes[q].second,
+                       w.cs);
+      kin = kbuf[cur];
+      vin = vbuf[cur];
+      cur ^= 1;
+    }
   }
   if (tail == Tail::kGram) {
     {
       Bracket b(c, w, "run_length", 4);
       launch_rle_gram(ch.wide, segs, ch.nseg, tseg, ch.ntiles, kin, vin, (const DsPack*)(base + p.o_pack),
                       (uint32_t*)w.tcnt.p, (uint32_t*)w.segtot.p, (uint32_t*)w.trec.p, (uint32_t*)w.ewin.p,
-                      (uint32_t*)w.eseq.p, (uint32_t*)w.efe.p, w.cs);
+                      (uint32_t*)w.eseq.p, (uint32_t*)w.efe.p,
+                      (unsigned long long*)((uint8_t*)w.status.p + 64) + 3, w.cs);
     }
     if (!p.heavy.empty() && p.heavy_level[ch.level]) {
       Bracket b(c, w, "heavy_mark", 1);
@@ -1387,6 +1480,14 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
       launch_accum(a, c->accum_threads, p.acc_blocks, p.acc_smem, w.cs);
     }
     if (fork) cudaStreamWaitEvent(w.cs, w.ev_join, 0);
+    if (p.partial_C) {
+      // A partial Gram: this slice's C_0..C_M (upper triangles) go to the
+      // caller, who sums the slices and finishes with gakco_combine_device.
+      if (p.c_elems) cudaMemcpyAsync(p.partial_C, w.Cacc.p, p.c_elems * 4, cudaMemcpyDeviceToDevice, w.cs);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return wcuda(w, e, "kernel launch");
+      return GAKCO_OK;
+    }
     {
       Bracket b(c, w, "diag", 1);
       launch_diag((const DsInfo*)(base + p.o_info), (uint32_t)p.ds.size(), p.nseq, a, w.cs);
@@ -1446,6 +1547,7 @@ int check_status(gakco_ctx* c, Work& w) {
   w.pairs = (double)wk[0];
   w.entries = (double)wk[1];
   w.windows = (double)wk[2];
+  w.rle_entries = (double)wk[3];
   w.heavy_cols = (double)wk[4];
   w.heavy_flops = (double)wk[5];
   if (st & kErrBadCode) return wfail(w, GAKCO_E_INVALID, "input holds a symbol >= sigma (%d)", c->sigma);
@@ -1498,6 +1600,9 @@ int run_gram(gakco_ctx* c, Plan& p, cudaStream_t user) {
   q.nmax = p.nmax;
   q.want_nm = p.want_nm;
   q.want_khat = p.want_khat;
+  q.mask_lo = p.mask_lo;
+  q.mask_hi = p.mask_hi;
+  q.partial_C = p.partial_C;
   int rc = run_gram_once(c, p, user);
   if (rc != GAKCO_OK && c->main.dense_overflow && c->dense != 0) {
     const int saved = c->dense;
@@ -1518,8 +1623,10 @@ int run_gram_once(gakco_ctx* c, Plan& p, cudaStream_t user) {
   c->ev_used = 0;
   c->last_replay = 0;
   c->last_mask_passes = 0;
-  p.first_level = (c->kernel_only && !p.want_nm && !plain) ? c->M : 0;
-  const int64_t masks_run = (int64_t)c->masks.size() - (int64_t)level_firsts(c)[p.first_level];
+  p.first_level = (c->kernel_only && !p.want_nm && !plain && !p.partial_C) ? c->M : 0;
+  const int64_t masks_run =
+      std::max<int64_t>(0, std::min<int64_t>((int64_t)c->masks.size(), (int64_t)p.mask_hi) -
+                               std::max<int64_t>((int64_t)level_firsts(c)[p.first_level], (int64_t)p.mask_lo));
   for (const DsHost& D : p.ds)
     if (D.G > 0) c->last_mask_passes += masks_run;
   if (p.ds.empty()) {
@@ -1530,7 +1637,7 @@ int run_gram_once(gakco_ctx* c, Plan& p, cudaStream_t user) {
   if (e == cudaSuccess) e = cudaStreamWaitEvent(w.cs, c->ev_in, 0);
   if (e != cudaSuccess) return wcuda(w, e, "stream ordering");
 
-  const bool graph = c->use_graph && !c->profile && !plain;
+  const bool graph = c->use_graph && !c->profile && !plain && !p.partial_C;
   const uint64_t key = graph ? plan_key(c, p, plain) : 0;
   int rc;
   if (graph && c->gexec && key == c->gkey) {
@@ -1549,6 +1656,10 @@ int run_gram_once(gakco_ctx* c, Plan& p, cudaStream_t user) {
     c->plan_dense_issued = p.dense_issued;
     c->plan_dense_bytes = p.dense_bytes;
     c->plan_sort_bytes = p.sort_bytes;
+    c->plan_rle_bytes = p.rle_bytes;
+    plan_io_bytes(c, p);
+    c->plan_pack_bytes = p.pack_bytes;
+    c->plan_combine_bytes = p.combine_bytes;
     plan_items(c, p);
     if (!plain) {
       const int nb = accum_blocks_per_sm(c->accum_threads, p.acc_smem);
@@ -1588,6 +1699,7 @@ int run_gram_once(gakco_ctx* c, Plan& p, cudaStream_t user) {
   c->last_windows = w.windows;
   c->last_heavy_cols = w.heavy_cols;
   c->last_heavy_flops = w.heavy_flops;
+  c->last_rle_entries = w.rle_entries;
   e = cudaEventRecord(c->ev_out, w.cs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(user, c->ev_out, 0);
   if (e != cudaSuccess && rc == GAKCO_OK) rc = wcuda(w, e, "stream ordering");
@@ -2563,6 +2675,10 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
       if (v < 128) return fail(c, GAKCO_E_INVALID, "dense run columns must be >= 128");
       c->dense_run_cols = v;
       break;
+    case GAKCO_OPT_SORT:
+      if (v != 0 && v != 1) return fail(c, GAKCO_E_INVALID, "sort must be 0 or 1");
+      c->sort_mode = (int)v;
+      break;
     case GAKCO_OPT_DENSE_ROUND_SUM:
       if (v < 1 || v > (int64_t)kDenseExactSum)
         return fail(c, GAKCO_E_INVALID, "dense round sum must be 1..%u", kDenseExactSum);
@@ -2633,6 +2749,18 @@ int gakco_get_stat(const gakco_ctx* c, int key, double* v) {
     case GAKCO_STAT_HEAVY_FLOPS:
       *v = c->last_heavy_flops;
       return GAKCO_OK;
+    case GAKCO_STAT_MASKS:
+      *v = (double)c->masks.size();
+      return GAKCO_OK;
+    case GAKCO_STAT_RLE_BYTES:
+      *v = c->plan_rle_bytes + 8.0 * c->last_rle_entries;
+      return GAKCO_OK;
+    case GAKCO_STAT_PACK_BYTES:
+      *v = c->plan_pack_bytes;
+      return GAKCO_OK;
+    case GAKCO_STAT_COMBINE_BYTES:
+      *v = c->plan_combine_bytes;
+      return GAKCO_OK;
     case GAKCO_STAT_SORT_BYTES:
       *v = c->plan_sort_bytes;
       return GAKCO_OK;
@@ -2689,6 +2817,89 @@ int gakco_gram_batch_device(gakco_ctx* c, int32_t nd, const uint8_t* const* code
 int gakco_gram_device(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t n,
                       int32_t* K, double* Khat, int32_t* Nm, void* stream) {
   return gakco_gram_batch_device(c, 1, &codes, &offsets, &n, &K, &Khat, &Nm, stream);
+}
+
+int gakco_gram_partial_device(gakco_ctx* c, const uint8_t* codes, const int64_t* offsets, int32_t n,
+                              int32_t mask_begin, int32_t mask_end, uint32_t* C, void* stream) {
+  if (!c) return GAKCO_E_INVALID;
+  c->err.clear();
+  const int32_t nmask = (int32_t)c->masks.size();
+  if (mask_begin < 0 || mask_end < mask_begin || mask_end > nmask)
+    return fail(c, GAKCO_E_INVALID, "mask slice [%d, %d) outside [0, %d)", mask_begin, mask_end, nmask);
+  if (c->engine != 0) return fail(c, GAKCO_E_INVALID, "partial Gram calls need the batched engine");
+  if (n > 0 && !C) return fail(c, GAKCO_E_INVALID, "partial Gram calls need a C buffer");
+  Plan p;
+  int32_t* kk = (int32_t*)C;  // passes the device-call check; no K is written
+  int rc = plan_datasets(c, c->main, p, 1, &codes, &offsets, &n, &kk, nullptr, nullptr, true);
+  if (rc == GAKCO_OK) {
+    for (DsHost& D : p.ds) D.K = nullptr;
+    p.mask_lo = (uint32_t)mask_begin;
+    p.mask_hi = (uint32_t)mask_end;
+    p.partial_C = C;
+    if (n > 0 && mask_end == mask_begin) {
+      // An empty slice adds nothing: its C is all zero.
+      cudaError_t e = cudaMemsetAsync(C, 0, (size_t)(c->M + 1) * n * n * 4, (cudaStream_t)stream);
+      if (e != cudaSuccess) return ret(c, c->main, wcuda(c->main, e, "clear C"));
+      c->last_mask_passes = 0;
+      c->last_launches = 0;
+      return GAKCO_OK;
+    }
+    rc = run_gram(c, p, (cudaStream_t)stream);
+  }
+  return ret(c, c->main, rc);
+}
+
+int gakco_combine_device(gakco_ctx* c, const uint32_t* C, int32_t n, int32_t* K, double* Khat,
+                         int32_t* Nm, void* stream) {
+  if (!c) return GAKCO_E_INVALID;
+  c->err.clear();
+  if (n < 0 || n > 65535) return fail(c, GAKCO_E_INVALID, "n = %d outside [0, 65535]", n);
+  if (n == 0) return GAKCO_OK;
+  if (!C || !K) return fail(c, GAKCO_E_INVALID, "combine needs C and K");
+  Work& w = c->main;
+  int rc;
+  // The table area and the norms buffer are rewritten: a cached Gram graph
+  // would replay with them.
+  drop_graph(c);
+  auto run = [&]() -> int {
+    ENSURE(rinv, (size_t)n * 8);
+    ENSURE(status, 128);
+    Tables t;
+    DsInfo in{};
+    in.K = K;
+    in.Nm = Nm;
+    in.Khat = Khat;
+    in.rinv = (double*)w.rinv.p;
+    in.C = const_cast<uint32_t*>(C);
+    in.n = (uint32_t)n;
+    const size_t o_info = t.add(&in, sizeof in);
+    if ((rc = upload_tables(c, w, t)) != GAKCO_OK) return rc;
+    cudaStream_t user = (cudaStream_t)stream;
+    cudaError_t e = cudaEventRecord(c->ev_in, user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(w.cs, c->ev_in, 0);
+    if (e != cudaSuccess) return wcuda(w, e, "stream ordering");
+    cudaMemsetAsync(w.status.p, 0, 128, w.cs);
+    c->timed.clear();
+    c->ev_used = 0;
+    AccParams a{};  // the tail kernels read only the coefficients and the status word
+    a.M = (uint32_t)c->M;
+    a.status = (uint32_t*)w.status.p;
+    memcpy(a.h, c->h, sizeof a.h);
+    memcpy(a.ie, c->ie, sizeof a.ie);
+    const DsInfo* d_info = (const DsInfo*)((uint8_t*)w.tables.p + o_info);
+    const uint32_t nt = (uint32_t)((n + 31) / 32);
+    launch_diag(d_info, 1, (uint32_t)n, a, w.cs);
+    launch_combine(d_info, 1, nt * nt, a, Nm != nullptr, Khat != nullptr, w.cs);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return wcuda(w, e, "kernel launch");
+    c->last_launches = 2;
+    rc = sync_and_check(c, w);
+    e = cudaEventRecord(c->ev_out, w.cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(user, c->ev_out, 0);
+    if (e != cudaSuccess && rc == GAKCO_OK) rc = wcuda(w, e, "stream ordering");
+    return rc;
+  };
+  return ret(c, w, run());
 }
 
 int gakco_autotune(gakco_ctx* c, int32_t nd, const uint8_t* const* codes,

@@ -362,6 +362,200 @@ k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
   }
 }
 
+// -------------------------------------------------------------- onesweep --
+//
+// The same stable LSD sort with one read of the keys per pass (Adinets and
+// Merrill, "Onesweep: a faster least significant digit radix sort for GPUs",
+// 2022): k_os_hist cuts the masked keys out of the full g-mer keys and
+// counts the digits of every pass of every segment at once; k_os_base turns
+// the counts into each digit's start in its segment; then one k_os_scatter
+// launch per pass ranks each tile exactly as k_downsweep does and finds its
+// digits' offsets among the segment's earlier tiles by a decoupled
+// look-back: every tile publishes, per digit, first its own count
+// (aggregate) and then its inclusive prefix, and a tile sums its
+// predecessors' published values, newest first, until it meets a prefix.
+// Tiles are taken in order from a counter, so a tile only ever waits on
+// tiles that running or finished blocks have taken.  Waits are bounded: a
+// wait that runs out raises kErrTimeout (the result is then invalid and the
+// call fails) and the tile goes on.
+//
+// A status word holds (epoch << 48) | (kind << 46) | value: the epoch
+// numbers the pass within the call (the words are cleared once per call),
+// the kind is 1 for an aggregate and 2 for an inclusive prefix.
+
+constexpr uint64_t kOsAgg = 1ull << 46, kOsIncl = 2ull << 46;
+constexpr uint64_t kOsValue = (1ull << 46) - 1;
+constexpr long long kOsWaitCycles = 4000000000ll;  // about 2 s
+
+__device__ __forceinline__ void os_store(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t os_load(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(kSortThreads)
+k_os_hist(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg,
+          const MaskDesc* __restrict__ masks, const uint64_t* __restrict__ fullkey,
+          KeyT* __restrict__ kx, uint32_t* __restrict__ dcount, OsPasses ps) {
+  __shared__ uint32_t sh[kOsMaxPasses * kOsRadix];
+  __shared__ MaskDesc md;
+  __shared__ uint32_t s_shift[kOsMaxPasses], s_mask[kOsMaxPasses];
+  const uint32_t t = blockIdx.x;
+  const uint32_t sx = tile_seg[t];
+  const SegDesc sd = segs[sx];
+  const uint32_t lt = t - sd.tile0;
+  if (threadIdx.x == 0) md = masks[sd.mask];
+  if (threadIdx.x < (uint32_t)ps.np) {
+    s_shift[threadIdx.x] = (uint32_t)ps.shift[threadIdx.x];
+    s_mask[threadIdx.x] = (1u << ps.bits[threadIdx.x]) - 1u;
+  }
+  for (uint32_t i = threadIdx.x; i < (uint32_t)ps.np * kOsRadix; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  MaskRegs mr;
+  mask_regs(md, mr);
+  const uint64_t beg = (uint64_t)lt * kTile;
+  const uint32_t cnt = (uint32_t)min((uint64_t)kTile, sd.G - beg);
+  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const KeyT key = (KeyT)masked_key_r(fullkey[sd.win0 + beg + i], mr, md);
+    kx[sd.base + beg + i] = key;
+    for (int q = 0; q < ps.np; ++q) atomicAdd(&sh[q * kOsRadix + ((uint32_t)(key >> s_shift[q]) & s_mask[q])], 1u);
+  }
+  __syncthreads();
+  uint32_t* __restrict__ dc = dcount + (uint64_t)sx * ps.np * kOsRadix;
+  for (uint32_t i = threadIdx.x; i < (uint32_t)ps.np * kOsRadix; i += blockDim.x)
+    if (sh[i]) atomicAdd(&dc[i], sh[i]);
+}
+
+// Grid (segments, passes): each digit's start in its segment, in place.
+__global__ void __launch_bounds__(kSortThreads)
+k_os_base(uint32_t* __restrict__ dcount, int np) {
+  __shared__ uint32_t sw[kWarps + 1];
+  uint32_t* __restrict__ d = dcount + ((uint64_t)blockIdx.x * np + blockIdx.y) * kOsRadix;
+  static_assert(kOsRadix == kSortThreads, "one digit per thread");
+  const uint32_t v = d[threadIdx.x];
+  d[threadIdx.x] = block_excl_scan(v, sw, nullptr);
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 3 : 4)
+k_os_scatter(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg,
+             const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin, bool first,
+             KeyT* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* __restrict__ dbase,
+             int np, int q, int shift, int rbits, uint64_t* __restrict__ st, uint32_t* __restrict__ ctr,
+             uint32_t epoch, uint32_t* __restrict__ status) {
+  extern __shared__ __align__(16) uint32_t sh[];
+  __shared__ uint32_t sw[kWarps + 1];
+  __shared__ uint32_t s_tile;
+  const uint32_t radix = 1u << rbits;
+  uint32_t* wc = sh;                     // kWarps x radix running counts
+  uint32_t* gb = sh + kWarps * radix;    // global position of each digit's first element, minus
+                                         // its tile-local start
+  uint32_t* ts = gb + radix;             // the tile's count of each digit
+  KeyT* skey = (KeyT*)(ts + radix);      // tile in digit order
+  uint32_t* sval = (uint32_t*)(skey + kTile);
+  if (threadIdx.x == 0) s_tile = atomicAdd(ctr, 1u);
+  for (uint32_t i = threadIdx.x; i < kWarps * radix; i += blockDim.x) wc[i] = 0;
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const uint32_t sx = tile_seg[t];
+  const SegDesc sd = segs[sx];
+  const uint32_t lt = t - sd.tile0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint64_t beg = (uint64_t)lt * kTile;
+  const uint32_t cnt = (uint32_t)min((uint64_t)kTile, sd.G - beg);
+  const KeyT* __restrict__ ki = kin + sd.base + beg;
+  const uint32_t* __restrict__ vi = vin + (first ? sd.win0 : sd.base) + beg;
+  KeyT keys[kSortIpt];
+  uint32_t vals[kSortIpt];
+  uint32_t rk[kSortIpt];
+#pragma unroll
+  for (int j = 0; j < kSortIpt; ++j) {
+    const uint32_t idx = (uint32_t)w * 32 * kSortIpt + j * 32 + lane;
+    keys[j] = idx < cnt ? ki[idx] : (KeyT)0;
+    vals[j] = idx < cnt ? vi[idx] : 0u;
+  }
+  if (rbits <= 7)
+    rank_items<7>(keys, rk, cnt, w, lane, shift, radix, wc);
+  else
+    rank_items<8>(keys, rk, cnt, w, lane, shift, radix, wc);
+  __syncthreads();
+  // Per digit (one per thread): exclusive prefix over warps and the tile's
+  // count; publish the count, then look back for the earlier tiles' sum.
+  const uint32_t dg = threadIdx.x;
+  uint32_t run = 0;
+  if (dg < radix) {
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) {
+      const uint32_t c = wc[ww * radix + dg];
+      wc[ww * radix + dg] = run;
+      run += c;
+    }
+    ts[dg] = run;
+  }
+  const uint64_t E = (uint64_t)epoch << 48;
+  uint64_t* __restrict__ my = st + (uint64_t)t * kOsRadix;
+  uint32_t excl = 0;
+  if (dg < radix) {
+    if (lt == 0) {
+      os_store(&my[dg], E | kOsIncl | run);
+    } else {
+      os_store(&my[dg], E | kOsAgg | run);
+      uint32_t j = t - 1;
+      long long t0 = clock64();
+      for (;;) {
+        const uint64_t v = os_load(&st[(uint64_t)j * kOsRadix + dg]);
+        if ((v >> 48) == epoch && (v & (kOsAgg | kOsIncl))) {
+          excl += (uint32_t)(v & kOsValue);
+          if ((v & kOsIncl) || j == sd.tile0) break;  // (the segment's first tile always publishes a prefix)
+          --j;
+          t0 = clock64();
+        } else if (clock64() - t0 > kOsWaitCycles) {
+          atomicOr(status, kErrTimeout);
+          break;
+        }
+      }
+      os_store(&my[dg], E | kOsIncl | (uint64_t)(excl + run));
+    }
+  }
+  // Tile-local digit starts: exclusive scan of the counts, folded into the
+  // warps' offsets and the global positions.
+  const uint32_t pre = block_excl_scan(dg < radix ? run : 0u, sw, nullptr);
+  if (dg < radix) {
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) wc[ww * radix + dg] += pre;
+    gb[dg] = dbase[((uint64_t)sx * np + q) * kOsRadix + dg] + excl - pre;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kSortIpt; ++j) {
+    const uint32_t idx = (uint32_t)w * 32 * kSortIpt + j * 32 + lane;
+    if (idx < cnt) {
+      const uint32_t d = (uint32_t)(keys[j] >> shift) & (radix - 1);
+      const uint32_t lpos = wc[w * radix + d] + rk[j];
+      skey[lpos] = keys[j];
+      sval[lpos] = vals[j];
+    }
+  }
+  __syncthreads();
+  KeyT* __restrict__ ko = kout + sd.base;
+  uint32_t* __restrict__ vo = vout + sd.base;
+  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const KeyT k = skey[i];
+    const uint32_t pos = gb[(uint32_t)(k >> shift) & (radix - 1)] + i;
+    if (pos < sd.G) {  // (only a look-back that ran out can miss the segment)
+      ko[pos] = k;
+      vo[pos] = sval[i];
+    } else {
+      atomicOr(status, kErrBadEntry);
+    }
+  }
+}
+
 // ------------------------------------------------------------ run-length --
 
 // Loads the elements a warp owns in a tile (element w*32*IPT + j*32 + lane)
@@ -452,10 +646,11 @@ k_rle_count(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
 }
 
 // Exclusive scan of the (entries, features) counts of each segment's tiles;
-// totals go to segtot[2 * s] (E) and segtot[2 * s + 1] (F).
+// totals go to segtot[2 * s] (E) and segtot[2 * s + 1] (F), and E is added
+// to *ecount when it is given (the call's work figure).
 __global__ void __launch_bounds__(kSortThreads)
 k_rle_scan(const SegDesc* __restrict__ segs, uint32_t* __restrict__ tcnt,
-           uint32_t* __restrict__ segtot) {
+           uint32_t* __restrict__ segtot, unsigned long long* __restrict__ ecount) {
   __shared__ uint32_t sw[kWarps + 1];
   const uint32_t s = blockIdx.x;
   const SegDesc sd = segs[s];
@@ -478,6 +673,7 @@ k_rle_scan(const SegDesc* __restrict__ segs, uint32_t* __restrict__ tcnt,
   if (threadIdx.x == 0) {
     segtot[2 * s] = carry_e;
     segtot[2 * s + 1] = carry_f;
+    if (ecount) atomicAdd(ecount, (unsigned long long)carry_e);
   }
 }
 
@@ -783,7 +979,7 @@ void rle_head_t(const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg,
                 uint32_t* fstart, uint32_t* ewin, cudaStream_t st) {
   const KeyT* k = (const KeyT*)keys;
   k_rle_count<KeyT><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, k, vals, tcnt);
-  k_rle_scan<<<nsegs, kSortThreads, 0, st>>>(segs, tcnt, segtot);
+  k_rle_scan<<<nsegs, kSortThreads, 0, st>>>(segs, tcnt, segtot, nullptr);
   k_rle_emit<KeyT><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, k, vals, dsp, tcnt,
                                                     estart, etseq, efid, fstart, ewin);
 }
@@ -792,10 +988,10 @@ template <typename KeyT>
 void rle_gram_t(const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg, uint32_t ntiles,
                 const void* keys, const uint32_t* vals, const DsPack* dsp, uint32_t* tcnt,
                 uint32_t* segtot, uint32_t* trec, uint32_t* ewin, uint32_t* eseq, uint32_t* efe,
-                cudaStream_t st) {
+                unsigned long long* ecount, cudaStream_t st) {
   const KeyT* k = (const KeyT*)keys;
   k_rle_count<KeyT><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, k, vals, tcnt);
-  k_rle_scan<<<nsegs, kSortThreads, 0, st>>>(segs, tcnt, segtot);
+  k_rle_scan<<<nsegs, kSortThreads, 0, st>>>(segs, tcnt, segtot, ecount);
   k_rle_emit_gram<KeyT><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, k, vals, dsp, tcnt, trec,
                                                          ewin, eseq, efe);
   k_rle_fix<<<(ntiles + 7) / 8, 256, 0, st>>>(segs, tile_seg, ntiles, segtot, trec, eseq, efe);
@@ -811,6 +1007,9 @@ int prep_init() {
   e = e ? e : cudaFuncSetAttribute(k_downsweep<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   e = e ? e : cudaFuncSetAttribute(k_downsweep<uint64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   e = e ? e : cudaFuncSetAttribute(k_downsweep<uint64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  const int os = (int)downsweep_smem(8, 8);
+  e = e ? e : cudaFuncSetAttribute(k_os_scatter<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, os);
+  e = e ? e : cudaFuncSetAttribute(k_os_scatter<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, os);
   return (int)e;
 }
 
@@ -819,6 +1018,33 @@ void launch_pack(const DsPack* d_ds, uint32_t nds, uint32_t nseq_total, int g,
                  uint32_t* status, cudaStream_t st) {
   if (nseq_total == 0) return;
   k_pack<<<nseq_total, 128, 0, st>>>(d_ds, nds, g, bits, sigma, fullkey, wid, status);
+}
+
+void launch_os_hist(bool wide, const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg,
+                    uint32_t ntiles, const MaskDesc* masks, const uint64_t* fullkey, void* kx,
+                    uint32_t* dcount, const OsPasses& ps, cudaStream_t st) {
+  if (ntiles == 0) return;
+  if (wide)
+    k_os_hist<uint64_t><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, masks, fullkey, (uint64_t*)kx, dcount, ps);
+  else
+    k_os_hist<uint32_t><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, masks, fullkey, (uint32_t*)kx, dcount, ps);
+  k_os_base<<<dim3(nsegs, ps.np), kSortThreads, 0, st>>>(dcount, ps.np);
+}
+
+void launch_os_scatter(bool wide, bool first, const SegDesc* segs, const uint32_t* tile_seg,
+                       uint32_t ntiles, const void* kin, const uint32_t* vin, void* kout,
+                       uint32_t* vout, const uint32_t* dbase, int np, int q, int shift, int rbits,
+                       uint64_t* st, uint32_t* ctr, uint32_t epoch, uint32_t* status, cudaStream_t stm) {
+  if (ntiles == 0) return;
+  const size_t smem = downsweep_smem(rbits, wide ? 8 : 4);
+  if (wide)
+    k_os_scatter<uint64_t><<<ntiles, kSortThreads, smem, stm>>>(segs, tile_seg, (const uint64_t*)kin, vin, first,
+                                                                (uint64_t*)kout, vout, dbase, np, q, shift, rbits,
+                                                                st, ctr, epoch, status);
+  else
+    k_os_scatter<uint32_t><<<ntiles, kSortThreads, smem, stm>>>(segs, tile_seg, (const uint32_t*)kin, vin, first,
+                                                                (uint32_t*)kout, vout, dbase, np, q, shift, rbits,
+                                                                st, ctr, epoch, status);
 }
 
 void launch_sort_pass(bool wide, bool first, const SegDesc* segs,
@@ -853,14 +1079,14 @@ void launch_rle_head(bool wide, const SegDesc* segs, uint32_t nsegs,
 void launch_rle_gram(bool wide, const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg,
                      uint32_t ntiles, const void* keys, const uint32_t* vals, const DsPack* dsp,
                      uint32_t* tcnt, uint32_t* segtot, uint32_t* trec, uint32_t* ewin,
-                     uint32_t* eseq, uint32_t* efe, cudaStream_t st) {
+                     uint32_t* eseq, uint32_t* efe, unsigned long long* ecount, cudaStream_t st) {
   if (ntiles == 0) return;
   if (wide)
     rle_gram_t<uint64_t>(segs, nsegs, tile_seg, ntiles, keys, vals, dsp, tcnt, segtot, trec, ewin,
-                         eseq, efe, st);
+                         eseq, efe, ecount, st);
   else
     rle_gram_t<uint32_t>(segs, nsegs, tile_seg, ntiles, keys, vals, dsp, tcnt, segtot, trec, ewin,
-                         eseq, efe, st);
+                         eseq, efe, ecount, st);
 }
 
 void launch_rle_final(const SegDesc* segs, const uint32_t* tile_seg, uint32_t ntiles,

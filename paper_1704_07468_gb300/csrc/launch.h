@@ -36,6 +36,30 @@ void launch_sort_pass(bool wide, bool first, const SegDesc* segs,
                       const uint32_t* vin, void* kout, uint32_t* vout,
                       uint32_t* hist, uint32_t* dtot, int shift, int rbits, cudaStream_t st);
 
+// Onesweep form of the same sort (digits of at most 8 bits): the digit
+// counts of every pass of a chunk in one read of the keys, then one scatter
+// per pass with a decoupled look-back.
+constexpr int kOsMaxPasses = 8;
+constexpr int kOsRadix = 256;
+struct OsPasses {
+  int np;
+  int shift[kOsMaxPasses];
+  int bits[kOsMaxPasses];
+};
+// Cuts the masked keys into kx and adds every pass's digit counts of each
+// segment into dcount[(segment * np + pass) * kOsRadix + digit] (zeroed by
+// the caller), then turns them into each digit's start in its segment.
+void launch_os_hist(bool wide, const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg,
+                    uint32_t ntiles, const MaskDesc* masks, const uint64_t* fullkey, void* kx,
+                    uint32_t* dcount, const OsPasses& ps, cudaStream_t st);
+// Pass q: tiles taken in order from *ctr (zero before the launch); st holds
+// kOsRadix status words per tile, whose epochs must differ from `epoch`
+// (1..65535) unless written by this pass.
+void launch_os_scatter(bool wide, bool first, const SegDesc* segs, const uint32_t* tile_seg,
+                       uint32_t ntiles, const void* kin, const uint32_t* vin, void* kout,
+                       uint32_t* vout, const uint32_t* dbase, int np, int q, int shift, int rbits,
+                       uint64_t* st, uint32_t* ctr, uint32_t epoch, uint32_t* status, cudaStream_t stm);
+
 // Run-length pass over sorted segments: entries (feature, sequence, count)
 // and features (runs of equal keys).  Writes, per segment, ewin / eseq /
 // efe into the pools.
@@ -95,11 +119,12 @@ void launch_rle_head(bool wide, const SegDesc* segs, uint32_t nsegs,
                      uint32_t* etseq, uint32_t* efid, uint32_t* fstart,
                      uint32_t* ewin, cudaStream_t st);
 // Gram engine: count/scan, then ewin, eseq and efe written directly, and
-// the tile-end fix-up; trec holds kRecWords words per tile.
+// the tile-end fix-up; trec holds kRecWords words per tile.  The chunk's
+// entries are added to *ecount.
 void launch_rle_gram(bool wide, const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg,
                      uint32_t ntiles, const void* keys, const uint32_t* vals, const DsPack* dsp,
                      uint32_t* tcnt, uint32_t* segtot, uint32_t* trec, uint32_t* ewin,
-                     uint32_t* eseq, uint32_t* efe, cudaStream_t st);
+                     uint32_t* eseq, uint32_t* efe, unsigned long long* ecount, cudaStream_t st);
 void launch_rle_final(const SegDesc* segs, const uint32_t* tile_seg, uint32_t ntiles,
                       const uint32_t* segtot, const uint32_t* estart,
                       const uint32_t* etseq, const uint32_t* efid,

@@ -100,6 +100,44 @@ def test_tuning_options_do_not_change_results(opts):
     _check(_gram(20, 8, 4, codes, off, **opts), ref)
 
 
+SORT_CASES = [  # (seed, n, sigma, lo, hi, g, k, options): the onesweep sort
+    (40, 70, 20, 0, 300, 8, 4, {}),                       # protein alphabet, 31-bit folded keys
+    (41, 50, 36, 5, 300, 8, 5, {}),                       # text, 64-bit keys (wide)
+    (42, 60, 4, 0, 260, 10, 6, {"radix_bits": 6}),        # 6-bit digits, 3-4 passes
+    (43, 40, 4, 50, 200, 10, 6, {"chunk_elems": 4096}),   # one tile per chunk: many chunks and epochs
+    (44, 300, 4, 100, 300, 10, 6, {"chunk_elems": 1 << 16}),  # many tiles per segment: long look-backs
+    (45, 20, 5, 1, 90, 5, 5, {}),                         # M = 0
+    (46, 30, 4, 0, 200, 8, 4, {"radix_bits": 11}),        # wider digits: the classic sort runs
+]
+
+
+@pytest.mark.parametrize("case", SORT_CASES)
+@pytest.mark.parametrize("engine", [0, 1])
+def test_onesweep_sort_bit_exact(case, engine):
+    seed, n, sigma, lo, hi, g, k, opts = case
+    codes, off = synth.random_small(seed, n, sigma, lo, hi)
+    ref = oracle.gram(codes, off, g, k)
+    _check(_gram(sigma, g, k, codes, off, sort=1, engine=engine, **opts), ref)
+
+
+def test_onesweep_fit_cross_and_graph_replay():
+    """The fitted index and the cross kernel sort through the same path;
+    a replayed Gram graph clears and renumbers the look-back words."""
+    codes, off = synth.random_small(47, 120, 20, 20, 400)
+    tcodes, toff = synth.random_small(48, 17, 20, 0, 300)
+    ref = oracle.gram(codes, off, 8, 4)
+    xref = oracle.cross(tcodes, toff, codes, off, 8, 4)
+    with pkg.gakco_create(20, 8, 4) as ctx:
+        ctx.set_option("sort", 1)
+        a = ctx.gram(codes, off, khat=True, nm=True)
+        b = ctx.gram(codes, off, khat=True, nm=True)
+        ctx.fit(codes, off)
+        x = ctx.cross_fitted(tcodes, toff, khat=True)
+    _check(a, ref)
+    _check(b, ref)
+    np.testing.assert_array_equal(x["K"], xref["K"])
+
+
 @pytest.mark.parametrize("kind", ["homopolymer", "period2", "mixed"])
 def test_repetitive_sequences_large_counts(kind):
     """Counts of one feature in one sequence far above 127."""

@@ -168,6 +168,26 @@ def test_mask_counting_route_equals_oracle(case):
 
 
 @pytest.mark.parametrize("case", CASES[:4])
+def test_oracle_counting_route_equals_brute_force(case):
+    """The oracle's own per-mask counting route (used to check sharded
+    computations) against its brute-force Hamming histogram, through Eq. 9,
+    and summed over any split of the masks."""
+    seed, n, sigma, lo, hi, g = case
+    codes, off = synth.random_small(seed, n, sigma, lo, hi)
+    M = g - 1 if g > 1 else 0
+    masks = oracle.position_masks(g, M)
+    assert len(masks) == sum(comb(g, m) for m in range(M + 1))
+    assert masks == sorted(masks, key=lambda d: (len(d), d))
+    C = oracle.cumulative_profile(codes, off, g, M)
+    np.testing.assert_array_equal(oracle.inclusion_exclusion(C, g),
+                                  oracle.mismatch_profile(codes, off, g, M))
+    cut = len(masks) // 3
+    parts = (oracle.cumulative_profile(codes, off, g, M, masks[:cut])
+             + oracle.cumulative_profile(codes, off, g, M, masks[cut:]))
+    np.testing.assert_array_equal(parts, C)
+
+
+@pytest.mark.parametrize("case", CASES[:4])
 def test_kernel_equals_top_level_cumulative_profile(case):
     """sum_m C(g-m, k) N_m equals C_M with M = g - k, because C(g-m, k) =
     C(g-m, M-m) is the coefficient of N_m in Eq. 8 at level M."""
