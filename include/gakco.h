@@ -181,6 +181,16 @@ const char *gakco_last_error(const gakco_ctx *ctx);
  * pass whose tiles find their digit offsets by a decoupled look-back
  * (digits of at most 8 bits; wider digits use 0). */
 #define GAKCO_OPT_SORT 26
+/* How the sparse accumulation (countAndUpdate, Alg. 1) walks a feature's
+ * entries when the range is shorter than a warp: 0 = up to four per lane
+ * directly, the rest in rounds of 32 whose owners a shuffle search finds;
+ * 1 = all in rounds of 32, owners from a warp-wide OR of range starts;
+ * 2 = the direct step of 0, then the rounds of 1.  Identical results; the
+ * autotuner picks one per workload (default 0). */
+#define GAKCO_OPT_ACCUM_VARIANT 27
+/* Elements per thread of the Gram call's run-length kernels: 16 (256-thread
+ * blocks, default) or 8 (512-thread blocks, fewer registers per thread). */
+#define GAKCO_OPT_RLE_ITEMS 28
 int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 
 /*

@@ -213,6 +213,8 @@ struct gakco_ctx {
   int overlap = 1;      // 1: dense and sparse levels of a Gram call run on two streams
   int dense_sms = 0;    // CTAs of the dense GEMM (0: one per SM)
   int sort_mode = 0;    // 0: upsweep / digit scans / downsweep per pass; 1: onesweep
+  int accum_variant = 0;  // how the accumulation walks short entry ranges (k_accum.cu)
+  int rle_items = 16;     // elements per thread of the Gram run-length kernels (16 or 8)
   int64_t dense_round_sum = kDenseExactSum;  // bound on a GEMM round's partial sums
   int64_t dense_wait_cycles = 0;             // GEMM role-wait limit (0: default)
   // Heavy features of sparse levels go to the tensor cores: threshold on a
@@ -1365,7 +1367,7 @@ void enqueue_chunk(gakco_ctx* c, Work& w, const Plan& p, const Chunk& ch, Tail t
       launch_rle_gram(ch.wide, segs, ch.nseg, tseg, ch.ntiles, kin, vin, (const DsPack*)(base + p.o_pack),
                       (uint32_t*)w.tcnt.p, (uint32_t*)w.segtot.p, (uint32_t*)w.trec.p, (uint32_t*)w.ewin.p,
                       (uint32_t*)w.eseq.p, (uint32_t*)w.efe.p,
-                      (unsigned long long*)((uint8_t*)w.status.p + 64) + 3, w.cs);
+                      (unsigned long long*)((uint8_t*)w.status.p + 64) + 3, c->rle_items, w.cs);
     }
     if (!p.heavy.empty() && p.heavy_level[ch.level]) {
       Bracket b(c, w, "heavy_mark", 1);
@@ -1477,7 +1479,7 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
     if (fork) cudaEventRecord(w.ev_join, w.cs2);
     {
       Bracket b(c, w, "accumulate", 1);
-      launch_accum(a, c->accum_threads, p.acc_blocks, p.acc_smem, w.cs);
+      launch_accum(a, c->accum_threads, c->accum_variant, p.acc_blocks, p.acc_smem, w.cs);
     }
     if (fork) cudaStreamWaitEvent(w.cs, w.ev_join, 0);
     if (p.partial_C) {
@@ -1662,7 +1664,7 @@ int run_gram_once(gakco_ctx* c, Plan& p, cudaStream_t user) {
     c->plan_combine_bytes = p.combine_bytes;
     plan_items(c, p);
     if (!plain) {
-      const int nb = accum_blocks_per_sm(c->accum_threads, p.acc_smem);
+      const int nb = accum_blocks_per_sm(c->accum_threads, c->accum_variant, p.acc_smem);
       if (nb <= 0)
         return wfail(w, GAKCO_E_CUDA, "accumulation kernel does not fit (%zu B shared)", p.acc_smem);
       p.acc_blocks = nb * c->nsm;
@@ -2321,6 +2323,8 @@ struct TuneChoice {
   int accum_threads;
   int64_t group_bytes;
   int dense;
+  int accum_variant;
+  int rle_items;
 };
 
 std::mutex g_tune_mu;
@@ -2366,6 +2370,8 @@ int autotune(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64_
       c->accum_threads = it->second.accum_threads;
       c->group_bytes = it->second.group_bytes;
       c->dense = it->second.dense;
+      c->accum_variant = it->second.accum_variant;
+      c->rle_items = it->second.rle_items;
       drop_graph(c);
       report = "cached";
       return GAKCO_OK;
@@ -2411,6 +2417,16 @@ int autotune(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64_
     if (t < best) best = t, best_ch = ch;
   }
   c->chunk_elems = best_ch;
+  // Elements per thread of the run-length kernels.
+  int best_ri = c->rle_items;
+  best = 1e30;
+  for (int ri : {16, 8}) {
+    if (rc != GAKCO_OK) break;
+    c->rle_items = ri;
+    if ((rc = trial("run_length", nullptr, t)) != GAKCO_OK) break;
+    if (t < best) best = t, best_ri = ri;
+  }
+  c->rle_items = best_ri;
   // Accumulation block size and mask-group bytes.
   int best_th = c->accum_threads;
   int64_t best_gb = c->group_bytes;
@@ -2436,16 +2452,27 @@ int autotune(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64_
     if (t < best) best = t, best_dense = dm;
   }
   c->dense = best_dense;
+  // How the accumulation walks short entry ranges, with the choices above.
+  int best_var = c->accum_variant;
+  best = 1e30;
+  for (int v : {0, 1, 2}) {
+    if (rc != GAKCO_OK) break;
+    c->accum_variant = v;
+    if ((rc = trial("accumulate", nullptr, t)) != GAKCO_OK) break;
+    if (t < best) best = t, best_var = v;
+  }
+  c->accum_variant = best_var;
   c->profile = saved_profile;
   c->engine = saved_engine;
   drop_graph(c);
   if (rc != GAKCO_OK) return rc;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = {best_rb, best_ch, best_th, best_gb, best_dense};
+    g_tune_cache[key] = {best_rb, best_ch, best_th, best_gb, best_dense, best_var, best_ri};
   }
-  snprintf(buf, sizeof buf, "radix_bits=%d chunk_elems=%lld accum_threads=%d group_bytes=%lld dense=%d", best_rb,
-           (long long)best_ch, best_th, (long long)best_gb, best_dense);
+  snprintf(buf, sizeof buf,
+           "radix_bits=%d chunk_elems=%lld rle_items=%d accum_threads=%d group_bytes=%lld dense=%d accum_variant=%d",
+           best_rb, (long long)best_ch, best_ri, best_th, (long long)best_gb, best_dense, best_var);
   report = buf;
   return GAKCO_OK;
 }
@@ -2674,6 +2701,14 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
     case GAKCO_OPT_DENSE_RUN_COLS:
       if (v < 128) return fail(c, GAKCO_E_INVALID, "dense run columns must be >= 128");
       c->dense_run_cols = v;
+      break;
+    case GAKCO_OPT_ACCUM_VARIANT:
+      if (v < 0 || v > 2) return fail(c, GAKCO_E_INVALID, "accumulation variant must be 0, 1 or 2");
+      c->accum_variant = (int)v;
+      break;
+    case GAKCO_OPT_RLE_ITEMS:
+      if (v != 8 && v != 16) return fail(c, GAKCO_E_INVALID, "run-length items must be 8 or 16");
+      c->rle_items = (int)v;
       break;
     case GAKCO_OPT_SORT:
       if (v != 0 && v != 1) return fail(c, GAKCO_E_INVALID, "sort must be 0 or 1");

@@ -69,13 +69,29 @@ __device__ __forceinline__ uint32_t ie_combine(const uint32_t* C, uint32_t M,
   return K;
 }
 
-template <int kThreads>
-__global__ void __launch_bounds__(kThreads)
+// kExpand chooses how a warp walks the entry ranges shorter than kLong
+// (results are identical; the autotuner picks per workload):
+//   0: up to four pairs per lane directly (each lane loads its own range),
+//      the rest in rounds of 32 pairs whose owner lanes are found by a
+//      shuffle binary search over the ranges' running counts;
+//   1: every pair in rounds of 32 (consecutive lanes load consecutive
+//      entries), owners found from a warp-wide OR of the range starts that
+//      fall in the round (no shuffles; the owners' data in a per-warp
+//      shared table);
+//   2: the direct step of 0, then the rounds of 1 for what is left.
+// Every variant is held to 32 registers, so that eight 256-thread blocks
+// stay resident per SM.
+template <int kThreads, int kExpand>
+__global__ void __launch_bounds__(kThreads, 2048 / kThreads)
 k_accum(const AccParams p) {
   extern __shared__ uint32_t acc[];   // ncols counters of one row of C_m + a trash slot
   __shared__ uint32_t s_item;
   constexpr int kWarps = kThreads / 32;
+  // Per warp: the chunk's non-empty entry ranges in lane order (first entry
+  // minus the range's first pair number, and the multiplier c_x).
+  __shared__ uint32_t s_rb[kWarps][32], s_rc[kWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_item = atomicAdd(p.counter, 1u);
@@ -160,9 +176,8 @@ k_accum(const AccParams p) {
         }
       }
       if (cnt >= kLong) cnt = 0;
-      // Short ranges: up to four pairs per lane directly, the rest of the
-      // range by a warp-wide expansion.
-      {
+      if constexpr (kExpand != 1) {
+        // Short ranges: up to four pairs per lane directly.
         const uint32_t s4 = min(cnt, 4u);
         uint32_t v[4];
 #pragma unroll
@@ -173,30 +188,70 @@ k_accum(const AccParams p) {
         lo += s4;
         cnt -= s4;
       }
-      if (__any_sync(kFull, cnt != 0)) {
-        uint32_t incl = cnt;
+      if constexpr (kExpand == 0) {
+        // The rest of the ranges in rounds of 32 pairs; the owner lane of a
+        // pair is the first lane whose inclusive count exceeds it.
+        if (__any_sync(kFull, cnt != 0)) {
+          uint32_t incl = cnt;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t t = __shfl_up_sync(kFull, incl, o);
-          if (lane >= o) incl += t;
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+          }
+          const uint32_t total = __shfl_sync(kFull, incl, 31);
+          const uint32_t excl = incl - cnt;
+          for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+            const uint32_t pp = p0 + lane;
+            uint32_t o = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+              const uint32_t t = __shfl_sync(kFull, incl, o + step - 1);
+              if (t <= pp) o += step;
+            }
+            const uint32_t lo_o = __shfl_sync(kFull, lo, o);
+            const uint32_t ex_o = __shfl_sync(kFull, excl, o);
+            const uint32_t c_o = __shfl_sync(kFull, c, o);
+            if (pp < total) {
+              const uint32_t v = es[lo_o + (pp - ex_o)];
+              atomicAdd(&acc[min((v >> 16) - c0, width)], c_o * (v & 0xFFFFu));
+            }
+          }
         }
-        const uint32_t total = __shfl_sync(kFull, incl, 31);
-        const uint32_t excl = incl - cnt;
-        for (uint32_t p0 = 0; p0 < total; p0 += 32) {
-          const uint32_t pp = p0 + lane;
-          uint32_t o = 0;  // owner lane: first lane whose inclusive count > pp
+      } else {
+        // Rounds of 32 pairs: round r gives lane i pair 32 r + i of the
+        // ranges laid end to end, so consecutive lanes load consecutive
+        // entries.  The ranges starting inside a round set one bit each in
+        // a warp-wide OR; a pair's owner is the round's first owner plus
+        // the starts at or before the pair.
+        const uint32_t nz = __ballot_sync(kFull, cnt != 0);
+        if (nz) {
+          uint32_t incl = cnt;
 #pragma unroll
-          for (int step = 16; step >= 1; step >>= 1) {
-            const uint32_t t = __shfl_sync(kFull, incl, o + step - 1);
-            if (t <= pp) o += step;
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
           }
-          const uint32_t lo_o = __shfl_sync(kFull, lo, o);
-          const uint32_t ex_o = __shfl_sync(kFull, excl, o);
-          const uint32_t c_o = __shfl_sync(kFull, c, o);
-          if (pp < total) {
-            const uint32_t v = es[lo_o + (pp - ex_o)];
-            atomicAdd(&acc[min((v >> 16) - c0, width)], c_o * (v & 0xFFFFu));
+          const uint32_t total = __shfl_sync(kFull, incl, 31);
+          const uint32_t start = incl - cnt;  // the range's first pair number
+          if (cnt) {
+            const uint32_t rank = __popc(nz & lt_mask);
+            s_rb[w][rank] = lo - start;
+            s_rc[w][rank] = c;
           }
+          __syncwarp();
+          uint32_t owner0 = 0;  // rank of the range holding the round's first pair
+          for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+            const uint32_t d = start - p0 - 1u;  // starts at p0 + 1 .. p0 + 32
+            const uint32_t bits = __reduce_or_sync(kFull, (cnt != 0 && d < 32u) ? (1u << d) : 0u);
+            const uint32_t pp = p0 + lane;
+            if (pp < total) {
+              const uint32_t o = owner0 + __popc(bits & lt_mask);
+              const uint32_t v = es[s_rb[w][o] + pp];
+              atomicAdd(&acc[min((v >> 16) - c0, width)], s_rc[w][o] * (v & 0xFFFFu));
+            }
+            owner0 += __popc(bits);
+          }
+          __syncwarp();
         }
       }
     }
@@ -454,36 +509,51 @@ k_ie_combine(const DsInfo* __restrict__ dsv, const uint32_t* __restrict__ Cg,
 
 int accum_max_threads() { return 1024; }
 
-template <int T>
+template <int T, int V>
 static void accum_t(const AccParams& p, int blocks, size_t smem, cudaStream_t st) {
-  k_accum<T><<<blocks, T, smem, st>>>(p);
+  k_accum<T, V><<<blocks, T, smem, st>>>(p);
 }
 
-void launch_accum(const AccParams& p, int threads, int blocks, size_t smem,
+template <int V>
+static void accum_v(const AccParams& p, int threads, int blocks, size_t smem, cudaStream_t st) {
+  if (threads == 256)
+    accum_t<256, V>(p, blocks, smem, st);
+  else if (threads == 1024)
+    accum_t<1024, V>(p, blocks, smem, st);
+  else
+    accum_t<512, V>(p, blocks, smem, st);
+}
+
+void launch_accum(const AccParams& p, int threads, int variant, int blocks, size_t smem,
                   cudaStream_t st) {
   if (p.nitems == 0) return;
-  if (threads == 256)
-    accum_t<256>(p, blocks, smem, st);
-  else if (threads == 1024)
-    accum_t<1024>(p, blocks, smem, st);
+  if (variant == 1)
+    accum_v<1>(p, threads, blocks, smem, st);
+  else if (variant == 2)
+    accum_v<2>(p, threads, blocks, smem, st);
   else
-    accum_t<512>(p, blocks, smem, st);
+    accum_v<0>(p, threads, blocks, smem, st);
 }
 
-int accum_blocks_per_sm(int threads, size_t smem) {
+template <int T, int V>
+static int accum_occ(size_t smem) {
   int nb = 0;
-  cudaError_t e;
-  if (threads == 256) {
-    e = cudaFuncSetAttribute(k_accum<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_accum<256>, 256, smem);
-  } else if (threads == 1024) {
-    e = cudaFuncSetAttribute(k_accum<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_accum<1024>, 1024, smem);
-  } else {
-    e = cudaFuncSetAttribute(k_accum<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_accum<512>, 512, smem);
-  }
+  cudaError_t e = cudaFuncSetAttribute(k_accum<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_accum<T, V>, T, smem);
   return e ? -1 : nb;
+}
+
+template <int V>
+static int accum_occ_v(int threads, size_t smem) {
+  if (threads == 256) return accum_occ<256, V>(smem);
+  if (threads == 1024) return accum_occ<1024, V>(smem);
+  return accum_occ<512, V>(smem);
+}
+
+int accum_blocks_per_sm(int threads, int variant, size_t smem) {
+  if (variant == 1) return accum_occ_v<1>(threads, smem);
+  if (variant == 2) return accum_occ_v<2>(threads, smem);
+  return accum_occ_v<0>(threads, smem);
 }
 
 void launch_finish(const DsInfo* d_ds, uint32_t nds, uint32_t ntiles, uint32_t M,

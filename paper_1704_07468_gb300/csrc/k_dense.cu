@@ -214,7 +214,7 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
     const uint32_t words = (uint32_t)(ld < (uint64_t)kDenseScatterCols ? ld : kDenseScatterCols) / 2;
     for (uint32_t i = tid; i < words / 4; i += kScatterThreads) ((uint4*)cnt)[i] = make_uint4(0, 0, 0, 0);
   }
-  uint32_t mx2 = 0;  // two 16-bit running maxima
+  uint32_t or2 = 0;  // OR of every count word: an upper bound of the largest count
   for (uint64_t c0 = 0; c0 < ld; c0 += kDenseScatterCols) {
     const uint32_t ncol = (uint32_t)(ld - c0 < (uint64_t)kDenseScatterCols ? ld - c0 : kDenseScatterCols);
     const uint32_t mu0 = (uint32_t)(c0 >> kb);
@@ -254,10 +254,13 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
       const uint4 a = cw[u];
       cw[u] = make_uint4(0, 0, 0, 0);
       const uint32_t w[4] = {a.x, a.y, a.z, a.w};
-      const uint32_t m = __vmaxu2(__vmaxu2(w[0], w[1]), __vmaxu2(w[2], w[3]));
-      mx2 = __vmaxu2(mx2, m);
+      // A 16-bit count c exceeds 16 iff c + 15 reaches bit 5 or c has bit
+      // 15 set (c + 15 then carries out of its half); both show in bits 5-15.
+      const uint32_t any = (a.x + 0x000F000Fu) | (a.y + 0x000F000Fu) | (a.z + 0x000F000Fu) |
+                           (a.w + 0x000F000Fu) | a.x | a.y | a.z | a.w;
+      or2 |= a.x | a.y | a.z | a.w;
       uint32_t e[4];
-      if ((m & 0xFFFFu) <= 16u && (m >> 16) <= 16u) {
+      if ((any & 0xFFE0FFE0u) == 0u) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) e[q] = e4m3x2_of_counts(w[q]);
       } else {
@@ -277,7 +280,7 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
     // The next chunk's counting waits at its first barrier for this
     // conversion (and its clearing) to finish.
   }
-  uint32_t mymax = min(max(mx2 & 0xFFFFu, mx2 >> 16), 16u);  // largest entry of A
+  uint32_t mymax = min((or2 & 0xFFFFu) | (or2 >> 16), 16u);  // >= the largest entry of A
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mymax = max(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
   if ((tid & 31) == 0 && mymax) atomicMax(P.maxc, mymax);

@@ -386,6 +386,10 @@ k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
 constexpr uint64_t kOsAgg = 1ull << 46, kOsIncl = 2ull << 46;
 constexpr uint64_t kOsValue = (1ull << 46) - 1;
 constexpr long long kOsWaitCycles = 4000000000ll;  // about 2 s
+#ifndef GK_OSB
+#define GK_OSB 8
+#endif
+constexpr int kOsBatch = GK_OSB;  // predecessor words loaded together in the look-back
 
 __device__ __forceinline__ void os_store(uint64_t* p, uint64_t v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -505,19 +509,35 @@ k_os_scatter(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile
       os_store(&my[dg], E | kOsIncl | run);
     } else {
       os_store(&my[dg], E | kOsAgg | run);
-      uint32_t j = t - 1;
-      long long t0 = clock64();
-      for (;;) {
-        const uint64_t v = os_load(&st[(uint64_t)j * kOsRadix + dg]);
-        if ((v >> 48) == epoch && (v & (kOsAgg | kOsIncl))) {
-          excl += (uint32_t)(v & kOsValue);
-          if ((v & kOsIncl) || j == sd.tile0) break;  // (the segment's first tile always publishes a prefix)
-          --j;
-          t0 = clock64();
-        } else if (clock64() - t0 > kOsWaitCycles) {
-          atomicOr(status, kErrTimeout);
-          break;
+      // Predecessors in batches of kOsBatch: their words are loaded
+      // together, then taken newest first; a word not yet published is
+      // polled until it is (the segment's first tile publishes a prefix at
+      // once, so the walk ends there at the latest).
+      uint32_t j = t;  // next predecessor is j - 1
+      bool done = false;
+      while (!done) {
+        const uint32_t nb = min((uint32_t)kOsBatch, j - sd.tile0);
+        uint64_t v[kOsBatch];
+#pragma unroll
+        for (int i = 0; i < kOsBatch; ++i)
+          v[i] = (uint32_t)i < nb ? os_load(&st[(uint64_t)(j - 1 - i) * kOsRadix + dg]) : 0ull;
+#pragma unroll
+        for (int i = 0; i < kOsBatch; ++i) {
+          if (done || (uint32_t)i >= nb) continue;
+          const long long t0 = clock64();
+          while (!((v[i] >> 48) == epoch && (v[i] & (kOsAgg | kOsIncl)))) {
+            if (clock64() - t0 > kOsWaitCycles) {
+              atomicOr(status, kErrTimeout);
+              v[i] = ((uint64_t)epoch << 48) | kOsIncl;  // give up: treat as a zero prefix
+              break;
+            }
+            v[i] = os_load(&st[(uint64_t)(j - 1 - i) * kOsRadix + dg]);
+          }
+          excl += (uint32_t)(v[i] & kOsValue);
+          if (v[i] & kOsIncl) done = true;
         }
+        j -= nb;
+        if (j == sd.tile0) done = true;
       }
       os_store(&my[dg], E | kOsIncl | (uint64_t)(excl + run));
     }
@@ -563,15 +583,15 @@ k_os_scatter(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile
 // sequence) pair changes, a new feature where the key changes.  The
 // predecessor comes from the neighbouring lane by shuffle; only the warp's
 // first element reads its predecessor from memory.
-template <typename KeyT>
+template <typename KeyT, int kIpt = kSortIpt>
 __device__ __forceinline__ void rle_load_flags(const SegDesc& sd, uint64_t beg, uint32_t cnt,
                                                int w, int lane,
                                                const KeyT* __restrict__ keys,
                                                const uint32_t* __restrict__ vals,
-                                               uint32_t (&vv)[kSortIpt], uint32_t& ne_bits,
+                                               uint32_t (&vv)[kIpt], uint32_t& ne_bits,
                                                uint32_t& nf_bits) {
   // Predecessor of the warp's first element.
-  const uint64_t first = beg + (uint64_t)w * 32 * kSortIpt;
+  const uint64_t first = beg + (uint64_t)w * 32 * kIpt;
   KeyT k_prev = 0;
   uint32_t s_prev = kNone;
   if (lane == 0 && first > 0 && first - beg < cnt) {
@@ -580,8 +600,8 @@ __device__ __forceinline__ void rle_load_flags(const SegDesc& sd, uint64_t beg, 
   }
   ne_bits = nf_bits = 0;
 #pragma unroll
-  for (int j = 0; j < kSortIpt; ++j) {
-    const uint32_t idx = (uint32_t)w * 32 * kSortIpt + j * 32 + lane;
+  for (int j = 0; j < kIpt; ++j) {
+    const uint32_t idx = (uint32_t)w * 32 * kIpt + j * 32 + lane;
     KeyT kj = 0;
     vv[j] = 0;
     if (idx < cnt) {
@@ -609,20 +629,21 @@ __device__ __forceinline__ void rle_load_flags(const SegDesc& sd, uint64_t beg, 
   }
 }
 
-template <typename KeyT>
-__global__ void __launch_bounds__(kSortThreads)
+template <typename KeyT, int kIpt = kSortIpt>
+__global__ void __launch_bounds__(kTile / kIpt)
 k_rle_count(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg,
             const KeyT* __restrict__ keys, const uint32_t* __restrict__ vals,
             uint32_t* __restrict__ tcnt) {
-  __shared__ uint32_t sw[2][kWarps];
+  constexpr int kW = kTile / kIpt / 32;
+  __shared__ uint32_t sw[2][kW];
   const uint32_t t = blockIdx.x;
   const SegDesc sd = segs[tile_seg[t]];
   const uint32_t lt = t - sd.tile0;
   const uint64_t beg = (uint64_t)lt * kTile;
   const uint32_t cnt = (uint32_t)min((uint64_t)kTile, sd.G - beg);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t vv[kSortIpt], ne_bits, nf_bits;
-  rle_load_flags<KeyT>(sd, beg, cnt, w, lane, keys, vals, vv, ne_bits, nf_bits);
+  uint32_t vv[kIpt], ne_bits, nf_bits;
+  rle_load_flags<KeyT, kIpt>(sd, beg, cnt, w, lane, keys, vals, vv, ne_bits, nf_bits);
   uint32_t ce = __popc(ne_bits), cf = __popc(nf_bits);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -636,7 +657,7 @@ k_rle_count(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t a = 0, b = 0;
-    for (int i = 0; i < kWarps; ++i) {
+    for (int i = 0; i < kW; ++i) {
       a += sw[0][i];
       b += sw[1][i];
     }
@@ -782,8 +803,8 @@ k_rle_final(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
 // trec[t * kRecWords ..] = {first entry element, last entry element, its
 // entry, first feature's entry, last feature's entry} (tile-local element
 // indices, kNone where absent) lets k_rle_fix complete them.
-template <typename KeyT>
-__global__ void __launch_bounds__(kSortThreads, 5)
+template <typename KeyT, int kIpt = kSortIpt>
+__global__ void __launch_bounds__(kTile / kIpt, kIpt == kSortIpt ? 5 : 4)
 k_rle_emit_gram(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_seg,
                 const KeyT* __restrict__ keys, const uint32_t* __restrict__ vals,
                 const DsPack* __restrict__ dsp, const uint32_t* __restrict__ tcnt,
@@ -791,7 +812,8 @@ k_rle_emit_gram(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ t
                 uint32_t* __restrict__ eseq, uint32_t* __restrict__ efe) {
   // Per warp: entries, first / last entry element (warp-local), and the
   // number of the warp's entries before its first / last feature start.
-  __shared__ uint32_t swe[kWarps], sfe[kWarps], sle[kWarps], sff[kWarps], slf[kWarps];
+  constexpr int kW = kTile / kIpt / 32;
+  __shared__ uint32_t swe[kW], sfe[kW], sle[kW], sff[kW], slf[kW];
   const uint32_t t = blockIdx.x;
   const uint32_t s = tile_seg[t];
   const SegDesc sd = segs[s];
@@ -802,12 +824,12 @@ k_rle_emit_gram(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ t
   const uint32_t lt_mask = lanemask_lt();
   const uint32_t gt_mask = lane == 31 ? 0u : (0xFFFFFFFFu << (lane + 1));
   const uint32_t* __restrict__ woff = dsp[sd.ds].woff;
-  uint32_t vv[kSortIpt], ne_bits, nf_bits;
-  rle_load_flags<KeyT>(sd, beg, cnt, w, lane, keys, vals, vv, ne_bits, nf_bits);
+  uint32_t vv[kIpt], ne_bits, nf_bits;
+  rle_load_flags<KeyT, kIpt>(sd, beg, cnt, w, lane, keys, vals, vv, ne_bits, nf_bits);
   {
     uint32_t nen = 0, fe = kNone, le = kNone, ff = kNone, lf = kNone;
 #pragma unroll
-    for (int j = 0; j < kSortIpt; ++j) {
+    for (int j = 0; j < kIpt; ++j) {
       const uint32_t be = __ballot_sync(0xffffffffu, (ne_bits >> j) & 1u);
       const uint32_t bf = __ballot_sync(0xffffffffu, (nf_bits >> j) & 1u);
       if (be) {
@@ -830,7 +852,7 @@ k_rle_emit_gram(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ t
     }
   }
   __syncthreads();
-  constexpr uint32_t kWarpElems = 32 * kSortIpt;
+  constexpr uint32_t kWarpElems = 32 * kIpt;
   const uint32_t e0 = tcnt[2 * (uint64_t)t];  // entries of the segment before this tile
   uint32_t re = e0;                           // entries before warp w
   for (int i = 0; i < w; ++i) re += swe[i];
@@ -839,7 +861,7 @@ k_rle_emit_gram(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ t
   uint32_t cne = kNone, cnf = kNone;
   {
     uint32_t r = re + swe[w];
-    for (int i = w + 1; i < kWarps; ++i) {
+    for (int i = w + 1; i < kW; ++i) {
       if (cne == kNone && sfe[i] != kNone) cne = i * kWarpElems + sfe[i];
       if (cnf == kNone && sff[i] != kNone) cnf = r + sff[i];
       r += swe[i];
@@ -847,7 +869,7 @@ k_rle_emit_gram(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ t
   }
   if (threadIdx.x == 0) {
     uint32_t r = e0, fe = kNone, le = kNone, le_e = kNone, ff = kNone, lf = kNone;
-    for (int i = 0; i < kWarps; ++i) {
+    for (int i = 0; i < kW; ++i) {
       if (sfe[i] != kNone) {
         if (fe == kNone) fe = i * kWarpElems + sfe[i];
         le = i * kWarpElems + sle[i];
@@ -868,7 +890,7 @@ k_rle_emit_gram(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ t
   }
   re += swe[w];  // entries before the item after the current one (walking back)
 #pragma unroll
-  for (int j = kSortIpt - 1; j >= 0; --j) {
+  for (int j = kIpt - 1; j >= 0; --j) {
     const bool ne = (ne_bits >> j) & 1u, nf = (nf_bits >> j) & 1u;
     const uint32_t be = __ballot_sync(0xffffffffu, ne);
     const uint32_t bf = __ballot_sync(0xffffffffu, nf);
@@ -984,16 +1006,16 @@ void rle_head_t(const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg,
                                                     estart, etseq, efid, fstart, ewin);
 }
 
-template <typename KeyT>
+template <typename KeyT, int kIpt>
 void rle_gram_t(const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg, uint32_t ntiles,
                 const void* keys, const uint32_t* vals, const DsPack* dsp, uint32_t* tcnt,
                 uint32_t* segtot, uint32_t* trec, uint32_t* ewin, uint32_t* eseq, uint32_t* efe,
                 unsigned long long* ecount, cudaStream_t st) {
   const KeyT* k = (const KeyT*)keys;
-  k_rle_count<KeyT><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, k, vals, tcnt);
+  k_rle_count<KeyT, kIpt><<<ntiles, kTile / kIpt, 0, st>>>(segs, tile_seg, k, vals, tcnt);
   k_rle_scan<<<nsegs, kSortThreads, 0, st>>>(segs, tcnt, segtot, ecount);
-  k_rle_emit_gram<KeyT><<<ntiles, kSortThreads, 0, st>>>(segs, tile_seg, k, vals, dsp, tcnt, trec,
-                                                         ewin, eseq, efe);
+  k_rle_emit_gram<KeyT, kIpt><<<ntiles, kTile / kIpt, 0, st>>>(segs, tile_seg, k, vals, dsp, tcnt, trec,
+                                                               ewin, eseq, efe);
   k_rle_fix<<<(ntiles + 7) / 8, 256, 0, st>>>(segs, tile_seg, ntiles, segtot, trec, eseq, efe);
 }
 
@@ -1079,14 +1101,21 @@ void launch_rle_head(bool wide, const SegDesc* segs, uint32_t nsegs,
 void launch_rle_gram(bool wide, const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg,
                      uint32_t ntiles, const void* keys, const uint32_t* vals, const DsPack* dsp,
                      uint32_t* tcnt, uint32_t* segtot, uint32_t* trec, uint32_t* ewin,
-                     uint32_t* eseq, uint32_t* efe, unsigned long long* ecount, cudaStream_t st) {
+                     uint32_t* eseq, uint32_t* efe, unsigned long long* ecount, int items,
+                     cudaStream_t st) {
   if (ntiles == 0) return;
-  if (wide)
-    rle_gram_t<uint64_t>(segs, nsegs, tile_seg, ntiles, keys, vals, dsp, tcnt, segtot, trec, ewin,
-                         eseq, efe, ecount, st);
+  if (wide && items == 8)
+    rle_gram_t<uint64_t, 8>(segs, nsegs, tile_seg, ntiles, keys, vals, dsp, tcnt, segtot, trec, ewin,
+                            eseq, efe, ecount, st);
+  else if (wide)
+    rle_gram_t<uint64_t, kSortIpt>(segs, nsegs, tile_seg, ntiles, keys, vals, dsp, tcnt, segtot, trec, ewin,
+                                   eseq, efe, ecount, st);
+  else if (items == 8)
+    rle_gram_t<uint32_t, 8>(segs, nsegs, tile_seg, ntiles, keys, vals, dsp, tcnt, segtot, trec, ewin,
+                            eseq, efe, ecount, st);
   else
-    rle_gram_t<uint32_t>(segs, nsegs, tile_seg, ntiles, keys, vals, dsp, tcnt, segtot, trec, ewin,
-                         eseq, efe, ecount, st);
+    rle_gram_t<uint32_t, kSortIpt>(segs, nsegs, tile_seg, ntiles, keys, vals, dsp, tcnt, segtot, trec, ewin,
+                                   eseq, efe, ecount, st);
 }
 
 void launch_rle_final(const SegDesc* segs, const uint32_t* tile_seg, uint32_t ntiles,

@@ -94,9 +94,11 @@ struct AccParams {
 constexpr int kItemWords = 8;
 
 int accum_max_threads();
-void launch_accum(const AccParams& p, int threads, int blocks,
+// variant: how a warp walks entry ranges shorter than a warp (0, 1 or 2;
+// see k_accum.cu); results are identical.
+void launch_accum(const AccParams& p, int threads, int variant, int blocks,
                   size_t smem, cudaStream_t st);
-int accum_blocks_per_sm(int threads, size_t smem);
+int accum_blocks_per_sm(int threads, int variant, size_t smem);
 
 void launch_finish(const DsInfo* d_ds, uint32_t nds, uint32_t ntiles,
                    uint32_t M, bool want_nm, bool want_khat, cudaStream_t st);
@@ -120,11 +122,13 @@ void launch_rle_head(bool wide, const SegDesc* segs, uint32_t nsegs,
                      uint32_t* ewin, cudaStream_t st);
 // Gram engine: count/scan, then ewin, eseq and efe written directly, and
 // the tile-end fix-up; trec holds kRecWords words per tile.  The chunk's
-// entries are added to *ecount.
+// entries are added to *ecount.  items: elements per thread of the count
+// and emit kernels (16: 256-thread blocks; 8: 512-thread blocks).
 void launch_rle_gram(bool wide, const SegDesc* segs, uint32_t nsegs, const uint32_t* tile_seg,
                      uint32_t ntiles, const void* keys, const uint32_t* vals, const DsPack* dsp,
                      uint32_t* tcnt, uint32_t* segtot, uint32_t* trec, uint32_t* ewin,
-                     uint32_t* eseq, uint32_t* efe, unsigned long long* ecount, cudaStream_t st);
+                     uint32_t* eseq, uint32_t* efe, unsigned long long* ecount, int items,
+                     cudaStream_t st);
 void launch_rle_final(const SegDesc* segs, const uint32_t* tile_seg, uint32_t ntiles,
                       const uint32_t* segtot, const uint32_t* estart,
                       const uint32_t* etseq, const uint32_t* efid,

@@ -1,14 +1,22 @@
 """Full-size parity: the workloads at their benchmark sizes, run in the
 benchmark's launch configuration (one batched device call, CUDA graph).
 
-The oracle cannot afford whole matrices here, so sampled rows are checked
-against it entry by entry (bit-exact K and N_m over all columns; normalised
-values within 1e-12), and the whole matrices are checked for properties
-that hold at any size: symmetry, unit diagonal, |Khat| <= 1, K == N-weighted
+Every row of the DNA toy, DNA large-M and protein Gram matrices, and the
+text rows the survey's sampling names (every 23rd plus the first and last
+8), is compared with the oracle through a per-row digest of K and N_0..N_M
+(``tests/golden/fullsize_row_hashes.json``, written by
+``tests/golden/make_fullsize_hashes.py`` from the oracle alone: hours of
+brute force, done once on a CPU host).  Sampled rows are also checked entry
+by entry against the oracle run here (bit-exact K and N_m over all columns;
+normalised values within 1e-12), and the whole matrices for properties that
+hold at any size: symmetry, unit diagonal, |Khat| <= 1, K == N-weighted
 sum, and agreement between the batched and the plain per-mask engines.
 """
 
+import hashlib
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -123,3 +131,77 @@ def test_dna_toy_config_exact():
     np.testing.assert_array_equal(out["K"], ref["K"])
     np.testing.assert_array_equal(out["Nm"], ref["Nm"])
     assert np.all(np.abs(out["Khat"] - ref["Khat"]) <= KHAT_RTOL * np.abs(ref["Khat"]) + 1e-300)
+
+
+DIGESTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fullsize_row_hashes.json")
+
+
+def _row_digests(K, Nm, rows):
+    out = []
+    for x in rows:
+        h = hashlib.sha256()
+        h.update(np.ascontiguousarray(K[x], dtype="<i8").tobytes())
+        for m in range(Nm.shape[0]):
+            h.update(np.ascontiguousarray(Nm[m, x], dtype="<i8").tobytes())
+        out.append(h.hexdigest()[:16])
+    return out
+
+
+def _bench_configuration(sigma, g, k, sets):
+    """The benchmark's launch: autotuned options, one batched device call,
+    N_m requested as well (the digests cover it)."""
+    import torch
+
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream().cuda_stream
+    ns = [len(o) - 1 for _, o in sets]
+    d_codes = [torch.from_numpy(c).to(dev) for c, _ in sets]
+    K = [torch.empty((n, n), dtype=torch.int32, device=dev) for n in ns]
+    Kh = [torch.empty((n, n), dtype=torch.float64, device=dev) for n in ns]
+    Nm = [torch.empty((g - k + 1, n, n), dtype=torch.int32, device=dev) for n in ns]
+    offs = [o for _, o in sets]
+    with pkg.gakco_create(sigma, g, k) as ctx:
+        ctx.autotune_device([t.data_ptr() for t in d_codes], offs, stream=stream)
+        for _ in range(2):  # the second call replays the captured graph
+            ctx.gram_batch_device([t.data_ptr() for t in d_codes], offs, [t.data_ptr() for t in K],
+                                  [t.data_ptr() for t in Kh], [t.data_ptr() for t in Nm], stream=stream)
+        torch.cuda.synchronize()
+        return [{"K": a.cpu().numpy(), "Khat": b.cpu().numpy(), "Nm": c.cpu().numpy()}
+                for a, b, c in zip(K, Kh, Nm)]
+
+
+def _digest_sets():
+    if not os.path.exists(DIGESTS):
+        pytest.skip("per-row oracle digests not generated (tests/golden/make_fullsize_hashes.py)")
+    with open(DIGESTS) as f:
+        return json.load(f)["datasets"]
+
+
+@pytest.mark.parametrize("workload", ["dna_toy", "dna_large", "protein", "text"])
+def test_every_row_matches_the_oracle_digests(workload):
+    ref = _digest_sets()
+    if workload == "dna_large":
+        sets = synth.dna_large()
+        names = [f"dna_large_{i}" for i in range(len(sets))]
+        sigma, g, k = 4, 10, 6
+    else:
+        sigma, g, k, builder = synth.WORKLOADS[workload]
+        sets, names = [builder()], [workload]
+    missing = [nm for nm in names if nm not in ref]
+    if missing:
+        pytest.skip(f"no digests for {missing}")
+    outs = _bench_configuration(sigma, g, k, sets)
+    for name, (codes, off), out in zip(names, sets, outs):
+        r = ref[name]
+        n = len(off) - 1
+        assert (r["sigma"], r["g"], r["k"], r["n"]) == (sigma, g, k, n)
+        rows = list(range(n)) if r["rows"] == "all" else r["rows"]
+        got = _row_digests(out["K"], out["Nm"], rows)
+        bad = [x for x, a, b in zip(rows, got, r["digests"]) if a != b]
+        assert not bad, f"{name}: {len(bad)} of {len(rows)} rows differ from the oracle, first {bad[:5]}"
+        _check_properties(out, g, k, off)
+        # Normalised values on a few rows, entry by entry against the oracle.
+        sample = np.array(sorted({rows[0], rows[len(rows) // 2], rows[-1]}), dtype=np.int32)
+        oref = oracle.gram(codes, off, g, k, rows=sample)
+        err = np.abs(out["Khat"][sample] - oref["Khat"])
+        assert np.all(err <= KHAT_RTOL * np.abs(oref["Khat"]) + 1e-300)

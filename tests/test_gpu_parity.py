@@ -93,6 +93,8 @@ def test_nsweep_configurations_bit_exact(case):
     {"radix_bits": 4}, {"radix_bits": 11}, {"chunk_elems": 4096},
     {"smem_cols": 7}, {"smem_cols": 32, "accum_threads": 256},
     {"accum_threads": 1024}, {"graph": 0},
+    {"accum_variant": 1}, {"accum_variant": 2}, {"accum_variant": 1, "accum_threads": 512},
+    {"accum_variant": 2, "smem_cols": 32}, {"rle_items": 8}, {"rle_items": 8, "chunk_elems": 4096},
 ])
 def test_tuning_options_do_not_change_results(opts):
     codes, off = synth.random_small(30, 70, 20, 0, 300)
@@ -136,6 +138,23 @@ def test_onesweep_fit_cross_and_graph_replay():
     _check(a, ref)
     _check(b, ref)
     np.testing.assert_array_equal(x["K"], xref["K"])
+
+
+@pytest.mark.parametrize("case", RAGGED)
+def test_run_length_with_eight_items_per_thread(case):
+    seed, n, sigma, lo, hi, g, k = case
+    codes, off = synth.random_small(seed, n, sigma, lo, hi)
+    ref = oracle.gram(codes, off, g, k)
+    _check(_gram(sigma, g, k, codes, off, rle_items=8), ref)
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("case", RAGGED[:4])
+def test_accumulation_variants_bit_exact(case, variant):
+    seed, n, sigma, lo, hi, g, k = case
+    codes, off = synth.random_small(seed, n, sigma, lo, hi)
+    ref = oracle.gram(codes, off, g, k)
+    _check(_gram(sigma, g, k, codes, off, accum_variant=variant), ref)
 
 
 @pytest.mark.parametrize("kind", ["homopolymer", "period2", "mixed"])
