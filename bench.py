@@ -697,7 +697,8 @@ def run_ours(args):
         "extend": extend,
         "nsweep_l100": nsweep,
         "e2e": {"value": entries * ws / (e2e_step / 1000.0), "unit": UNIT,
-                "ms_per_step": e2e_step, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "ms_per_step": e2e_step, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "calls_ms": [round(v, 3) for v in e2e_ms]},
         "gpu_launches": launches * args.steps,
         "kernel_ms": {kname: {"ms": v[0], "launches": v[1]} for kname, v in timings.items()},
         "roofline": roof,

@@ -191,6 +191,10 @@ const char *gakco_last_error(const gakco_ctx *ctx);
 /* Elements per thread of the Gram call's run-length kernels: 16 (256-thread
  * blocks, default) or 8 (512-thread blocks, fewer registers per thread). */
 #define GAKCO_OPT_RLE_ITEMS 28
+/* Sort digit width of one level: value (level << 8) | bits, bits 4..11, or
+ * 0 to use GAKCO_OPT_RADIX_BITS for that level (the default).  The
+ * autotuner sets these where a level's key width favours another digit. */
+#define GAKCO_OPT_LEVEL_RADIX_BITS 29
 int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 
 /*

@@ -191,6 +191,7 @@ struct gakco_ctx {
   // options
   int engine = 0;
   int radix_bits = 8;
+  int level_bits[kMaxLevels] = {};  // per-level digit width (0: radix_bits)
   int64_t chunk_elems = (int64_t)1 << 26;
   int use_graph = 1;
   int accum_threads = 256;
@@ -689,7 +690,8 @@ void plan_chunks(gakco_ctx* c, Plan& p, bool plain) {
   const uint64_t limit = plain ? 0 : (uint64_t)std::max<int64_t>(c->chunk_elems, kTile);
   for (int m = p.first_level; m <= c->M; ++m) {
     const int kb = c->lkbits[m];
-    const int np = (kb + c->radix_bits - 1) / c->radix_bits;
+    const int rbits = c->level_bits[m] ? c->level_bits[m] : c->radix_bits;
+    const int np = (kb + rbits - 1) / rbits;
     const int rb = (kb + np - 1) / np;
     std::vector<std::pair<int, int>> passes;
     for (int q = 0; q < np; ++q) passes.push_back({q * rb, std::min(rb, kb - q * rb)});
@@ -1090,7 +1092,7 @@ int upload_tables(gakco_ctx* c, Work& w, Tables& t) {
 // The onesweep sort takes digits of at most 8 bits (one look-back thread
 // per digit) and at most kOsMaxPasses passes.
 bool use_onesweep(const gakco_ctx* c) {
-  return c->sort_mode == 1 && c->radix_bits <= 8 && (64 + c->radix_bits - 1) / c->radix_bits <= kOsMaxPasses;
+  return c->sort_mode == 1;
 }
 
 // Sort / run-length buffers for the plan's largest chunk.
@@ -1314,7 +1316,9 @@ void enqueue_chunk(gakco_ctx* c, Work& w, const Plan& p, const Chunk& ch, Tail t
   void* kin = kbuf[1];  // the first pass extracts the masked keys here
   const uint32_t* vin = (const uint32_t*)w.wid.p;  // first-pass payload: window ids
   int cur = 0;
-  if (use_onesweep(c) && ch.passes.size() <= (size_t)kOsMaxPasses) {
+  bool os = use_onesweep(c) && ch.passes.size() <= (size_t)kOsMaxPasses;
+  for (const auto& ps : ch.passes) os = os && ps.second <= 8;
+  if (os) {
     const int np = (int)ch.passes.size();
     OsPasses ps{};
     ps.np = np;
@@ -2325,6 +2329,7 @@ struct TuneChoice {
   int dense;
   int accum_variant;
   int rle_items;
+  int level_bits[kMaxLevels];
 };
 
 std::mutex g_tune_mu;
@@ -2372,6 +2377,7 @@ int autotune(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64_
       c->dense = it->second.dense;
       c->accum_variant = it->second.accum_variant;
       c->rle_items = it->second.rle_items;
+      memcpy(c->level_bits, it->second.level_bits, sizeof c->level_bits);
       drop_graph(c);
       report = "cached";
       return GAKCO_OK;
@@ -2386,6 +2392,7 @@ int autotune(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64_
     o += (uint64_t)n[d] * n[d];
   }
   const int saved_profile = c->profile, saved_engine = c->engine;
+  memset(c->level_bits, 0, sizeof c->level_bits);
   c->profile = 1;
   c->engine = 0;
   c->dense = 0;
@@ -2407,6 +2414,23 @@ int autotune(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64_
     if (t < best) best = t, best_rb = rb;
   }
   c->radix_bits = best_rb;
+  // Digit width per level: the levels' key widths differ (e.g. 26 bits take
+  // four 8-bit passes but three 9-bit ones), so each level may take its
+  // own width.
+  for (int m = 0; m <= c->M && rc == GAKCO_OK; ++m) {
+    if (c->lkbits[m] <= 8) continue;  // one pass at any width
+    c->level_bits[m] = 0;
+    double best_t;
+    if ((rc = trial("sort_pass", "run_length", best_t)) != GAKCO_OK) break;
+    int best_b = 0;
+    for (int rb : {7, 9, 10, 11}) {
+      if (rb == best_rb) continue;
+      c->level_bits[m] = rb;
+      if ((rc = trial("sort_pass", "run_length", t)) != GAKCO_OK) break;
+      if (t < 0.98 * best_t) best_t = t, best_b = rb;  // a clear gain only
+    }
+    c->level_bits[m] = best_b;
+  }
   // Sort chunk size.
   int64_t best_ch = c->chunk_elems;
   best = 1e30;
@@ -2468,12 +2492,16 @@ int autotune(gakco_ctx* c, int32_t nd, const uint8_t* const* codes, const int64_
   if (rc != GAKCO_OK) return rc;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = {best_rb, best_ch, best_th, best_gb, best_dense, best_var, best_ri};
+    TuneChoice tc{best_rb, best_ch, best_th, best_gb, best_dense, best_var, best_ri, {}};
+    memcpy(tc.level_bits, c->level_bits, sizeof tc.level_bits);
+    g_tune_cache[key] = tc;
   }
   snprintf(buf, sizeof buf,
            "radix_bits=%d chunk_elems=%lld rle_items=%d accum_threads=%d group_bytes=%lld dense=%d accum_variant=%d",
            best_rb, (long long)best_ch, best_ri, best_th, (long long)best_gb, best_dense, best_var);
   report = buf;
+  for (int m = 0; m <= c->M; ++m)
+    if (c->level_bits[m]) report += " level" + std::to_string(m) + "_bits=" + std::to_string(c->level_bits[m]);
   return GAKCO_OK;
 }
 
@@ -2706,6 +2734,14 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
       if (v < 0 || v > 2) return fail(c, GAKCO_E_INVALID, "accumulation variant must be 0, 1 or 2");
       c->accum_variant = (int)v;
       break;
+    case GAKCO_OPT_LEVEL_RADIX_BITS: {
+      const int64_t m = v >> 8, b = v & 0xFF;
+      if (m < 0 || m > c->M || (b != 0 && (b < 4 || b > kMaxRadixBits)))
+        return fail(c, GAKCO_E_INVALID, "level digit width: (level << 8) | bits, level 0..M, bits 0 or 4..%d",
+                    kMaxRadixBits);
+      c->level_bits[m] = (int)b;
+      break;
+    }
     case GAKCO_OPT_RLE_ITEMS:
       if (v != 8 && v != 16) return fail(c, GAKCO_E_INVALID, "run-length items must be 8 or 16");
       c->rle_items = (int)v;

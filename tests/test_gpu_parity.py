@@ -95,6 +95,7 @@ def test_nsweep_configurations_bit_exact(case):
     {"accum_threads": 1024}, {"graph": 0},
     {"accum_variant": 1}, {"accum_variant": 2}, {"accum_variant": 1, "accum_threads": 512},
     {"accum_variant": 2, "smem_cols": 32}, {"rle_items": 8}, {"rle_items": 8, "chunk_elems": 4096},
+    {"level_radix_bits": (2 << 8) | 11}, {"level_radix_bits": (4 << 8) | 5},
 ])
 def test_tuning_options_do_not_change_results(opts):
     codes, off = synth.random_small(30, 70, 20, 0, 300)
