@@ -207,8 +207,16 @@ NCU_BYTES_PER_UNIT = {
     "accumulate": (4.426e9 / 3.16e9, "pair update"),
     "dense_gemm": (3.534e9 / 1.19e13, "flop"),
     "dense_scatter": (3.506e9 / 3.46e9, "byte of A"),
+    "sort_pass": (2.103e9 / 2.493e9, "algorithmic byte"),
+    "run_length": (1.923e9 / 1.344e9, "algorithmic byte"),
 }
-NCU_SOURCE = "profiles/dense_scatter_gemm_accum_dna_4000.md (scaled by units)"
+NCU_SOURCE = {
+    "accumulate": "profiles/dense_scatter_gemm_accum_dna_4000.md (scaled by units)",
+    "dense_gemm": "profiles/dense_scatter_gemm_accum_dna_4000.md (scaled by units)",
+    "dense_scatter": "profiles/dense_scatter_gemm_accum_dna_4000.md (scaled by units)",
+    "sort_pass": "profiles/traffic_dna_2000.md (scaled by units)",
+    "run_length": "profiles/traffic_dna_2000.md (scaled by units)",
+}
 
 
 def kernel_rooflines(timings, work, peaks, sm_count, smem_atomic_peak=None):
@@ -274,11 +282,12 @@ def kernel_rooflines(timings, work, peaks, sm_count, smem_atomic_peak=None):
         e["frac"] = e["achieved"] / e["peak"]
         e["traffic"] = None
         units = {"accumulate": work["pairs"], "dense_gemm": work["dense_flops"],
-                 "dense_scatter": work["dense_bytes"]}.get(name)
+                 "dense_scatter": work["dense_bytes"], "sort_pass": work["sort_bytes"],
+                 "run_length": work.get("rle_bytes", 0)}.get(name)
         if name in NCU_BYTES_PER_UNIT and units:
             per, unit = NCU_BYTES_PER_UNIT[name]
             e["traffic"] = per * units / n          # bytes per launch
-            e["traffic_source"] = f"{NCU_SOURCE}: {per:.4g} B per {unit}"
+            e["traffic_source"] = f"{NCU_SOURCE[name]}: {per:.4g} B per {unit}"
         e["launch_ms"] = ms / n
         e["launches"] = n
         out[name] = e
@@ -634,9 +643,14 @@ def run_ours(args):
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     try:
         smem_peak = pkg.gakco_measure_smem_atomics(stream.cuda_stream)
+        smem_random = pkg.gakco_measure_smem_atomics(stream.cuda_stream, random_columns=True)
     except pkg.GakcoError:
-        smem_peak = None
+        smem_peak = smem_random = None
     roofs = kernel_rooflines(timings, work, peaks, sm_count, smem_peak)
+    if smem_random and "accumulate" in roofs:
+        # Context: the same adds at random columns (the accumulation's pattern).
+        roofs["accumulate"]["random_column_rate"] = smem_random / 1e12
+        roofs["accumulate"]["frac_of_random_column_rate"] = roofs["accumulate"]["achieved"] / (smem_random / 1e12)
     total_ms = sum(v[0] for v in timings.values())
     for name, e in roofs.items():
         e["peak_kind"] = peak_kind

@@ -195,6 +195,12 @@ const char *gakco_last_error(const gakco_ctx *ctx);
  * 0 to use GAKCO_OPT_RADIX_BITS for that level (the default).  The
  * autotuner sets these where a level's key width favours another digit. */
 #define GAKCO_OPT_LEVEL_RADIX_BITS 29
+/* The dense GEMM's persistent CTAs may take the tiles of a partial last
+ * wave as K-parts (up to 8 per tile, taken part by part), so that the wave
+ * ends sooner: 1 = always, 0 = never, -1 (default) = when the call has no
+ * sparse level, whose kernels would otherwise fill the wave's idle SMs.
+ * Identical results. */
+#define GAKCO_OPT_DENSE_SPLIT 30
 int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 
 /*
@@ -437,6 +443,12 @@ int gakco_combine_device(gakco_ctx *ctx, const uint32_t *C, int32_t n,
  * denominator of the accumulation's roofline.
  */
 int gakco_measure_smem_atomics(void *stream, double *updates_per_s);
+/* The same rate with each lane adding at pseudo-random words of a 4096-word
+ * row (random_columns = 1), the column pattern of the accumulation: lanes
+ * meet in banks as random draws do.  random_columns = 0 is
+ * gakco_measure_smem_atomics. */
+int gakco_measure_smem_atomics_pattern(void *stream, int random_columns,
+                                       double *updates_per_s);
 
 /*
  * Gram kernel of one dataset that allocates nothing.  The paper has no

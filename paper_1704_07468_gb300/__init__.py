@@ -42,7 +42,7 @@ OPT = {"engine": 1, "radix_bits": 2, "chunk_elems": 3, "graph": 4,
        "heavy": 21, "heavy_bytes": 22, "direct_d2h": 23,
        "dense_round_sum": 24, "dense_wait_cycles": 25, "sort": 26,
        "accum_variant": 27, "rle_items": 28,
-       "level_radix_bits": 29}
+       "level_radix_bits": 29, "dense_split": 30}
 STAT = {"launches": 1, "mask_passes": 2, "device_bytes": 3,
         "graph_replay": 4, "pair_updates": 5, "entries_visited": 6,
         "windows_visited": 7, "served_batches": 8, "served_requests": 9,
@@ -108,6 +108,8 @@ def load_library(build_if_missing: bool = False):
         "gakco_gram_partial_device": ([p, p, p, i32, i32, i32, p, p], ctypes.c_int),
         "gakco_combine_device": ([p, p, i32, p, p, p, p], ctypes.c_int),
         "gakco_measure_smem_atomics": ([p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "gakco_measure_smem_atomics_pattern": ([p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
+                                               ctypes.c_int),
         "gakco_gram_device_noalloc": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, p, p, i32,
                                        p, p, p, p, ctypes.c_char_p, ctypes.c_int],
                                       ctypes.c_int),
@@ -423,12 +425,14 @@ def gakco_gram_device_noalloc(sigma, g, k, codes_ptr, offsets, K_ptr, Khat_ptr=N
 _add_cross_methods(Context)
 
 
-def gakco_measure_smem_atomics(stream=None) -> float:
-    """Conflict-free shared-memory atomic adds per second of the current
-    GPU (C: ``gakco_measure_smem_atomics``)."""
+def gakco_measure_smem_atomics(stream=None, random_columns=False) -> float:
+    """Shared-memory atomic adds per second of the current GPU, conflict-free
+    or at random columns of a 4096-word row (C:
+    ``gakco_measure_smem_atomics_pattern``)."""
     lib = load_library()
     v = ctypes.c_double()
-    rc = lib.gakco_measure_smem_atomics(ctypes.c_void_p(stream) if stream else None, ctypes.byref(v))
+    rc = lib.gakco_measure_smem_atomics_pattern(ctypes.c_void_p(stream) if stream else None,
+                                                int(bool(random_columns)), ctypes.byref(v))
     if rc != GAKCO_OK:
         raise GakcoError(rc, "shared-memory atomic probe failed")
     return v.value

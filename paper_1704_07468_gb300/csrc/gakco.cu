@@ -216,6 +216,8 @@ struct gakco_ctx {
   int sort_mode = 0;    // 0: upsweep / digit scans / downsweep per pass; 1: onesweep
   int accum_variant = 0;  // how the accumulation walks short entry ranges (k_accum.cu)
   int rle_items = 16;     // elements per thread of the Gram run-length kernels (16 or 8)
+  int dense_split = -1;   // cut the GEMM's partial last wave into K-parts: 1 always, 0 never,
+                          // -1 when no sparse level runs beside the GEMM
   int64_t dense_round_sum = kDenseExactSum;  // bound on a GEMM round's partial sums
   int64_t dense_wait_cycles = 0;             // GEMM role-wait limit (0: default)
   // Heavy features of sparse levels go to the tensor cores: threshold on a
@@ -904,6 +906,15 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
     return (I2 * 256 < n ? 2 : 0) + (I2 * 256 + 128 < n ? 2 : 0);  // in 128 x 128 units
   };
   DenseWave wv{};
+  // Cutting the partial last wave into K-parts pays only when no sparse
+  // level runs beside the GEMM (otherwise the sparse branch fills the idle
+  // SMs of that wave): auto (-1) splits when every level with work is dense.
+  bool all_dense = true;
+  for (size_t d = 0; d < p.ds.size(); ++d)
+    for (int m = p.first_level; m <= c->M; ++m)
+      if (p.ds[d].G > 0 && !p.is_dense(d, m, c->M) && std::min(lf[m + 1], p.mask_hi) > std::max(lf[m], p.mask_lo))
+        all_dense = false;
+  const bool split = c->dense_split == 1 || (c->dense_split == -1 && all_dense);
   auto close = [&]() {
     if (wv.np == 0) return;
     // Macro tiles per (dataset, level) run of problems, each sweeping all
@@ -925,16 +936,47 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
       for (uint32_t I2 = 0; I2 < R; ++I2)
         for (uint32_t J2 = I2; J2 < R; ++J2) {
           const int k = sub_tiles(I2, J2, h.n);
-          if (k > 0) best.push_back({{g0, g1 - g0, I2, J2}, stages * k});
+          if (k > 0) best.push_back({{g0, g1 - g0, I2, J2, 0u, (uint32_t)stages}, stages * k});
         }
       g0 = g1;
     }
     std::stable_sort(best.begin(), best.end(), [](const Part& x, const Part& y) { return x.cost > y.cost; });
+    // The persistent CTAs take tiles b, b + C, ...: the tiles past the last
+    // full multiple of C form a partial last wave.  Cut each of those into q
+    // K-parts (q minimising the tail's length in tile units, ceil(r q / C) /
+    // q, when the tail tiles cost the same), ordered part by part so that
+    // concurrent CTAs still sweep the same columns of A.
+    {
+      const uint32_t C = (uint32_t)(c->dense_sms > 0 ? std::min(c->dense_sms, c->nsm) : c->nsm);
+      const size_t T = best.size(), full = C ? T / C * C : T, r = T - full;
+      bool equal = r > 0 && split;
+      for (size_t i = full; i < T && equal; ++i) equal = best[i].cost == best[full].cost;
+      if (equal && C > 0) {
+        uint32_t q = 1;
+        double span = 1.0;
+        for (uint32_t cand = 2; cand <= 8; ++cand) {
+          const double sp = std::ceil((double)r * cand / C) / cand;
+          if (sp < span - 1e-9 && best[full].w[5] >= 16 * cand) span = sp, q = cand;
+        }
+        if (q > 1) {
+          std::vector<Part> tail(best.begin() + full, best.end());
+          best.resize(full);
+          for (uint32_t part = 0; part < q; ++part)
+            for (const Part& pt : tail) {
+              Part x = pt;
+              const uint32_t S = pt.w[5];
+              x.w[4] = (uint32_t)((uint64_t)S * part / q);
+              x.w[5] = (uint32_t)((uint64_t)S * (part + 1) / q);
+              x.cost = pt.cost / q;
+              best.push_back(x);
+            }
+        }
+      }
+    }
     wv.t0 = (uint32_t)(p.dtiles.size() / kDenseTileWords);
     for (const Part& pt : best) {
       p.dtiles.insert(p.dtiles.end(), pt.w.begin(), pt.w.end());
-      double cols = 0;
-      for (uint32_t j = pt.w[0]; j < pt.w[0] + pt.w[1]; ++j) cols += (double)p.dprobs[j].ld;
+      const double cols = 128.0 * (double)(pt.w[5] - pt.w[4]);
       p.dense_issued += 2.0 * 128.0 * 128.0 * cols * sub_tiles(pt.w[2], pt.w[3], p.dprobs[pt.w[0]].n);
     }
     wv.nt = (uint32_t)best.size();
@@ -1048,7 +1090,8 @@ void plan_heavy(gakco_ctx* c, Plan& p, bool plain) {
     for (uint32_t I2 = 0; I2 < R; ++I2)
       for (uint32_t J2 = I2; J2 < R; ++J2)
         if (I2 * 256 < h.n)
-          parts.push_back({{h.prob, 1u, I2, J2}, cost[i] * (double)h.n * (I2 * 256 + 128 < h.n ? 2.0 : 1.0)});
+          parts.push_back({{h.prob, 1u, I2, J2, 0u, 0xFFFFFFFFu},
+                           cost[i] * (double)h.n * (I2 * 256 + 128 < h.n ? 2.0 : 1.0)});
   }
   std::stable_sort(parts.begin(), parts.end(), [](const Part& x, const Part& y) { return x.cost > y.cost; });
   for (const Part& pt : parts) p.dtiles.insert(p.dtiles.end(), pt.w.begin(), pt.w.end());
@@ -2742,6 +2785,10 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
       c->level_bits[m] = (int)b;
       break;
     }
+    case GAKCO_OPT_DENSE_SPLIT:
+      if (v < -1 || v > 1) return fail(c, GAKCO_E_INVALID, "dense split must be -1, 0 or 1");
+      c->dense_split = (int)v;
+      break;
     case GAKCO_OPT_RLE_ITEMS:
       if (v != 8 && v != 16) return fail(c, GAKCO_E_INVALID, "run-length items must be 8 or 16");
       c->rle_items = (int)v;

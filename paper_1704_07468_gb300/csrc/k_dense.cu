@@ -366,14 +366,17 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
       bool stop = false;
       for (uint32_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
         const uint32_t* tl = tiles + kDenseTileWords * t;
-        const uint32_t pa = tl[0], pn = tl[1], I2 = tl[2], J2 = tl[3];
+        const uint32_t pa = tl[0], pn = tl[1], I2 = tl[2], J2 = tl[3], s0 = tl[4], s1 = tl[5];
         const uint32_t st = row_halves(I2, probs[pa].n);
         const bool needA[2] = {(st & 1u) != 0, (st & 2u) != 0};
         const uint32_t bytes = kSubBytes * (2 + needA[0] + needA[1]);  // B: both 128-row blocks
-        for (uint32_t p = pa; p < pa + pn && !stop; ++p) {
+        uint32_t g = 0;  // the run's stages before problem p
+        for (uint32_t p = pa; p < pa + pn && !stop && g < s1; ++p) {
           const void* tm = probs[p].tmap;
           const uint32_t nk = (uint32_t)(probs[p].ld / 128);
-          for (uint32_t k = 0; k < nk; ++k, ++it) {
+          const uint32_t k0 = s0 > g ? min(s0 - g, nk) : 0u, k1 = min(nk, s1 - g);
+          g += nk;
+          for (uint32_t k = k0; k < k1; ++k, ++it) {
             const uint32_t s = it % kStages;
             if (!bar_wait(&empty_bar[s], ((it / kStages) & 1) ^ 1, &abort_flag, wait_cycles)) {
               stop = true;
@@ -405,15 +408,19 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
       bool stop = false;
       for (uint32_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
         const uint32_t* tl = tiles + kDenseTileWords * t;
-        const uint32_t pa = tl[0], pn = tl[1], I2 = tl[2], J2 = tl[3];
+        const uint32_t pa = tl[0], pn = tl[1], I2 = tl[2], s0 = tl[4], s1 = tl[5];
         const uint32_t st = row_halves(I2, probs[pa].n);
         uint32_t total = 0;
         for (uint32_t p = pa; p < pa + pn; ++p) total += (uint32_t)(probs[p].ld / 128);
-        const uint32_t spr = stages_per_round(probs[pa].maxc, total, probs[pa].wmasks, sum_cap);
+        const uint32_t lo = min(s0, total), hi = min(s1, total);
+        const uint32_t spr = stages_per_round(probs[pa].maxc, hi - lo, probs[pa].wmasks, sum_cap);
         uint32_t kr = 0;  // stages into the current round
-        for (uint32_t p = pa; p < pa + pn && !stop; ++p) {
+        uint32_t g = 0;   // the run's stages before problem p
+        for (uint32_t p = pa; p < pa + pn && !stop && g < hi; ++p) {
           const uint32_t nk = (uint32_t)(probs[p].ld / 128);
-          for (uint32_t k = 0; k < nk; ++k, ++it) {
+          const uint32_t k0 = lo > g ? min(lo - g, nk) : 0u, k1 = min(nk, hi - g);
+          g += nk;
+          for (uint32_t k = k0; k < k1; ++k, ++it) {
             if (kr == 0) {
               if (!bar_wait(&tempty, (round & 1) ^ 1, &abort_flag, wait_cycles)) {
                 stop = true;
@@ -465,16 +472,17 @@ k_dense_gemm(const DenseProb* __restrict__ probs, const uint32_t* __restrict__ t
     bool stop = false;
     for (uint32_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
       const uint32_t* tl = tiles + kDenseTileWords * t;
-      const uint32_t pa = tl[0], pn = tl[1], I2 = tl[2], J2 = tl[3];
+      const uint32_t pa = tl[0], pn = tl[1], I2 = tl[2], J2 = tl[3], s0 = tl[4], s1 = tl[5];
       const uint32_t n = probs[pa].n;
       const uint32_t st = row_halves(I2, n);
       uint32_t total = 0;
       for (uint32_t p = pa; p < pa + pn; ++p) total += (uint32_t)(probs[p].ld / 128);
-      const uint32_t spr = stages_per_round(probs[pa].maxc, total, probs[pa].wmasks, sum_cap);
-      const uint32_t nr = (total + spr - 1) / spr;
-      // One round and no other writer: the tile's C entries are still zero,
-      // so plain (vector) stores replace the atomic adds.
-      const bool store = nr == 1 && probs[pa].sole != 0;
+      const uint32_t lo = min(s0, total), hi = min(s1, total);
+      const uint32_t spr = stages_per_round(probs[pa].maxc, hi - lo, probs[pa].wmasks, sum_cap);
+      const uint32_t nr = (hi - lo + spr - 1) / spr;
+      // One round, the whole run and no other writer: the tile's C entries
+      // are still zero, so plain (vector) stores replace the atomic adds.
+      const bool store = nr == 1 && probs[pa].sole != 0 && lo == 0 && hi == total;
       uint32_t* C = probs[pa].C;
       for (uint32_t r = 0; r < nr; ++r, ++round) {
         if (!__all_sync(0xffffffffu, bar_wait(&tfull, round & 1, &abort_flag, wait_cycles))) {

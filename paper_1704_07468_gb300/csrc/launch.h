@@ -253,8 +253,10 @@ void launch_dense_scatter(const DenseProb* d_probs, uint32_t nprobs, uint32_t p0
                           cudaStream_t st);
 // Macro tiles of kDenseTileWords words: first problem, problem count (the
 // consecutive problems of one dataset and level, whose columns the tile
-// sweeps), I2, J2 (256-row and 256-column blocks, I2 <= J2).
-constexpr int kDenseTileWords = 4;
+// sweeps), I2, J2 (256-row and 256-column blocks, I2 <= J2), and the range
+// [s0, s1) of the run's 128-column stages the tile sweeps (0, ~0 = all; a
+// tile of the last, partial wave of CTAs may be cut into K-parts).
+constexpr int kDenseTileWords = 6;
 // Largest partial sum of one exact accumulation round: f32 holds every
 // integer up to 2^24.
 constexpr uint32_t kDenseExactSum = (1u << 24) - 1;

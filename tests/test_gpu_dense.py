@@ -63,6 +63,28 @@ def test_dense_levels_match_the_oracle(case):
     _check(out, ref)
 
 
+@pytest.mark.parametrize("case", CASES[:3])
+def test_dense_tail_split_is_exact(case):
+    """K-parts of the last wave's tiles (and of every tile when there are
+    fewer tiles than CTAs) change nothing."""
+    seed, n, sigma, lo, hi, g, k = case
+    codes, off = synth.random_small(seed, n, sigma, lo, hi)
+    ref = oracle.gram(codes, off, g, k)
+    for sms in (0, 3):
+        out = _run(sigma, g, k, codes, off, dense=2, dense_split=1, dense_sms=sms)
+        assert out["dense_problems"] > 0
+        _check(out, ref)
+        # Kernel-only mode with a dense top level: no sparse level at all,
+        # so the automatic choice splits.
+        with pkg.gakco_create(sigma, g, k) as ctx:
+            for name, v in (("dense", 2), ("dense_split", -1), ("kernel_only", 1), ("dense_sms", sms)):
+                ctx.set_option(name, v)
+            ko = ctx.gram(codes, off, khat=True, nm=False)
+            assert ctx.get_stat("dense_problems") > 0
+        np.testing.assert_array_equal(ko["K"], ref["K"])
+        assert np.all(np.abs(ko["Khat"] - ref["Khat"]) <= KHAT_RTOL * np.abs(ref["Khat"]) + 1e-300)
+
+
 def test_dense_equals_sparse_on_several_waves():
     """A small wave budget cuts each level into several mask runs and the
     runs into several waves; the result must not change."""
