@@ -507,6 +507,10 @@ def run_ours(args):
     if args.sort is not None:
         ctx.set_option("sort", args.sort)
         tuned += f"; sort={args.sort} set by --sort"
+    for kv in args.set or []:
+        name, val = kv.split("=", 1)
+        ctx.set_option(name, int(val))
+        tuned += f"; {name}={val} set by --set"
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -610,6 +614,9 @@ def run_ours(args):
             kctx.set_option("dense", args.dense)
         if args.sort is not None:
             kctx.set_option("sort", args.sort)
+        for kv in args.set or []:
+            name, val = kv.split("=", 1)
+            kctx.set_option(name, int(val))
         kctx.set_option("kernel_only", 1)
         kk = [torch.empty((n, n), dtype=torch.int32, device=dev) for n in ns]
         kkh = [torch.empty((n, n), dtype=torch.float64, device=dev) for n in ns]
@@ -773,6 +780,8 @@ def main():
                     help="also time the toy, protein and text workloads (dna_large run only); 0 to skip")
     ap.add_argument("--sort", type=int, default=None, choices=[0, 1],
                     help="sort after autotuning: 0 upsweep/scan/downsweep per pass, 1 onesweep")
+    ap.add_argument("--set", action="append", metavar="NAME=VALUE",
+                    help="engine option (paper_1704_07468_gb300.OPT name) set after autotuning; repeatable")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--dna-sizes", type=lambda v: [int(t) for t in v.split(",")], default=None,

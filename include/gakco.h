@@ -201,6 +201,11 @@ const char *gakco_last_error(const gakco_ctx *ctx);
  * sparse level, whose kernels would otherwise fill the wave's idle SMs.
  * Identical results. */
 #define GAKCO_OPT_DENSE_SPLIT 30
+/* 1: when a Gram call runs its dense and sparse levels side by side, the
+ * dense GEMM starts after the sparse levels' sort and run-length passes (it
+ * then runs beside the on-chip accumulation); 0 (default): as soon as its
+ * count matrices are built.  Identical results. */
+#define GAKCO_OPT_DENSE_LATE 31
 int gakco_set_option(gakco_ctx *ctx, int key, int64_t value);
 
 /*

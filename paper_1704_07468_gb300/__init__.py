@@ -42,7 +42,8 @@ OPT = {"engine": 1, "radix_bits": 2, "chunk_elems": 3, "graph": 4,
        "heavy": 21, "heavy_bytes": 22, "direct_d2h": 23,
        "dense_round_sum": 24, "dense_wait_cycles": 25, "sort": 26,
        "accum_variant": 27, "rle_items": 28,
-       "level_radix_bits": 29, "dense_split": 30}
+       "level_radix_bits": 29, "dense_split": 30,
+       "dense_late": 31}
 STAT = {"launches": 1, "mask_passes": 2, "device_bytes": 3,
         "graph_replay": 4, "pair_updates": 5, "entries_visited": 6,
         "windows_visited": 7, "served_batches": 8, "served_requests": 9,

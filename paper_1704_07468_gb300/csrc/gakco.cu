@@ -104,7 +104,7 @@ double now_ms() {
 struct Work {
   cudaStream_t cs = nullptr;
   cudaStream_t cs2 = nullptr;                      // second branch of a Gram call
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_heavy = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_heavy = nullptr, ev_sparse = nullptr;
   DevBuf fullkey, wid, ewin, eseq, efe, keyA, keyB, valA, valB, hist, tcnt, segtot, estart,
       etseq, efid, fstart, tables, codes, outK, outKhat, outNm, rinv, status, Cplain, Cacc, ea, eb,
       Cd, Cx, Adense, dmaxc, dovf, outF, trec, Aheavy, hctr, hlist, dtot, osst, osctr, oscnt;
@@ -216,6 +216,7 @@ struct gakco_ctx {
   int sort_mode = 0;    // 0: upsweep / digit scans / downsweep per pass; 1: onesweep
   int accum_variant = 0;  // how the accumulation walks short entry ranges (k_accum.cu)
   int rle_items = 16;     // elements per thread of the Gram run-length kernels (16 or 8)
+  int dense_late = 0;     // 1: the GEMM waits for the sparse sort / run-length passes
   int dense_split = -1;   // cut the GEMM's partial last wave into K-parts: 1 always, 0 never,
                           // -1 when no sparse level runs beside the GEMM
   int64_t dense_round_sum = kDenseExactSum;  // bound on a GEMM round's partial sums
@@ -336,8 +337,9 @@ void release_work(Work& w) {
   if (w.ev_fork) cudaEventDestroy(w.ev_fork);
   if (w.ev_join) cudaEventDestroy(w.ev_join);
   if (w.ev_heavy) cudaEventDestroy(w.ev_heavy);
+  if (w.ev_sparse) cudaEventDestroy(w.ev_sparse);
   w.cs2 = nullptr;
-  w.ev_fork = w.ev_join = w.ev_heavy = nullptr;
+  w.ev_fork = w.ev_join = w.ev_heavy = w.ev_sparse = nullptr;
   for (DevBuf* b : w.all()) release(*b);
   if (w.h_tables) cudaFreeHost(w.h_tables);
   if (w.h_status) cudaFreeHost(w.h_status);
@@ -358,6 +360,7 @@ int init_work(Work& w) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev_heavy, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev_sparse, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost(&w.h_status, 128);
   if (e != cudaSuccess) return wcuda(w, e, "work set-up");
   return GAKCO_OK;
@@ -1483,6 +1486,10 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
       const uint32_t cap = (uint32_t)c->dense_overflow;
       const int gemm_ctas = c->dense_sms > 0 ? std::min(c->dense_sms, c->nsm) : c->nsm;
       cudaMemsetAsync(w.dmaxc.p, 0, nmax_words * 4, ds);
+      // Optionally (one wave, two branches) the GEMM waits for the sparse
+      // levels' sort and run-length passes, so that it runs beside the
+      // accumulation rather than beside them.
+      const bool late = c->dense_late && fork && p.dwaves.size() == 1 && !p.chunks.empty();
       for (const DenseWave& wv : p.dwaves) {
         cudaMemsetAsync(ovf_n, 0, 4, ds);
         {
@@ -1490,6 +1497,11 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
           launch_dense_scatter(probs + wv.p0, wv.np, wv.p0, wv.rows, (const DsPack*)(base + p.o_pack),
                                (const MaskDesc*)(base + p.o_masks), (const uint64_t*)w.fullkey.p,
                                (uint32_t)(c->g * c->bits), ovf_n, (DenseOvf*)w.dovf.p, cap, ds);
+        }
+        if (late) {
+          for (const Chunk& ch : p.chunks) enqueue_chunk(c, w, p, ch, Tail::kGram);
+          cudaEventRecord(w.ev_sparse, w.cs);
+          cudaStreamWaitEvent(ds, w.ev_sparse, 0);
         }
         {
           Bracket b(c, w, "dense_gemm", 1);
@@ -1499,8 +1511,11 @@ int enqueue_gram(gakco_ctx* c, Work& w, const Plan& p, bool plain) {
         Bracket b(c, w, "dense_fix", 1);
         launch_dense_fix(probs, ovf_n, (const DenseOvf*)w.dovf.p, cap, status, ds);
       }
+      if (!late)
+        for (const Chunk& ch : p.chunks) enqueue_chunk(c, w, p, ch, Tail::kGram);
+    } else {
+      for (const Chunk& ch : p.chunks) enqueue_chunk(c, w, p, ch, Tail::kGram);
     }
-    for (const Chunk& ch : p.chunks) enqueue_chunk(c, w, p, ch, Tail::kGram);
     if (nh) {
       const HeavyProb* hp = (const HeavyProb*)(base + p.o_hprobs);
       const uint32_t* nitems = (const uint32_t*)w.hctr.p + 2 * nh;
@@ -2785,6 +2800,10 @@ int gakco_set_option(gakco_ctx* c, int key, int64_t v) {
       c->level_bits[m] = (int)b;
       break;
     }
+    case GAKCO_OPT_DENSE_LATE:
+      if (v != 0 && v != 1) return fail(c, GAKCO_E_INVALID, "dense late must be 0 or 1");
+      c->dense_late = (int)v;
+      break;
     case GAKCO_OPT_DENSE_SPLIT:
       if (v < -1 || v > 1) return fail(c, GAKCO_E_INVALID, "dense split must be -1, 0 or 1");
       c->dense_split = (int)v;

@@ -64,6 +64,16 @@ def test_dense_levels_match_the_oracle(case):
 
 
 @pytest.mark.parametrize("case", CASES[:3])
+def test_dense_gemm_after_the_sparse_passes_is_exact(case):
+    seed, n, sigma, lo, hi, g, k = case
+    codes, off = synth.random_small(seed, n, sigma, lo, hi)
+    ref = oracle.gram(codes, off, g, k)
+    out = _run(sigma, g, k, codes, off, dense=2, dense_late=1)
+    assert out["dense_problems"] > 0
+    _check(out, ref)
+
+
+@pytest.mark.parametrize("case", CASES[:3])
 def test_dense_tail_split_is_exact(case):
     """K-parts of the last wave's tiles (and of every tile when there are
     fewer tiles than CTAs) change nothing."""

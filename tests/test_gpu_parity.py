@@ -6,6 +6,8 @@ as (K * r_x) * r_y with r = 1/sqrt(K(x, x)), a few ulp from the oracle's
 K / sqrt(Kxx Kyy)).
 """
 
+import math
+
 import numpy as np
 import pytest
 
@@ -274,3 +276,26 @@ def test_autotune_keeps_results_and_caches_its_choice():
         assert ctx.autotune_device([t.data_ptr() for t in d_codes], [o for _, o in sets]) == "cached"
     for (c, o), out in zip(sets, outs):
         _check(out, oracle.gram(c, o, 8, 5))
+
+
+def test_work_statistics_follow_their_definitions():
+    """Packing reads every symbol once and writes a key and a window id per
+    window; the combine tail reads the upper triangles of C_0..C_M once and
+    writes every requested output; every stage with work reports bytes."""
+    g, k = 8, 4
+    codes, off = synth.random_small(60, 45, 20, 0, 300)
+    n, M = len(off) - 1, g - k
+    G = int(np.maximum(np.diff(off) - g + 1, 0).sum())
+    with pkg.gakco_create(20, g, k) as ctx:
+        ctx.gram(codes, off, khat=True, nm=True)
+        assert ctx.get_stat("pack_bytes") == float(off[-1] + 12 * G)
+        assert ctx.get_stat("combine_bytes") == 4.0 * (M + 1) * n * (n + 1) / 2 + (4 + 8 + 4 * (M + 1)) * n * n
+        assert ctx.get_stat("sort_bytes") > 0 and ctx.get_stat("rle_bytes") > 0
+        assert ctx.get_stat("masks") == sum(math.comb(g, m) for m in range(M + 1))
+
+
+def test_shared_atomic_probe_rates():
+    a = pkg.gakco_measure_smem_atomics()
+    r = pkg.gakco_measure_smem_atomics(random_columns=True)
+    assert a > 1e11 and r > 1e10
+    assert r <= 1.05 * a
