@@ -386,10 +386,9 @@ k_downsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_
 constexpr uint64_t kOsAgg = 1ull << 46, kOsIncl = 2ull << 46;
 constexpr uint64_t kOsValue = (1ull << 46) - 1;
 constexpr long long kOsWaitCycles = 4000000000ll;  // about 2 s
-#ifndef GK_OSB
-#define GK_OSB 8
-#endif
-constexpr int kOsBatch = GK_OSB;  // predecessor words loaded together in the look-back
+// Predecessor words loaded together in the look-back.  One at a time
+// measured fastest (4, 8 and 16 raise register pressure and spill).
+constexpr int kOsBatch = 1;
 
 __device__ __forceinline__ void os_store(uint64_t* p, uint64_t v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
