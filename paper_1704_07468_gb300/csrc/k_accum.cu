@@ -531,6 +531,7 @@ void launch_accum(const AccParams& p, int threads, int variant, int blocks, size
     accum_v<1>(p, threads, blocks, smem, st);
   else if (variant == 2)
     accum_v<2>(p, threads, blocks, smem, st);
+
   else
     accum_v<0>(p, threads, blocks, smem, st);
 }
