@@ -46,8 +46,10 @@ L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 SMEM_BANKS = 32              # shared-memory banks per SM (32-bit each)
 
 
-def make_workload(name, rank=0, dna_sizes=None):
-    """-> (description, sigma, g, k, list of (codes, offsets))."""
+def make_workload(name, rank=0, dna_sizes=None, n=None):
+    """-> (description, sigma, g, k, list of (codes, offsets)); ``n``
+    overrides the sequence count of the single-dataset workloads (smaller
+    cases for profiling)."""
     off = 1000 * rank
     if name == "dna_large":
         sizes = tuple(dna_sizes) if dna_sizes else synth.DNA_LARGE_SIZES
@@ -56,15 +58,18 @@ def make_workload(name, rank=0, dna_sizes=None):
         return (f"DNA large-M batched: {len(sizes)} datasets, N={'/'.join(map(str, sizes))}, "
                 "lengths U[100,300], GC 0.4, g=10 k=6 (M=4)", 4, 10, 6, sets)
     if name == "dna_toy":
-        return ("DNA toy: N=200, length 100, uniform ACGT, g=7 k=5 (M=2)", 4, 7, 5,
-                [synth.dna_toy(seed=1 + off)])
+        nn = n or 200
+        return (f"DNA toy: N={nn}, length 100, uniform ACGT, g=7 k=5 (M=2)", 4, 7, 5,
+                [synth.dna_toy(seed=1 + off, n=nn)])
     if name == "protein":
-        return ("protein: N=3312, sigma=20, Dirichlet(2) residues, log-normal lengths "
+        nn = n or 3312
+        return (f"protein: N={nn}, sigma=20, Dirichlet(2) residues, log-normal lengths "
                 "(median 300, clipped [50,1000]), g=8 k=4 (M=4)", 20, 8, 4,
-                [synth.protein(seed=7 + off)])
+                [synth.protein(seed=7 + off, n=nn)])
     if name == "text":
-        return ("text: N=6000, sigma=36, Zipf(1.1) symbols, lengths U[200,2000], "
-                "g=8 k=5 (M=3)", 36, 8, 5, [synth.text(seed=8 + off)])
+        nn = n or 6000
+        return (f"text: N={nn}, sigma=36, Zipf(1.1) symbols, lengths U[200,2000], "
+                "g=8 k=5 (M=3)", 36, 8, 5, [synth.text(seed=8 + off, n=nn)])
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -512,7 +517,7 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     lib_build.build()
-    desc, sigma, g, k, sets = make_workload(args.workload, rank, args.dna_sizes)
+    desc, sigma, g, k, sets = make_workload(args.workload, rank, args.dna_sizes, args.n)
     ns = [len(o) - 1 for _, o in sets]
     entries = float(sum(n * n for n in ns))
 
@@ -832,6 +837,8 @@ def main():
                     help="engine option (paper_1704_07468_gb300.OPT name) set after autotuning; repeatable")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
+    ap.add_argument("--n", type=int, default=None,
+                    help="sequences of the dna_toy / protein / text workload (smaller cases for profiling)")
     ap.add_argument("--dna-sizes", type=lambda v: [int(t) for t in v.split(",")], default=None,
                     help="subset of DNA dataset sizes (small cases for profiling)")
     args = ap.parse_args()
