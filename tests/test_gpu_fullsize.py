@@ -1,8 +1,8 @@
 """Full-size parity: the workloads at their benchmark sizes, run in the
 benchmark's launch configuration (one batched device call, CUDA graph).
 
-Every row of the DNA toy, DNA large-M and protein Gram matrices, and the
-text rows the survey's sampling names (every 23rd plus the first and last
+Every row of the DNA toy, DNA large-M and protein Gram matrices, and a
+deterministic sample of the text rows (every 23rd plus the first and last
 8), is compared with the oracle through a per-row digest of K and N_0..N_M
 (``tests/golden/fullsize_row_hashes.json``, written by
 ``tests/golden/make_fullsize_hashes.py`` from the oracle alone: hours of
