@@ -184,7 +184,8 @@ const char *gakco_last_error(const gakco_ctx *ctx);
 /* How the sparse accumulation (countAndUpdate, Alg. 1) walks a feature's
  * entries when the range is shorter than a warp: 0 = up to four per lane
  * directly, the rest in rounds of 32 whose owners a shuffle search finds;
- * 1 = all in rounds of 32, owners from a warp-wide OR of range starts;
+ * 1 = ranges shorter than 64 in rounds of 32, owners from a warp-wide OR
+ * of range starts;
  * 2 = the direct step of 0, then the rounds of 1.  Identical results; the
  * autotuner picks one per workload (default 0). */
 #define GAKCO_OPT_ACCUM_VARIANT 27

@@ -32,7 +32,11 @@ namespace gk {
 namespace {
 
 constexpr uint32_t kFull = 0xffffffffu;
-constexpr uint32_t kLong = 32;  // entry ranges this long are walked by a warp
+// Entry ranges at least this long are walked by a whole warp, one range at
+// a time; shorter ones by the variant's rounds.  The OR-owner rounds fill
+// every lane, so variant 1 keeps ranges up to 63 in them (measured on DNA:
+// threshold 32 / 64 / 128 / none: 10.74 / 10.37 / 10.78 / 10.88 ms).
+constexpr uint32_t long_threshold(int variant) { return variant == 1 ? 64u : 32u; }
 
 // First entry in [lo, hi) whose sequence is >= seq.
 __device__ __forceinline__ uint32_t lower_bound_seq(const uint32_t* __restrict__ es,
@@ -74,16 +78,17 @@ __device__ __forceinline__ uint32_t ie_combine(const uint32_t* C, uint32_t M,
 //   0: up to four pairs per lane directly (each lane loads its own range),
 //      the rest in rounds of 32 pairs whose owner lanes are found by a
 //      shuffle binary search over the ranges' running counts;
-//   1: every pair in rounds of 32 (consecutive lanes load consecutive
-//      entries), owners found from a warp-wide OR of the range starts that
-//      fall in the round (no shuffles; the owners' data in a per-warp
-//      shared table);
+//   1: every pair of a range shorter than 64 in rounds of 32 (consecutive
+//      lanes load consecutive entries), owners found from a warp-wide OR of
+//      the range starts that fall in the round (no shuffles; the owners'
+//      data in a per-warp shared table);
 //   2: the direct step of 0, then the rounds of 1 for what is left.
 // Every variant is held to 32 registers, so that eight 256-thread blocks
 // stay resident per SM.
 template <int kThreads, int kExpand>
 __global__ void __launch_bounds__(kThreads, 2048 / kThreads)
 k_accum(const AccParams p) {
+  constexpr uint32_t kLong = long_threshold(kExpand);
   extern __shared__ uint32_t acc[];   // ncols counters of one row of C_m + a trash slot
   __shared__ uint32_t s_item;
   constexpr int kWarps = kThreads / 32;
@@ -531,7 +536,6 @@ void launch_accum(const AccParams& p, int threads, int variant, int blocks, size
     accum_v<1>(p, threads, blocks, smem, st);
   else if (variant == 2)
     accum_v<2>(p, threads, blocks, smem, st);
-
   else
     accum_v<0>(p, threads, blocks, smem, st);
 }
