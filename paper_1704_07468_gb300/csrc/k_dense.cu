@@ -166,6 +166,19 @@ __device__ __forceinline__ uint32_t e4m3x2_of_counts(uint32_t clamped) {
   return e;
 }
 
+// e4m3 bytes of the counts 0..7 (1 = 0x38: exponent 7, mantissa 0; ...;
+// 7 = 0x4E), as the eight bytes of a byte-permute table.
+constexpr uint32_t kE4m3Counts0to3 = 0x44403800u;
+constexpr uint32_t kE4m3Counts4to7 = 0x4E4C4A48u;
+
+// Four counts 0..7, two per word with the lower column in the low half, ->
+// their four e4m3 bytes in column order: the counts become the four 3-bit
+// selectors of one byte permute over the table above.
+__device__ __forceinline__ uint32_t e4m3x4_of_small_counts(uint32_t w01, uint32_t w23) {
+  const uint32_t t = w01 | (w23 << 8);  // c0 at bit 0, c2 at 8, c1 at 16, c3 at 24
+  return __byte_perm(kE4m3Counts0to3, kE4m3Counts4to7, t | (t >> 12));
+}
+
 // The integer an e4m3 byte of a count (0..16) encodes: exponent bias 7,
 // three mantissa bits, v = 2^(e-7) (1 + m/8).
 __device__ __forceinline__ uint32_t e4m3_small_value(uint32_t b) {
@@ -214,7 +227,7 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
     const uint32_t words = (uint32_t)(ld < (uint64_t)kDenseScatterCols ? ld : kDenseScatterCols) / 2;
     for (uint32_t i = tid; i < words / 4; i += kScatterThreads) ((uint4*)cnt)[i] = make_uint4(0, 0, 0, 0);
   }
-  uint32_t or2 = 0;  // OR of every count word: an upper bound of the largest count
+  uint32_t cmax = 0;  // per-half maximum of every count word
   for (uint64_t c0 = 0; c0 < ld; c0 += kDenseScatterCols) {
     const uint32_t ncol = (uint32_t)(ld - c0 < (uint64_t)kDenseScatterCols ? ld - c0 : kDenseScatterCols);
     const uint32_t mu0 = (uint32_t)(c0 >> kb);
@@ -253,34 +266,38 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
     for (uint32_t u = tid; u < ncol / 8; u += kScatterThreads) {
       const uint4 a = cw[u];
       cw[u] = make_uint4(0, 0, 0, 0);
-      const uint32_t w[4] = {a.x, a.y, a.z, a.w};
-      // A 16-bit count c exceeds 16 iff c + 15 reaches bit 5 or c has bit
-      // 15 set (c + 15 then carries out of its half); both show in bits 5-15.
-      const uint32_t any = (a.x + 0x000F000Fu) | (a.y + 0x000F000Fu) | (a.z + 0x000F000Fu) |
-                           (a.w + 0x000F000Fu) | a.x | a.y | a.z | a.w;
-      or2 |= a.x | a.y | a.z | a.w;
-      uint32_t e[4];
-      if ((any & 0xFFE0FFE0u) == 0u) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) e[q] = e4m3x2_of_counts(w[q]);
+      const uint32_t m = __vmaxu2(__vmaxu2(a.x, a.y), __vmaxu2(a.z, a.w));
+      cmax = __vmaxu2(cmax, m);
+      uint2 o;
+      if ((m & 0xFFF8FFF8u) == 0u) {
+        // Every count <= 7 (nearly all words): table lookup.
+        o = make_uint2(e4m3x4_of_small_counts(a.x, a.y), e4m3x4_of_small_counts(a.z, a.w));
       } else {
+        const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+        uint32_t e[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) e[q] = e4m3x2_of_counts(__vminu2(w[q], 0x00100010u));
+        o = make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
+        // A half h of m exceeds 16 iff h + 15 reaches bit 5 or h is above
+        // 65520 (h + 15 then carries out of its half); both show in bits
+        // 5-15 of (m + 15) | m.
+        if ((((m + 0x000F000Fu) | m) & 0xFFE0FFE0u) != 0u) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const uint32_t c = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-          if (c > 16) {
-            const uint32_t slot = atomicAdd(ovf_n, 1u);
-            if (slot < ovf_cap) ovf[slot] = DenseOvf{p0 + lo, x, (uint32_t)(c0 + 8 * u + q), c};
+          for (int q = 0; q < 8; ++q) {
+            const uint32_t c = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+            if (c > 16) {
+              const uint32_t slot = atomicAdd(ovf_n, 1u);
+              if (slot < ovf_cap) ovf[slot] = DenseOvf{p0 + lo, x, (uint32_t)(c0 + 8 * u + q), c};
+            }
           }
         }
       }
-      out[u] = make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
+      out[u] = o;
     }
     // The next chunk's counting waits at its first barrier for this
     // conversion (and its clearing) to finish.
   }
-  uint32_t mymax = min((or2 & 0xFFFFu) | (or2 >> 16), 16u);  // >= the largest entry of A
+  uint32_t mymax = min(max(cmax & 0xFFFFu, cmax >> 16), 16u);  // the largest entry of A
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mymax = max(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
   if ((tid & 31) == 0 && mymax) atomicMax(P.maxc, mymax);

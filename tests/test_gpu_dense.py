@@ -139,6 +139,25 @@ def test_overflows_sharing_a_column():
     _check(out, ref)
 
 
+def test_every_count_value_is_encoded_exactly():
+    """A homopolymer of length g - 1 + c holds one column of count c in
+    every mask, for c = 0..20: each count 1..7 goes through the scatter's
+    table of e4m3 bytes, 8..16 through the f16 conversion, 17..20 through
+    the overflow list.  Mixed with random rows and two-symbol blocks, whose
+    counts share 8-column words with other counts."""
+    g, k = 6, 3
+    rng = np.random.default_rng(130)
+    seqs = [np.full(g - 1 + c, c % 4, np.uint8) for c in range(21)]
+    seqs += [np.concatenate([np.zeros(g - 1 + a, np.uint8), np.ones(g - 1 + b, np.uint8)])
+             for a, b in ((3, 9), (7, 8), (12, 2), (16, 17))]
+    seqs += [rng.integers(0, 4, int(n), dtype=np.uint8) for n in rng.integers(5, 90, 12)]
+    codes, off = synth.pack(seqs)
+    ref = oracle.gram(codes, off, g, k)
+    out = _run(4, g, k, codes, off, dense=2)
+    assert out["dense_problems"] > 0
+    _check(out, ref)
+
+
 def test_full_overflow_list_reruns_sparse():
     """An overflow list too small for the input: the call reruns with every
     level sparse and stays exact."""
