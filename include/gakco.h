@@ -258,14 +258,15 @@ int gakco_kernel_timing(const gakco_ctx *ctx, int idx, char *name,
 
 /*
  * Autotuner: times the stages of gakco_gram_batch_device on the given
- * datasets (device codes, host offsets) for a few values of the sort digit
- * width (6, 8, 10 bits), the sort chunk size (2^22..2^26 elements), the
- * accumulation block size (256, 512 threads) and the mask-group size
- * (32..128 MiB), one parameter at a time, and sets the fastest on the
- * context.  Results are cached per (sigma, g, k, SM count, size buckets)
- * for the life of the process, so a second call for a similar workload
- * returns at once.  `report` (may be NULL) receives the choice.  The
- * options only change speed, never results.
+ * datasets (device codes, host offsets), one parameter at a time, and sets
+ * the fastest on the context: the sort digit width (6, 8, 10 bits, then
+ * per level 7..11), the sort chunk size (2^22..2^26 elements), the
+ * run-length items per thread (16, 8), the accumulation block size (256,
+ * 512 threads) with the mask-group size (64..512 MiB), the dense-level mode
+ * (0, 1, 2) and the accumulation variant (0, 1, 2).  Results are cached per
+ * (sigma, g, k, SM count, size buckets) for the life of the process, so a
+ * second call for a similar workload returns at once.  `report` (may be
+ * NULL) receives the choice.  The options only change speed, never results.
  */
 int gakco_autotune(gakco_ctx *ctx, int32_t ndata, const uint8_t *const *codes,
                    const int64_t *const *offsets, const int32_t *n,

@@ -1615,13 +1615,16 @@ int check_status(gakco_ctx* c, Work& w) {
   w.heavy_cols = (double)wk[4];
   w.heavy_flops = (double)wk[5];
   if (st & kErrBadCode) return wfail(w, GAKCO_E_INVALID, "input holds a symbol >= sigma (%d)", c->sigma);
-  if (st & kErrKneCM) return wfail(w, GAKCO_E_INTERNAL, "internal check failed: sum h_m N_m != C_M");
-  if (st & kErrBadEntry) return wfail(w, GAKCO_E_INTERNAL, "internal check failed: entry out of range");
-  if (st & kErrTimeout) return wfail(w, GAKCO_E_TIMEOUT, "a bounded wait in the dense GEMM ran out");
+  // A full overflow list leaves the dense levels uncorrected (which later
+  // checks may flag too): the caller reruns the call with every level
+  // sparse, so this comes first.
   if (st & kErrDenseOverflow) {
     w.dense_overflow = true;
     return wfail(w, GAKCO_E_INTERNAL, "dense overflow list full");
   }
+  if (st & kErrKneCM) return wfail(w, GAKCO_E_INTERNAL, "internal check failed: sum h_m N_m != C_M");
+  if (st & kErrBadEntry) return wfail(w, GAKCO_E_INTERNAL, "internal check failed: entry out of range");
+  if (st & kErrTimeout) return wfail(w, GAKCO_E_TIMEOUT, "a bounded wait in the dense GEMM ran out");
   if (st) return wfail(w, GAKCO_E_INTERNAL, "device status 0x%x", st);
   return GAKCO_OK;
 }
