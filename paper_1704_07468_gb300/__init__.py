@@ -204,23 +204,43 @@ class Context:
         return out
 
     # -- host-buffer calls -----------------------------------------------
-    def gram(self, codes, offsets, khat=True, nm=False, K=True):
+    def gram(self, codes, offsets, khat=True, nm=False, K=True, out=None):
         """Gram kernel of one dataset (host arrays).  Returns a dict with
-        ``K`` (n, n) int32, ``Khat`` (n, n) float64, ``Nm`` (M+1, n, n)."""
-        return self.gram_batch([(codes, offsets)], khat=khat, nm=nm, K=K)[0]
+        ``K`` (n, n) int32, ``Khat`` (n, n) float64, ``Nm`` (M+1, n, n).
+        ``out``: such a dict to write into instead of new arrays."""
+        return self.gram_batch([(codes, offsets)], khat=khat, nm=nm, K=K,
+                               out=None if out is None else [out])[0]
 
-    def gram_batch(self, datasets, khat=True, nm=False, K=True):
-        """Gram kernels of several datasets in one batched call."""
+    def gram_batch(self, datasets, khat=True, nm=False, K=True, out=None):
+        """Gram kernels of several datasets in one batched call.  ``out``:
+        one dict per dataset (keys ``K``, ``Khat``, ``Nm``, C-contiguous
+        arrays of the shapes and dtypes above) that the call writes into, so
+        that repeated calls reuse their host buffers; returned as given."""
         ds = [_dataset(c, o) for c, o in datasets]
         nd = len(ds)
         ns = np.array([len(o) - 1 for _, o in ds], dtype=np.int32)
-        outs = []
-        for (c, o), n in zip(ds, ns):
-            outs.append({
-                "K": np.empty((n, n), np.int32) if K else None,
-                "Khat": np.empty((n, n), np.float64) if khat else None,
-                "Nm": np.empty((self.M + 1, n, n), np.int32) if nm else None,
-            })
+        if out is not None:
+            if len(out) != nd:
+                raise ValueError("out needs one dict per dataset")
+            specs = (("K", K, np.int32, lambda n: (n, n)), ("Khat", khat, np.float64, lambda n: (n, n)),
+                     ("Nm", nm, np.int32, lambda n: (self.M + 1, n, n)))
+            for o, n in zip(out, ns):
+                for key, want, dt, shape in specs:
+                    a = o.get(key) if want else None
+                    if want and (a is None or a.dtype != dt or a.shape != shape(int(n))
+                                 or not a.flags.c_contiguous or not a.flags.writeable):
+                        raise ValueError(f"out[{key!r}] must be a writable C-contiguous "
+                                         f"{np.dtype(dt).name} array of shape {shape(int(n))}")
+                    o[key] = a
+            outs = out
+        else:
+            outs = []
+            for (c, o), n in zip(ds, ns):
+                outs.append({
+                    "K": np.empty((n, n), np.int32) if K else None,
+                    "Khat": np.empty((n, n), np.float64) if khat else None,
+                    "Nm": np.empty((self.M + 1, n, n), np.int32) if nm else None,
+                })
         keep = [c if c.size else np.zeros(1, np.uint8) for c, _ in ds]
         rc = self._lib.gakco_gram_batch(
             self._h, nd,

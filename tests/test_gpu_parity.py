@@ -160,6 +160,31 @@ def test_accumulation_variants_bit_exact(case, variant):
     _check(_gram(sigma, g, k, codes, off, accum_variant=variant), ref)
 
 
+def test_caller_kept_outputs_are_rewritten_in_place():
+    """gram_batch(out=...) writes every call's results into the given host
+    arrays (returned as the same objects); a wrong shape or dtype is
+    refused before the call."""
+    sets = [synth.random_small(31, 40, 4, 50, 200), synth.random_small(32, 25, 4, 50, 200)]
+    refs = [oracle.gram(c, o, 10, 6) for c, o in sets]
+    outs = [{"K": np.full((len(o) - 1, len(o) - 1), -1, np.int32),
+             "Khat": np.full((len(o) - 1, len(o) - 1), np.nan)} for _, o in sets]
+    with pkg.gakco_create(4, 10, 6) as ctx:
+        for _ in range(2):
+            got = ctx.gram_batch(sets, khat=True, nm=False, out=outs)
+            assert got is outs
+            for out, ref in zip(outs, refs):
+                _check(out, ref, nm=False)
+            for out in outs:
+                out["K"].fill(-1)
+                out["Khat"].fill(np.nan)
+        bad = [{"K": np.empty((3, 3), np.int32), "Khat": outs[0]["Khat"]}, outs[1]]
+        with pytest.raises(ValueError):
+            ctx.gram_batch(sets, khat=True, out=bad)
+        with pytest.raises(ValueError):
+            ctx.gram_batch(sets, khat=True, out=[{"K": outs[0]["K"], "Khat": outs[0]["Khat"].astype(np.float32)},
+                                                 outs[1]])
+
+
 @pytest.mark.parametrize("kind", ["homopolymer", "period2", "mixed"])
 def test_repetitive_sequences_large_counts(kind):
     """Counts of one feature in one sequence far above 127."""
