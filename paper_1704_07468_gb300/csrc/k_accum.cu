@@ -38,6 +38,13 @@ constexpr uint32_t kFull = 0xffffffffu;
 // threshold 32 / 64 / 128 / none: 10.74 / 10.37 / 10.78 / 10.88 ms).
 constexpr uint32_t long_threshold(int variant) { return variant == 1 ? 64u : 32u; }
 
+// 1 << d, and 0 for d >= 32 (PTX clamps the shift amount at the width).
+__device__ __forceinline__ uint32_t bit_or_zero(uint32_t d) {
+  uint32_t b;
+  asm("shl.b32 %0, %1, %2;" : "=r"(b) : "r"(1u), "r"(d));
+  return b;
+}
+
 // First entry in [lo, hi) whose sequence is >= seq.
 __device__ __forceinline__ uint32_t lower_bound_seq(const uint32_t* __restrict__ es,
                                                     uint32_t lo, uint32_t hi,
@@ -94,7 +101,7 @@ k_accum(const AccParams p) {
   constexpr int kWarps = kThreads / 32;
   // Per warp: the chunk's non-empty entry ranges in lane order (first entry
   // minus the range's first pair number, and the multiplier c_x).
-  __shared__ uint32_t s_rb[kWarps][32], s_rc[kWarps][32];
+  __shared__ uint2 s_rbc[kWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   for (;;) {
@@ -240,21 +247,29 @@ k_accum(const AccParams p) {
           const uint32_t start = incl - cnt;  // the range's first pair number
           if (cnt) {
             const uint32_t rank = __popc(nz & lt_mask);
-            s_rb[w][rank] = lo - start;
-            s_rc[w][rank] = c;
+            s_rbc[w][rank] = make_uint2(lo - start, c);
           }
           __syncwarp();
+          // Round p0 sets bit start - p0 - 1 for every range starting at
+          // pairs p0 + 1 .. p0 + 32; empty ranges never set one.
+          const uint32_t dpos = cnt ? start - 1u : 0x80000000u;
           uint32_t owner0 = 0;  // rank of the range holding the round's first pair
-          for (uint32_t p0 = 0; p0 < total; p0 += 32) {
-            const uint32_t d = start - p0 - 1u;  // starts at p0 + 1 .. p0 + 32
-            const uint32_t bits = __reduce_or_sync(kFull, (cnt != 0 && d < 32u) ? (1u << d) : 0u);
-            const uint32_t pp = p0 + lane;
-            if (pp < total) {
-              const uint32_t o = owner0 + __popc(bits & lt_mask);
-              const uint32_t v = es[s_rb[w][o] + pp];
-              atomicAdd(&acc[min((v >> 16) - c0, width)], s_rc[w][o] * (v & 0xFFFFu));
-            }
+          uint32_t pp = lane;   // this lane's pair in the round
+          const uint32_t full = total & ~31u;
+          for (uint32_t p0 = 0; p0 < full; p0 += 32, pp += 32) {
+            const uint32_t bits = __reduce_or_sync(kFull, bit_or_zero(dpos - p0));
+            const uint2 rc = s_rbc[w][owner0 + __popc(bits & lt_mask)];
+            const uint32_t v = es[rc.x + pp];
+            atomicAdd(&acc[min((v >> 16) - c0, width)], rc.y * (v & 0xFFFFu));
             owner0 += __popc(bits);
+          }
+          if (full < total) {
+            const uint32_t bits = __reduce_or_sync(kFull, bit_or_zero(dpos - full));
+            if (pp < total) {
+              const uint2 rc = s_rbc[w][owner0 + __popc(bits & lt_mask)];
+              const uint32_t v = es[rc.x + pp];
+              atomicAdd(&acc[min((v >> 16) - c0, width)], rc.y * (v & 0xFFFFu));
+            }
           }
           __syncwarp();
         }
