@@ -611,7 +611,9 @@ def run_ours(args):
         dt = (time.perf_counter() - t0) * 1000.0
         if i > 1:
             e2e_ms.append(dt)
-    e2e_step = float(np.mean(e2e_ms))
+    # Median: a single host-side stall (seen at times on the shared box, tens
+    # of ms) would otherwise dominate the mean; every call is listed in calls_ms.
+    e2e_step = float(np.median(e2e_ms))
     h2d = int(sum(c.nbytes + o.nbytes for c, o in sets))
     d2h = int(sum(n * n * (4 + 8) for n in ns))
 
