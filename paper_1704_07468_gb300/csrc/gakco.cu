@@ -881,7 +881,10 @@ void plan_dense(gakco_ctx* c, Plan& p, bool plain) {
       p.dense[d * L + m] = 1;
       const uint32_t mc = me - mf;
       const uint64_t by_mem = std::max<uint64_t>(1, budget / per_mask);
-      const uint64_t by_cols = std::max<uint64_t>(1, (uint64_t)c->dense_run_cols / S);
+      // (A problem's row stays below 2^31 columns: the scatter indexes a
+      // row's columns in 32-bit arithmetic.)
+      const uint64_t by_cols =
+          std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)c->dense_run_cols, (uint64_t)1 << 31) / S);
       const uint32_t gmax = (uint32_t)std::min<uint64_t>(mc, std::min(by_mem, by_cols));
       const uint32_t ng = (mc + gmax - 1) / gmax;
       for (uint32_t gi = 0; gi < ng; ++gi) {

@@ -58,6 +58,18 @@ constexpr int kGemmThreads = 192;
 constexpr uint32_t kTmemCols = 512;  // two 128 x 256 f32 accumulators
 constexpr int kScatterThreads = 512;
 constexpr int kScatterMasks = 16;  // masks of one scatter block held in shared memory
+constexpr int kScatterWarps = kScatterThreads / 32;
+constexpr int kScatterRuns = 5;    // kept-position runs of a mask cut in registers
+constexpr int kRunMasks = 64;      // masks of one problem whose runs a scatter block stages
+
+// A mask's kept-position runs for the scatter's 32-bit cut (nruns = ~0:
+// the mask takes the generic cut).  A run moves from bit sr of the full key
+// to bit sl <= sr of the masked key, so it is (full >> (sr - sl)) & (mask
+// << sl): one shift and one AND-OR per run.
+struct MaskRuns {
+  uint32_t nruns;
+  uint32_t sh[kScatterRuns], mk[kScatterRuns];
+};
 constexpr long long kWaitCycles = 4000000000ll;  // about 2 s (drains; default for the role waits)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -201,7 +213,8 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
                 const MaskDesc* __restrict__ masks, const uint64_t* __restrict__ fullkey, uint32_t* __restrict__ ovf_n,
                 DenseOvf* __restrict__ ovf, uint32_t ovf_cap) {
   extern __shared__ uint32_t cnt[];  // two 16-bit counts per word (counts <= 65535 windows)
-  __shared__ MaskDesc smask[kScatterMasks];
+  __shared__ MaskDesc smask[kNarrow ? 1 : kScatterMasks];
+  __shared__ MaskRuns sruns[kNarrow ? kRunMasks : 1];
   const uint32_t bx = blockIdx.x, tid = threadIdx.x;
   uint32_t lo = 0, hi = nprobs;  // last problem with row0 <= bx
   while (hi - lo > 1) {
@@ -227,6 +240,22 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
     const uint32_t words = (uint32_t)(ld < (uint64_t)kDenseScatterCols ? ld : kDenseScatterCols) / 2;
     for (uint32_t i = tid; i < words / 4; i += kScatterThreads) ((uint4*)cnt)[i] = make_uint4(0, 0, 0, 0);
   }
+  // 32-bit keys: the runs of every mask of the problem, staged once.
+  const bool runs_staged = kNarrow && P.mcount <= (uint32_t)kRunMasks;
+  if (runs_staged) {
+    for (uint32_t i = tid; i < P.mcount; i += kScatterThreads) {
+      const MaskDesc& md = masks[P.mfirst + i];
+      MaskRuns r{};
+      r.nruns = (md.fold == 0 && md.nruns <= (uint32_t)kScatterRuns) ? md.nruns : ~0u;
+#pragma unroll
+      for (int q = 0; q < kScatterRuns; ++q) {
+        const bool on = (uint32_t)q < md.nruns && r.nruns != ~0u;
+        r.sh[q] = on ? md.sr[q] - md.sl[q] : 0u;
+        r.mk[q] = on ? (uint32_t)md.msk[q] << md.sl[q] : 0u;
+      }
+      sruns[i] = r;
+    }
+  }
   uint32_t cmax = 0;  // per-half maximum of every count word
   for (uint64_t c0 = 0; c0 < ld; c0 += kDenseScatterCols) {
     const uint32_t ncol = (uint32_t)(ld - c0 < (uint64_t)kDenseScatterCols ? ld - c0 : kDenseScatterCols);
@@ -234,7 +263,7 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
     uint32_t mu1 = (uint32_t)((c0 + ncol - 1) >> kb) + 1;
     if (mu1 > P.mcount) mu1 = P.mcount;
     const uint32_t nmu = (nw > 0 && mu1 > mu0) ? mu1 - mu0 : 0;
-    const bool staged = nmu <= (uint32_t)kScatterMasks;
+    const bool staged = !kNarrow && nmu <= (uint32_t)kScatterMasks;
     if (staged) {
       // The chunk's masks, for warp-broadcast reads below.
       const uint32_t words = nmu * (uint32_t)(sizeof(MaskDesc) / 4);
@@ -242,18 +271,59 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
       for (uint32_t i = tid; i < words; i += kScatterThreads) ((uint32_t*)smask)[i] = src[i];
     }
     __syncthreads();
-    // Mask-major: the lanes of a warp mostly share one mask and read
-    // consecutive windows.
-    uint32_t mi = nw ? tid / nw : 0, w = nw ? tid - mi * nw : 0;
-    for (uint32_t i = tid; i < nw * nmu; i += kScatterThreads) {
-      const MaskDesc& md = staged ? smask[mi] : masks[P.mfirst + mu0 + mi];
-      const uint64_t key = kNarrow ? (uint64_t)masked_key32((uint32_t)fk[w], md) : masked_key(fk[w], md);
-      const uint64_t col = (((uint64_t)(mu0 + mi) << kb) | key) - c0;
-      if (col < ncol) atomicAdd(&cnt[col >> 1], 1u << (16 * (uint32_t)(col & 1)));
-      w += kScatterThreads;
-      while (w >= nw) {
-        w -= nw;
-        ++mi;
+    if constexpr (kNarrow) {
+      // Tasks of (mask, slice of the row's windows), one per warp at a time,
+      // kScatterWarps of them per chunk when the chunk has that few masks: a
+      // warp loads its mask's runs once (uniform shared-memory reads) and
+      // walks its windows 32 at a time, cutting each key with shifts and
+      // masks alone (runs mode; folded keys take the generic cut).
+      const uint32_t S = nmu ? max(1u, (uint32_t)kScatterWarps / nmu) : 1u;
+      const uint32_t per = ((nw + S - 1) / S + 31) & ~31u;
+      for (uint32_t task = tid >> 5; task < nmu * S; task += kScatterWarps) {
+        const uint32_t mi = task / S, s = task - mi * S;
+        // Column of key 0 of the mask within the chunk, modulo 2^32 (a
+        // problem's row holds fewer than 2^31 columns): keys of the masks
+        // outside the chunk wrap to indices above ncol.
+        const uint32_t cbase = ((mu0 + mi) << kb) - (uint32_t)c0;
+        const uint32_t wlo = s * per, whi = min(nw, wlo + per);
+        const uint32_t nr = runs_staged ? sruns[mu0 + mi].nruns : ~0u;
+        if (nr != ~0u) {
+          const MaskRuns& mr = sruns[mu0 + mi];
+          uint32_t sh[kScatterRuns], mk[kScatterRuns];
+#pragma unroll
+          for (int r = 0; r < kScatterRuns; ++r) {
+            sh[r] = mr.sh[r];
+            mk[r] = mr.mk[r];
+          }
+          for (uint32_t wi = wlo + (tid & 31); wi < whi; wi += 32) {
+            const uint32_t f = (uint32_t)fk[wi];
+            uint32_t k = 0;
+#pragma unroll
+            for (int r = 0; r < kScatterRuns; ++r) k |= (f >> sh[r]) & mk[r];
+            const uint32_t col = cbase + k;
+            if (col < ncol) atomicAdd(&cnt[col >> 1], 1u << (16 * (col & 1)));
+          }
+        } else {
+          const MaskDesc& md = masks[P.mfirst + mu0 + mi];
+          for (uint32_t wi = wlo + (tid & 31); wi < whi; wi += 32) {
+            const uint32_t col = cbase + masked_key32((uint32_t)fk[wi], md);
+            if (col < ncol) atomicAdd(&cnt[col >> 1], 1u << (16 * (col & 1)));
+          }
+        }
+      }
+    } else {
+      // 64-bit keys: mask-major over (mask, window), the lanes of a warp
+      // mostly sharing one mask and reading consecutive windows.
+      uint32_t mi = nw ? tid / nw : 0, w = nw ? tid - mi * nw : 0;
+      for (uint32_t i = tid; i < nw * nmu; i += kScatterThreads) {
+        const MaskDesc& md = staged ? smask[mi] : masks[P.mfirst + mu0 + mi];
+        const uint64_t col = (((uint64_t)(mu0 + mi) << kb) | masked_key(fk[w], md)) - c0;
+        if (col < ncol) atomicAdd(&cnt[col >> 1], 1u << (16 * (uint32_t)(col & 1)));
+        w += kScatterThreads;
+        while (w >= nw) {
+          w -= nw;
+          ++mi;
+        }
       }
     }
     __syncthreads();

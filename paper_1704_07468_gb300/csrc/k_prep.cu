@@ -94,28 +94,40 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v,
 constexpr int kRegRuns = 6;
 
 struct MaskRegs {
-  uint32_t sr[kRegRuns], sl[kRegRuns];
-  uint64_t mk[kRegRuns];
-  bool fits;
+  uint32_t sh[kRegRuns];  // sr - sl: a run moves from bit sr of the full key to bit sl <= sr
+  uint64_t mk[kRegRuns];  // the run's mask at its place in the masked key (msk << sl)
+  bool fits;              // runs mode with at most kRegRuns runs
+  bool fits32;            // ... every run within the full key's low 32 bits
 };
 
 __device__ __forceinline__ void mask_regs(const MaskDesc& md, MaskRegs& r) {
   r.fits = md.fold == 0 && md.nruns <= (uint32_t)kRegRuns;
+  r.fits32 = r.fits;
 #pragma unroll
   for (int i = 0; i < kRegRuns; ++i) {
     const bool on = (uint32_t)i < md.nruns;
-    r.sr[i] = on ? md.sr[i] : 0u;
-    r.sl[i] = on ? md.sl[i] : 0u;
-    r.mk[i] = on ? md.msk[i] : 0ull;
+    r.sh[i] = on ? md.sr[i] - md.sl[i] : 0u;
+    r.mk[i] = on ? md.msk[i] << md.sl[i] : 0ull;
+    if (on && md.sr[i] + (uint32_t)(64 - __clzll(md.msk[i])) > 32u) r.fits32 = false;
   }
 }
 
+// (full >> sr) & msk) << sl == (full >> (sr - sl)) & (msk << sl): one
+// shift and one AND-OR per run, in 32-bit arithmetic when every run lies in
+// the low 32 bits (the masked key then fits 32 bits as well).
 __device__ __forceinline__ uint64_t masked_key_r(uint64_t full, const MaskRegs& r,
                                                  const MaskDesc& md) {
   if (!r.fits) return masked_key(full, md);
+  if (r.fits32) {
+    const uint32_t f = (uint32_t)full;
+    uint32_t k = 0;
+#pragma unroll
+    for (int i = 0; i < kRegRuns; ++i) k |= (f >> r.sh[i]) & (uint32_t)r.mk[i];
+    return k;
+  }
   uint64_t k = 0;
 #pragma unroll
-  for (int i = 0; i < kRegRuns; ++i) k |= ((full >> r.sr[i]) & r.mk[i]) << r.sl[i];
+  for (int i = 0; i < kRegRuns; ++i) k |= (full >> r.sh[i]) & r.mk[i];
   return k;
 }
 

@@ -50,6 +50,7 @@ CASES = [  # (seed, n, sigma, lo, hi, g, k)
     (123, 25, 2, 0, 80, 4, 1),        # binary alphabet: 2..16-column masks, rows padded to 128 columns
     (124, 19, 3, 5, 60, 6, 2),        # sigma = 3 (2 bits per symbol, code 3 unused)
     (125, 9, 4, 10, 40, 5, 5),        # M = 0: the spectrum level alone
+    (126, 30, 4, 20, 150, 13, 7),     # 26-bit full keys: four byte tables per mask
 ]
 
 
