@@ -62,13 +62,14 @@ __device__ __forceinline__ uint32_t lower_bound_seq(const uint32_t* __restrict__
 // Eq. 9 then Eq. 7 for one (x, y): N_m = C_m - sum_{j<m} C(g-j, m-j) N_j,
 // K = sum_m h_m N_m.  Arithmetic is modulo 2^32; every final N_m lies in
 // [0, W_x W_y] and K < 2^31 (checked on the host), so the results are exact.
+template <int kL = kMaxLevels>
 __device__ __forceinline__ uint32_t ie_combine(const uint32_t* C, uint32_t M,
                                                const uint32_t (*ie)[kMaxLevels],
                                                const uint32_t* h,
                                                uint32_t* N) {
   uint32_t K = 0;
 #pragma unroll
-  for (int m = 0; m < kMaxLevels; ++m) {
+  for (int m = 0; m < kL; ++m) {
     if ((uint32_t)m <= M) {
       uint32_t v = C[m];
 #pragma unroll
@@ -325,9 +326,13 @@ k_diag(const DsInfo* __restrict__ dsv, uint32_t nds, uint32_t nseq, const AccPar
 // and Khat at (x, y) and, through a shared-memory transpose, at (y, x).
 // Khat(x, y) = (K * r_x) * r_y (a few ulp from K / sqrt(Kxx Kyy)), exactly
 // 1 on a nonzero diagonal, 0 where a diagonal is 0.  Lower tiles exit.
+// kL >= M + 1 bounds the levels held in registers; kNm: the N_m planes are
+// written too (every row's profile is then kept until its planes are
+// stored; without them a row's profile lives only while its K is formed,
+// which keeps the kernel at a third of the registers).
+template <int kL, bool kNm>
 __global__ void __launch_bounds__(256)
-k_combine(const DsInfo* __restrict__ dsv, uint32_t nds, const AccParams p, int want_nm,
-          int want_khat) {
+k_combine(const DsInfo* __restrict__ dsv, uint32_t nds, const AccParams p, int want_khat) {
   __shared__ int32_t ti[32][33];
   __shared__ double td[32][33];
   const uint32_t b = blockIdx.x;
@@ -342,7 +347,7 @@ k_combine(const DsInfo* __restrict__ dsv, uint32_t nds, const AccParams p, int w
   const uint64_t nn = (uint64_t)n * n;
   const uint32_t M = p.M;
   // Four elements per thread: rows I*32 + ty + 8 r, column J*32 + tx.
-  uint32_t Nv[4][kMaxLevels];
+  uint32_t Nv[kNm ? 4 : 1][kL];
   uint32_t Kv[4];
   bool up[4];
   const uint32_t col = J * 32 + tx;
@@ -351,32 +356,35 @@ k_combine(const DsInfo* __restrict__ dsv, uint32_t nds, const AccParams p, int w
     const uint32_t row = I * 32 + ty + 8 * r;
     up[r] = row < n && col < n && row <= col;
     Kv[r] = 0;
+    uint32_t* N = Nv[kNm ? r : 0];
 #pragma unroll
-    for (int m = 0; m < kMaxLevels; ++m) Nv[r][m] = 0;
+    for (int m = 0; m < kL; ++m) N[m] = 0;
     if (up[r]) {
-      uint32_t C[kMaxLevels];
+      uint32_t C[kL];
       const uint64_t o = (uint64_t)row * n + col;
 #pragma unroll
-      for (int m = 0; m < kMaxLevels; ++m) C[m] = (uint32_t)m <= M ? D.C[m * nn + o] : 0u;
-      Kv[r] = ie_combine(C, M, p.ie, p.h, Nv[r]);
+      for (int m = 0; m < kL; ++m) C[m] = (uint32_t)m <= M ? D.C[m * nn + o] : 0u;
+      Kv[r] = ie_combine<kL>(C, M, p.ie, p.h, N);
       uint32_t CM = 0;
 #pragma unroll
-      for (int m = 0; m < kMaxLevels; ++m)
+      for (int m = 0; m < kL; ++m)
         if ((uint32_t)m == M) CM = C[m];
       if (Kv[r] != CM) atomicOr(p.status, kErrKneCM);
     }
   }
   // Plane 0 is K, planes 1..M+1 are N_0..N_M: upper write, then the
   // mirrored lower write.
-  const int nplanes = 1 + ((want_nm && D.Nm) ? (int)M + 1 : 0);
+  const int nplanes = 1 + ((kNm && D.Nm) ? (int)M + 1 : 0);
   for (int pl = 0; pl < nplanes; ++pl) {
     int32_t* X = pl == 0 ? D.K : D.Nm + (uint64_t)(pl - 1) * nn;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       uint32_t v = Kv[r];
+      if constexpr (kNm) {
 #pragma unroll
-      for (int m = 0; m < kMaxLevels; ++m)
-        if (m == pl - 1) v = Nv[r][m];
+        for (int m = 0; m < kL; ++m)
+          if (m == pl - 1) v = Nv[r][m];
+      }
       const uint32_t row = I * 32 + ty + 8 * r;
       if (up[r]) X[(uint64_t)row * n + col] = (int32_t)v;
       ti[ty + 8 * r][tx] = (int32_t)v;
@@ -591,7 +599,19 @@ void launch_diag(const DsInfo* d_ds, uint32_t nds, uint32_t nseq_total, const Ac
 void launch_combine(const DsInfo* d_ds, uint32_t nds, uint32_t ntiles, const AccParams& coef,
                     bool want_nm, bool want_khat, cudaStream_t st) {
   if (ntiles == 0) return;
-  k_combine<<<ntiles, 256, 0, st>>>(d_ds, nds, coef, want_nm ? 1 : 0, want_khat ? 1 : 0);
+  const int kh = want_khat ? 1 : 0;
+  // want_nm asks for the planes; a dataset without an N_m buffer writes none.
+  if (coef.M + 1 <= 8) {
+    if (want_nm)
+      k_combine<8, true><<<ntiles, 256, 0, st>>>(d_ds, nds, coef, kh);
+    else
+      k_combine<8, false><<<ntiles, 256, 0, st>>>(d_ds, nds, coef, kh);
+  } else {
+    if (want_nm)
+      k_combine<kMaxLevels, true><<<ntiles, 256, 0, st>>>(d_ds, nds, coef, kh);
+    else
+      k_combine<kMaxLevels, false><<<ntiles, 256, 0, st>>>(d_ds, nds, coef, kh);
+  }
 }
 
 void launch_pairs_global(const uint32_t* segtot_E, const uint32_t* eseq,
