@@ -437,23 +437,6 @@ int copy_to_host(Work& w, const std::vector<Xfer>& xs, bool direct) {
   size_t total = 0;
   for (const Xfer& x : xs) total += x.bytes;
   cudaError_t e = cudaSuccess;
-  if (direct && total >= ((size_t)64 << 20) && w.cs2) {
-    // Large outputs: pieces alternate between the two streams of the Work,
-    // so that two copies are in flight at once (one device-to-host copy
-    // does not fill the link to the host).
-    constexpr size_t kPiece = (size_t)16 << 20;
-    e = cudaEventRecord(w.ev_fork, w.cs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(w.cs2, w.ev_fork, 0);
-    size_t k = 0;
-    for (const Xfer& x : xs)
-      for (size_t o = 0; o < x.bytes && e == cudaSuccess; o += kPiece, ++k)
-        e = cudaMemcpyAsync((uint8_t*)x.dst + o, (const uint8_t*)x.src + o, std::min(kPiece, x.bytes - o),
-                            cudaMemcpyDeviceToHost, (k & 1) ? w.cs2 : w.cs);
-    if (e == cudaSuccess) e = cudaEventRecord(w.ev_join, w.cs2);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(w.cs, w.ev_join, 0);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(w.cs);
-    return e == cudaSuccess ? GAKCO_OK : wcuda(w, e, "copy results to host");
-  }
   if (direct || total < ((size_t)8 << 20)) {
     for (const Xfer& x : xs)
       if (x.bytes && e == cudaSuccess) e = cudaMemcpyAsync(x.dst, x.src, x.bytes, cudaMemcpyDeviceToHost, w.cs);
