@@ -206,23 +206,17 @@ def run_reference(args):
 
 
 # DRAM bytes (read + write) per unit of work from one ncu capture of the
-# same kernels on a smaller case (the DNA N = 4000 dataset, see
-# profiles/dense_scatter_gemm_accum_dna_4000.md), scaled to a launch of the
-# bench by its units; traffic grows in proportion to them.
+# same kernels on a smaller case (one step of the DNA N = 2000 dataset, see
+# profiles/traffic_dna_2000.md), scaled to a launch of the bench by its
+# units; traffic grows in proportion to them.
 NCU_BYTES_PER_UNIT = {
-    "accumulate": (4.426e9 / 3.16e9, "pair update"),
-    "dense_gemm": (3.534e9 / 1.19e13, "flop"),
-    "dense_scatter": (3.506e9 / 3.46e9, "byte of A"),
-    "sort_pass": (2.103e9 / 2.493e9, "algorithmic byte"),
-    "run_length": (1.923e9 / 1.344e9, "algorithmic byte"),
+    "accumulate": ((1.3178e9 + 0.1110e9) / 8.292e8, "pair update"),
+    "dense_gemm": ((1.7627e9 + 0.0002e9) / 3.442e12, "flop"),
+    "dense_scatter": ((0.0216e9 + 1.6967e9) / 1.762e9, "byte of A"),
+    "sort_pass": ((1.1910e9 + 0.9118e9) / 2.493e9, "algorithmic byte"),
+    "run_length": ((1.1468e9 + 0.6909e9) / 1.344e9, "algorithmic byte"),
 }
-NCU_SOURCE = {
-    "accumulate": "profiles/dense_scatter_gemm_accum_dna_4000.md (scaled by units)",
-    "dense_gemm": "profiles/dense_scatter_gemm_accum_dna_4000.md (scaled by units)",
-    "dense_scatter": "profiles/dense_scatter_gemm_accum_dna_4000.md (scaled by units)",
-    "sort_pass": "profiles/traffic_dna_2000.md (scaled by units)",
-    "run_length": "profiles/traffic_dna_2000.md (scaled by units)",
-}
+NCU_SOURCE = {name: "profiles/traffic_dna_2000.md (scaled by units)" for name in NCU_BYTES_PER_UNIT}
 
 
 def kernel_rooflines(timings, work, peaks, sm_count, smem_atomic_peak=None):
