@@ -257,12 +257,28 @@ k_accum(const AccParams p) {
           uint32_t owner0 = 0;  // rank of the range holding the round's first pair
           uint32_t pp = lane;   // this lane's pair in the round
           const uint32_t full = total & ~31u;
-          for (uint32_t p0 = 0; p0 < full; p0 += 32, pp += 32) {
+          uint32_t p0 = 0;
+          // Two rounds at a time: both entry loads are in flight before
+          // either round's atomic.
+          for (; p0 + 32 < full; p0 += 64, pp += 64) {
+            const uint32_t bits0 = __reduce_or_sync(kFull, bit_or_zero(dpos - p0));
+            const uint32_t bits1 = __reduce_or_sync(kFull, bit_or_zero(dpos - p0 - 32u));
+            const uint32_t o1 = owner0 + __popc(bits0);
+            const uint2 rc0 = s_rbc[w][owner0 + __popc(bits0 & lt_mask)];
+            const uint2 rc1 = s_rbc[w][o1 + __popc(bits1 & lt_mask)];
+            const uint32_t v0 = es[rc0.x + pp];
+            const uint32_t v1 = es[rc1.x + pp + 32u];
+            atomicAdd(&acc[min((v0 >> 16) - c0, width)], rc0.y * (v0 & 0xFFFFu));
+            atomicAdd(&acc[min((v1 >> 16) - c0, width)], rc1.y * (v1 & 0xFFFFu));
+            owner0 = o1 + __popc(bits1);
+          }
+          if (p0 < full) {
             const uint32_t bits = __reduce_or_sync(kFull, bit_or_zero(dpos - p0));
             const uint2 rc = s_rbc[w][owner0 + __popc(bits & lt_mask)];
             const uint32_t v = es[rc.x + pp];
             atomicAdd(&acc[min((v >> 16) - c0, width)], rc.y * (v & 0xFFFFu));
             owner0 += __popc(bits);
+            pp += 32;
           }
           if (full < total) {
             const uint32_t bits = __reduce_or_sync(kFull, bit_or_zero(dpos - full));
