@@ -61,6 +61,7 @@ constexpr int kScatterMasks = 16;  // masks of one scatter block held in shared 
 constexpr int kScatterWarps = kScatterThreads / 32;
 constexpr int kScatterRuns = 5;    // kept-position runs of a mask cut in registers
 constexpr int kRunMasks = 64;      // masks of one problem whose runs a scatter block stages
+constexpr int kRowKeys = 1024;     // windows of a row whose 32-bit full keys a block stages
 
 // A mask's kept-position runs for the scatter's 32-bit cut (nruns = ~0:
 // the mask takes the generic cut).  A run moves from bit sr of the full key
@@ -215,6 +216,7 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
   extern __shared__ uint32_t cnt[];  // two 16-bit counts per word (counts <= 65535 windows)
   __shared__ MaskDesc smask[kNarrow ? 1 : kScatterMasks];
   __shared__ MaskRuns sruns[kNarrow ? kRunMasks : 1];
+  __shared__ uint32_t srow[kNarrow ? kRowKeys : 1];
   const uint32_t bx = blockIdx.x, tid = threadIdx.x;
   uint32_t lo = 0, hi = nprobs;  // last problem with row0 <= bx
   while (hi - lo > 1) {
@@ -240,7 +242,11 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
     const uint32_t words = (uint32_t)(ld < (uint64_t)kDenseScatterCols ? ld : kDenseScatterCols) / 2;
     for (uint32_t i = tid; i < words / 4; i += kScatterThreads) ((uint4*)cnt)[i] = make_uint4(0, 0, 0, 0);
   }
-  // 32-bit keys: the runs of every mask of the problem, staged once.
+  // 32-bit keys: the runs of every mask of the problem, and the row's full
+  // keys, staged once (every chunk cuts the same keys).
+  const bool keys_staged = kNarrow && nw <= (uint32_t)kRowKeys;
+  if (keys_staged)
+    for (uint32_t i = tid; i < nw; i += kScatterThreads) srow[i] = (uint32_t)fk[i];
   const bool runs_staged = kNarrow && P.mcount <= (uint32_t)kRunMasks;
   if (runs_staged) {
     for (uint32_t i = tid; i < P.mcount; i += kScatterThreads) {
@@ -296,7 +302,7 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
             mk[r] = mr.mk[r];
           }
           for (uint32_t wi = wlo + (tid & 31); wi < whi; wi += 32) {
-            const uint32_t f = (uint32_t)fk[wi];
+            const uint32_t f = keys_staged ? srow[wi] : (uint32_t)fk[wi];
             uint32_t k = 0;
 #pragma unroll
             for (int r = 0; r < kScatterRuns; ++r) k |= (f >> sh[r]) & mk[r];
