@@ -167,36 +167,34 @@ k_upsweep(const SegDesc* __restrict__ segs, const uint32_t* __restrict__ tile_se
     hist[sd.hist + (uint64_t)i * sd.ntiles + lt] = sh[i];
 }
 
-// Grid (segments, digits): exclusive scan of one digit's per-tile counts
-// of one segment (contiguous in the digit-major layout), in place; the
-// digit's total to dtot[segment * radix + digit].
+// Grid (segments, digits / kWarps), one warp per (segment, digit):
+// exclusive scan of the digit's per-tile counts of the segment (contiguous
+// in the digit-major layout), in place; the digit's total to
+// dtot[segment * radix + digit].  (A block per digit spent most of its time
+// being scheduled: a segment has a few hundred tiles.)
 __global__ void __launch_bounds__(kSortThreads)
 k_digit_scan(const SegDesc* __restrict__ segs, uint32_t* __restrict__ hist, uint32_t* __restrict__ dtot,
              int rbits) {
-  __shared__ uint32_t sw[kWarps + 1];
-  const uint32_t s = blockIdx.x, d = blockIdx.y;
+  const uint32_t s = blockIdx.x;
+  const uint32_t d = blockIdx.y * kWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (d >= (1u << rbits)) return;  // (the whole warp)
   const SegDesc sd = segs[s];
   uint32_t* __restrict__ h = hist + sd.hist + (uint64_t)d * sd.ntiles;
   uint32_t carry = 0;
-  for (uint32_t b = 0; b < sd.ntiles; b += kSortThreads * 4) {
-    uint32_t v[4], sum = 0;
+  for (uint32_t b = 0; b < sd.ntiles; b += 32) {
+    const uint32_t i = b + lane;
+    const uint32_t v = i < sd.ntiles ? h[i] : 0u;
+    uint32_t incl = v;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t i = b + threadIdx.x * 4 + q;
-      v[q] = i < sd.ntiles ? h[i] : 0u;
-      sum += v[q];
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
     }
-    uint32_t tot;
-    uint32_t pre = block_excl_scan(sum, sw, &tot) + carry;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t i = b + threadIdx.x * 4 + q;
-      if (i < sd.ntiles) h[i] = pre;
-      pre += v[q];
-    }
-    carry += tot;
+    if (i < sd.ntiles) h[i] = carry + incl - v;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
   }
-  if (threadIdx.x == 0) dtot[((uint64_t)s << rbits) + d] = carry;
+  if (lane == 0) dtot[((uint64_t)s << rbits) + d] = carry;
 }
 
 // One block per segment: the digit totals become the digits' starts
@@ -982,7 +980,7 @@ void sort_pass_t(bool first, const SegDesc* segs, uint32_t nsegs,
                  uint32_t* vout, uint32_t* hist, uint32_t* dtot, int shift, int rbits,
                  cudaStream_t st) {
   const size_t radix = (size_t)1 << rbits;
-  const dim3 scan_grid(nsegs, (unsigned)radix);
+  const dim3 scan_grid(nsegs, (unsigned)((radix + kWarps - 1) / kWarps));
   const size_t up_smem = radix * 4;
   const size_t dn_smem = downsweep_smem(rbits, (int)sizeof(KeyT));
   KeyT* ki = (KeyT*)kin;
