@@ -197,6 +197,37 @@ k_digit_scan(const SegDesc* __restrict__ segs, uint32_t* __restrict__ hist, uint
   if (lane == 0) dtot[((uint64_t)s << rbits) + d] = carry;
 }
 
+// The same with a block per (segment, digit), four counts per thread: for
+// segments of many tiles (grid (segments, digits)).
+__global__ void __launch_bounds__(kSortThreads)
+k_digit_scan_block(const SegDesc* __restrict__ segs, uint32_t* __restrict__ hist, uint32_t* __restrict__ dtot,
+             int rbits) {
+  __shared__ uint32_t sw[kWarps + 1];
+  const uint32_t s = blockIdx.x, d = blockIdx.y;
+  const SegDesc sd = segs[s];
+  uint32_t* __restrict__ h = hist + sd.hist + (uint64_t)d * sd.ntiles;
+  uint32_t carry = 0;
+  for (uint32_t b = 0; b < sd.ntiles; b += kSortThreads * 4) {
+    uint32_t v[4], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t i = b + threadIdx.x * 4 + q;
+      v[q] = i < sd.ntiles ? h[i] : 0u;
+      sum += v[q];
+    }
+    uint32_t tot;
+    uint32_t pre = block_excl_scan(sum, sw, &tot) + carry;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t i = b + threadIdx.x * 4 + q;
+      if (i < sd.ntiles) h[i] = pre;
+      pre += v[q];
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) dtot[((uint64_t)s << rbits) + d] = carry;
+}
+
 // One block per segment: the digit totals become the digits' starts
 // (exclusive scan, in place).
 __global__ void __launch_bounds__(kSortThreads)
@@ -980,7 +1011,9 @@ void sort_pass_t(bool first, const SegDesc* segs, uint32_t nsegs,
                  uint32_t* vout, uint32_t* hist, uint32_t* dtot, int shift, int rbits,
                  cudaStream_t st) {
   const size_t radix = (size_t)1 << rbits;
-  const dim3 scan_grid(nsegs, (unsigned)((radix + kWarps - 1) / kWarps));
+  // A warp per digit while segments average at most 256 tiles, else a block.
+  const bool warp_scan = ntiles <= 256u * nsegs;
+  const dim3 scan_grid(nsegs, (unsigned)(warp_scan ? (radix + kWarps - 1) / kWarps : radix));
   const size_t up_smem = radix * 4;
   const size_t dn_smem = downsweep_smem(rbits, (int)sizeof(KeyT));
   KeyT* ki = (KeyT*)kin;
@@ -988,14 +1021,20 @@ void sort_pass_t(bool first, const SegDesc* segs, uint32_t nsegs,
   if (first) {
     k_upsweep<KeyT, true><<<ntiles, kSortThreads, up_smem, st>>>(segs, tile_seg, masks, fullkey, ki,
                                                                   hist, shift, rbits);
-    k_digit_scan<<<scan_grid, kSortThreads, 0, st>>>(segs, hist, dtot, rbits);
+    if (warp_scan)
+      k_digit_scan<<<scan_grid, kSortThreads, 0, st>>>(segs, hist, dtot, rbits);
+    else
+      k_digit_scan_block<<<scan_grid, kSortThreads, 0, st>>>(segs, hist, dtot, rbits);
     k_digit_base<<<nsegs, kSortThreads, 0, st>>>(dtot, rbits);
     k_downsweep<KeyT, true><<<ntiles, kSortThreads, dn_smem, st>>>(segs, tile_seg, ki, vin, ko, vout,
                                                                     hist, dtot, shift, rbits);
   } else {
     k_upsweep<KeyT, false><<<ntiles, kSortThreads, up_smem, st>>>(segs, tile_seg, masks, fullkey, ki,
                                                                    hist, shift, rbits);
-    k_digit_scan<<<scan_grid, kSortThreads, 0, st>>>(segs, hist, dtot, rbits);
+    if (warp_scan)
+      k_digit_scan<<<scan_grid, kSortThreads, 0, st>>>(segs, hist, dtot, rbits);
+    else
+      k_digit_scan_block<<<scan_grid, kSortThreads, 0, st>>>(segs, hist, dtot, rbits);
     k_digit_base<<<nsegs, kSortThreads, 0, st>>>(dtot, rbits);
     k_downsweep<KeyT, false><<<ntiles, kSortThreads, dn_smem, st>>>(segs, tile_seg, ki, vin, ko, vout,
                                                                      hist, dtot, shift, rbits);
