@@ -258,6 +258,23 @@ k_accum(const AccParams p) {
           uint32_t pp = lane;   // this lane's pair in the round
           const uint32_t full = total & ~31u;
           uint32_t p0 = 0;
+          // Four rounds at a time: every entry load in flight before the atomics.
+          for (; p0 + 96 < full; p0 += 128, pp += 128) {
+            uint32_t bits[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bits[q] = __reduce_or_sync(kFull, bit_or_zero(dpos - p0 - 32u * q));
+            uint2 rc[4];
+            uint32_t v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              rc[q] = s_rbc[w][owner0 + __popc(bits[q] & lt_mask)];
+              owner0 += __popc(bits[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = es[rc[q].x + pp + 32u * q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) atomicAdd(&acc[min((v[q] >> 16) - c0, width)], rc[q].y * (v[q] & 0xFFFFu));
+          }
           // Two rounds at a time: both entry loads are in flight before
           // either round's atomic.
           for (; p0 + 32 < full; p0 += 64, pp += 64) {
