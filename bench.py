@@ -210,11 +210,11 @@ def run_reference(args):
 # profiles/traffic_dna_2000.md), scaled to a launch of the bench by its
 # units; traffic grows in proportion to them.
 NCU_BYTES_PER_UNIT = {
-    "accumulate": ((1.3178e9 + 0.1110e9) / 8.292e8, "pair update"),
-    "dense_gemm": ((1.7627e9 + 0.0002e9) / 3.442e12, "flop"),
-    "dense_scatter": ((0.0216e9 + 1.6967e9) / 1.762e9, "byte of A"),
-    "sort_pass": ((1.1910e9 + 0.9118e9) / 2.493e9, "algorithmic byte"),
-    "run_length": ((1.1468e9 + 0.6909e9) / 1.344e9, "algorithmic byte"),
+    "accumulate": ((1.3201e9 + 0.0887e9) / 8.292e8, "pair update"),
+    "dense_gemm": ((1.7618e9 + 0.0001e9) / 3.442e12, "flop"),
+    "dense_scatter": ((0.0217e9 + 1.6969e9) / 1.762e9, "byte of A"),
+    "sort_pass": ((1.1911e9 + 0.9131e9) / 2.493e9, "algorithmic byte"),
+    "run_length": ((1.1498e9 + 0.6941e9) / 1.344e9, "algorithmic byte"),
 }
 NCU_SOURCE = {name: "profiles/traffic_dna_2000.md (scaled by units)" for name in NCU_BYTES_PER_UNIT}
 
