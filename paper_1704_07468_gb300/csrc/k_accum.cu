@@ -213,7 +213,27 @@ k_accum(const AccParams p) {
           }
           const uint32_t total = __shfl_sync(kFull, incl, 31);
           const uint32_t excl = incl - cnt;
-          for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+          uint32_t p0 = 0;
+          // Two full rounds at a time: both owner searches, then both entry
+          // loads in flight before either atomic.
+          for (; p0 + 64 <= total; p0 += 64) {
+            const uint32_t pa = p0 + lane, pb = pa + 32;
+            uint32_t oa = 0, ob = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+              const uint32_t ta = __shfl_sync(kFull, incl, oa + step - 1);
+              const uint32_t tb = __shfl_sync(kFull, incl, ob + step - 1);
+              if (ta <= pa) oa += step;
+              if (tb <= pb) ob += step;
+            }
+            const uint32_t la = __shfl_sync(kFull, lo, oa) - __shfl_sync(kFull, excl, oa);
+            const uint32_t lb = __shfl_sync(kFull, lo, ob) - __shfl_sync(kFull, excl, ob);
+            const uint32_t ca = __shfl_sync(kFull, c, oa), cb = __shfl_sync(kFull, c, ob);
+            const uint32_t va = es[la + pa], vb = es[lb + pb];
+            atomicAdd(&acc[min((va >> 16) - c0, width)], ca * (va & 0xFFFFu));
+            atomicAdd(&acc[min((vb >> 16) - c0, width)], cb * (vb & 0xFFFFu));
+          }
+          for (; p0 < total; p0 += 32) {
             const uint32_t pp = p0 + lane;
             uint32_t o = 0;
 #pragma unroll
