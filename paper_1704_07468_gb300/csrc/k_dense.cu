@@ -339,36 +339,44 @@ k_dense_scatter(const DenseProb* __restrict__ probs, uint32_t nprobs, uint32_t p
     // 256 contiguous bytes.
     uint2* out = (uint2*)(P.A + (uint64_t)x * ld + c0);
     uint4* cw = (uint4*)cnt;
-    for (uint32_t u = tid; u < ncol / 8; u += kScatterThreads) {
-      const uint4 a = cw[u];
-      cw[u] = make_uint4(0, 0, 0, 0);
+    auto convert = [&](uint32_t u, const uint4 a) {
       const uint32_t m = __vmaxu2(__vmaxu2(a.x, a.y), __vmaxu2(a.z, a.w));
       cmax = __vmaxu2(cmax, m);
-      uint2 o;
-      if ((m & 0xFFF8FFF8u) == 0u) {
-        // Every count <= 7 (nearly all words): table lookup.
-        o = make_uint2(e4m3x4_of_small_counts(a.x, a.y), e4m3x4_of_small_counts(a.z, a.w));
-      } else {
-        const uint32_t w[4] = {a.x, a.y, a.z, a.w};
-        uint32_t e[4];
+      if ((m & 0xFFF8FFF8u) == 0u)  // every count <= 7 (nearly all words): table lookup
+        return make_uint2(e4m3x4_of_small_counts(a.x, a.y), e4m3x4_of_small_counts(a.z, a.w));
+      const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+      uint32_t e[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) e[q] = e4m3x2_of_counts(__vminu2(w[q], 0x00100010u));
-        o = make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
-        // A half h of m exceeds 16 iff h + 15 reaches bit 5 or h is above
-        // 65520 (h + 15 then carries out of its half); both show in bits
-        // 5-15 of (m + 15) | m.
-        if ((((m + 0x000F000Fu) | m) & 0xFFE0FFE0u) != 0u) {
+      for (int q = 0; q < 4; ++q) e[q] = e4m3x2_of_counts(__vminu2(w[q], 0x00100010u));
+      // A half h of m exceeds 16 iff h + 15 reaches bit 5 or h is above
+      // 65520 (h + 15 then carries out of its half); both show in bits
+      // 5-15 of (m + 15) | m.
+      if ((((m + 0x000F000Fu) | m) & 0xFFE0FFE0u) != 0u) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const uint32_t c = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-            if (c > 16) {
-              const uint32_t slot = atomicAdd(ovf_n, 1u);
-              if (slot < ovf_cap) ovf[slot] = DenseOvf{p0 + lo, x, (uint32_t)(c0 + 8 * u + q), c};
-            }
+        for (int q = 0; q < 8; ++q) {
+          const uint32_t c = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+          if (c > 16) {
+            const uint32_t slot = atomicAdd(ovf_n, 1u);
+            if (slot < ovf_cap) ovf[slot] = DenseOvf{p0 + lo, x, (uint32_t)(c0 + 8 * u + q), c};
           }
         }
       }
-      out[u] = o;
+      return make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
+    };
+    // Two words per thread and step (both reads in flight together).
+    const uint32_t nwords = ncol / 8;
+    uint32_t u = tid;
+    for (; u + kScatterThreads < nwords; u += 2 * kScatterThreads) {
+      const uint4 a = cw[u], b = cw[u + kScatterThreads];
+      cw[u] = make_uint4(0, 0, 0, 0);
+      cw[u + kScatterThreads] = make_uint4(0, 0, 0, 0);
+      out[u] = convert(u, a);
+      out[u + kScatterThreads] = convert(u + kScatterThreads, b);
+    }
+    if (u < nwords) {
+      const uint4 a = cw[u];
+      cw[u] = make_uint4(0, 0, 0, 0);
+      out[u] = convert(u, a);
     }
     // The next chunk's counting waits at its first barrier for this
     // conversion (and its clearing) to finish.
